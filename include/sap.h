@@ -1,0 +1,232 @@
+/*
+ * sap.h -- C ABI of libsap, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of the Secant-Avoidance Projection (SAP) algorithm:
+ * Kvinge, Farnell, Kirby, Peterson, "A GPU-Oriented Algorithm Design for
+ * Secant-Based Dimensionality Reduction", arXiv:1807.03425.
+ *
+ * Problem (Sec. IV): for a point set X = {x_1..x_N} in R^n and an orthonormal
+ * n x k basis U, every pair i<j of distinct points has the unit secant
+ * s_ij = (x_i - x_j)/||x_i - x_j|| and the ratio r_ij = ||U^T s_ij||.  One SAP
+ * iteration (Algorithm 1) finds the pair with the smallest ratio and rotates U
+ * towards its secant with step alpha.  Dimension estimation (Sec. VI-A) runs
+ * SAP for k = 1..k_max; the noisy-data variant (Sec. VII) discards secants
+ * shorter than a threshold before normalising.
+ *
+ * Conventions shared by every call:
+ *  - X is N x n row-major.  A basis U is n x k column-major FP64, i.e. k
+ *    consecutive length-n vectors u_1..u_k.
+ *  - Pairs are reported as (i, j) with 0 <= i < j < N.  Ties in the argmin go
+ *    to the smallest pair index p(i,j) = i*N - i(i+1)/2 + (j-i-1); ties in the
+ *    pivot choice go to the smallest column.
+ *  - The library copies every input: the caller may free or reuse X and U as
+ *    soon as the call returns.  Outputs are written only into caller-owned
+ *    buffers.  Device memory the library needs is allocated at sap_create
+ *    (and grown by sap_run for longer histories) and freed by sap_destroy.
+ *  - A pointer argument is a host pointer unless the matching *_is_device
+ *    flag is non-zero, in which case it is a device pointer on the handle's
+ *    device.
+ *  - Work is enqueued on the handle's stream (default: a stream the library
+ *    creates; see sap_set_stream).  Calls that return values to the host
+ *    synchronise that stream before returning.
+ *  - Every call returns a status; nothing aborts, throws or traps.  A CUDA
+ *    error is sticky: after SAP_E_CUDA only sap_destroy is valid.  A handle is
+ *    not thread-safe.
+ *  - Precision: the argmin pair and the min ratio returned are decided by an
+ *    FP64 evaluation on the device from explicit differences; faster
+ *    low-precision tiers only select candidates, under certified error
+ *    bounds, so both paths return the same pair as an FP64 evaluation of all
+ *    pairs (up to FP64 rounding on exact ties).  The basis update and its
+ *    re-orthonormalisation are FP64.
+ */
+#ifndef SAP_H
+#define SAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sap_ctx *sap_handle; /* opaque; one per dataset or batch */
+
+typedef enum {
+    SAP_OK = 0,
+    SAP_E_ARG = 1,             /* an argument is out of range or NULL */
+    SAP_E_STATE = 2,           /* call not valid now (e.g. no basis set yet) */
+    SAP_E_NOT_ORTHONORMAL = 3, /* max |U^T U - I| > 1e-10 at sap_set_basis */
+    SAP_E_NO_SECANT = 4,       /* every pair is excluded (N < 2, duplicates, eps) */
+    SAP_E_OOM = 5,             /* device or host allocation failed */
+    SAP_E_CUDA = 6,            /* CUDA runtime error (sticky for the handle) */
+    SAP_E_TIMEOUT = 7,         /* a device-side bounded wait gave up */
+    SAP_E_NO_DEVICE = 8,       /* no usable CUDA device */
+    SAP_E_UNSUPPORTED = 9      /* valid request this build does not cover */
+} sap_status;
+
+typedef enum { SAP_F32 = 0, SAP_BF16 = 1, SAP_F64 = 2 } sap_dtype;
+
+/* Which all-pairs form evaluates the ratios (both return the same pair):
+ *  SAP_PLAIN        -- secants formed on the fly from tiles of X, projected
+ *                      with U (Sec. IV; the secant set is never stored).
+ *  SAP_RESTRUCTURED -- Y = X U once per iteration on tensor cores, then
+ *                      r_ij = ||y_i - y_j|| / ||x_i - x_j|| over all pairs
+ *                      with the lengths computed once (U^T(x_i - x_j) =
+ *                      y_i - y_j). */
+typedef enum { SAP_PLAIN = 0, SAP_RESTRUCTURED = 1 } sap_path;
+
+/* Reading of the rotation step (Sec. IV): LITERAL uses the printed direction
+ * (1-alpha) P P^T s + alpha (s - P P^T s); ANGLE blends the two unit vectors
+ * (1-alpha) v/|v| + alpha e/|e|. */
+typedef enum { SAP_UPDATE_LITERAL = 0, SAP_UPDATE_ANGLE = 1 } sap_update_mode;
+
+/* Operand split of the tensor-core Y = X U: two-term FP16 (hi + lo, three
+ * products) or two-term BF16, both with FP32 accumulation. */
+typedef enum { SAP_SPLIT_FP16 = 0, SAP_SPLIT_BF16 = 1 } sap_split;
+
+/* Statistics of the handle (read by sap_get_stats). */
+typedef struct {
+    int64_t n_points;        /* N */
+    int32_t n_dim;           /* n */
+    int32_t k;               /* target dimension of the current basis (0 if none) */
+    int64_t n_pairs;         /* N(N-1)/2 */
+    int64_t n_excluded;      /* duplicates plus pairs shorter than eps */
+    int64_t n_near;          /* pairs evaluated from explicit differences every
+                                iteration of the restructured form */
+    int64_t last_tier1;      /* candidates from the all-pairs pass, last iteration */
+    int64_t last_tier2;      /* candidates rechecked in FP64, last iteration */
+    int64_t kernel_launches; /* kernels launched since create (graph nodes count) */
+    double cert_bound;       /* absolute ratio bound of the restructured pass */
+    double y_error_unit;     /* bound on |y~ - y| per unit ||x - mean|| */
+} sap_stats;
+
+/* Library version string. */
+const char *sap_version(void);
+
+/* Human-readable name of a status code. */
+const char *sap_status_str(sap_status s);
+
+/* Message of the last failed call on this handle ("" if none). */
+const char *sap_last_error(sap_handle h);
+
+/*
+ * Create a handle for one dataset of N points in R^n (Sec. IV: "data set of k
+ * points" -- N here).  X is N x n row-major in dtype dt (FP32, BF16 as
+ * uint16 bits, or FP64); it is copied to the device.  The one-time length
+ * preparation (explicit-difference secant lengths, exclusions, the near-pair
+ * list of the restructured form) runs here.  FP64 data supports SAP_PLAIN
+ * only.  N >= 2, 1 <= n <= 16384, N <= 92681 (pair indices fit in 32 bits).
+ */
+sap_status sap_create(const void *X, int64_t N, int32_t n, sap_dtype dt,
+                      int x_is_device, sap_handle *out);
+
+/* Release every resource of the handle.  NULL is accepted. */
+sap_status sap_destroy(sap_handle h);
+
+/* Enqueue all later work on this cudaStream_t (NULL = the library's own
+ * stream).  The stream must belong to the handle's device. */
+sap_status sap_set_stream(sap_handle h, void *cuda_stream);
+
+/* Select the all-pairs form (default SAP_RESTRUCTURED for FP32/BF16 data,
+ * SAP_PLAIN for FP64 data). */
+sap_status sap_set_path(sap_handle h, sap_path p);
+
+/* Select the reading of the rotation step (default SAP_UPDATE_LITERAL). */
+sap_status sap_set_update_mode(sap_handle h, sap_update_mode m);
+
+/* Select the operand split of the tensor-core product (default FP16). */
+sap_status sap_set_split(sap_handle h, sap_split s);
+
+/*
+ * Noisy-data variant (Sec. VII): discard every secant whose length is less
+ * than eps before normalising (d == eps is kept; decided in FP64 as
+ * d^2 < eps^2).  eps = 0 restores the plain algorithm.  Re-runs the length
+ * preparation.  eps < 0 or not finite -> SAP_E_ARG.
+ */
+sap_status sap_set_min_secant_length(sap_handle h, double eps);
+
+/*
+ * Set the current basis P^(i) (Sec. IV): U is n x k column-major FP64 with
+ * orthonormal columns, 1 <= k <= min(n, 32).  Rejects max |U^T U - I| > 1e-10
+ * with SAP_E_NOT_ORTHONORMAL.  Resets the iteration counter.
+ */
+sap_status sap_set_basis(sap_handle h, const double *U, int32_t k,
+                         int u_is_device);
+
+/* Copy the current basis (n x k column-major FP64) into U_out. */
+sap_status sap_get_basis(sap_handle h, double *U_out, int out_is_device);
+
+/*
+ * Algorithm 1, argmin step, under the current basis: the pair whose unit
+ * secant has the smallest projected length, and that length.  Any output
+ * pointer may be NULL.  Synchronises.  SAP_E_NO_SECANT if every pair is
+ * excluded.
+ */
+sap_status sap_min_secant(sap_handle h, int64_t *i, int64_t *j, double *ratio);
+
+/*
+ * One SAP iteration (Algorithm 1): evaluate every secant, take the argmin,
+ * then pivot, modified Gram-Schmidt, rotate the first column by alpha and
+ * re-orthonormalise in FP64.  alpha in [0, 1].  The evaluated pair and ratio
+ * (of the basis before the update) are returned through the optional
+ * outputs; with all three NULL the call does not synchronise.
+ */
+sap_status sap_step(sap_handle h, double alpha, int64_t *i, int64_t *j,
+                    double *ratio);
+
+/*
+ * iters SAP iterations followed by one more evaluation, as a captured CUDA
+ * graph (Algorithm 1 loop).  hist (nullable, iters+1 entries) receives the
+ * min ratio of U_0..U_iters and argmins (nullable, 2*(iters+1) entries) the
+ * pairs; with both NULL the call does not synchronise and the results stay
+ * on the device (sap_get_history).  The basis afterwards is U_iters.
+ */
+sap_status sap_run(sap_handle h, double alpha, int32_t iters, double *hist,
+                   int64_t *argmins);
+
+/* Copy the history of the last sap_run (iters+1 entries each; argmins as
+ * (i, j) pairs).  Synchronises.  Either pointer may be NULL. */
+sap_status sap_get_history(sap_handle h, double *hist, int64_t *argmins,
+                           int32_t capacity);
+
+/*
+ * Dimension estimation (Sec. VI-A): run SAP for every k = 1..k_max (k_max <=
+ * min(n, 32)) from the first k columns of U0 (n x k_max column-major FP64,
+ * orthonormal), iters iterations each with step alpha; ratios_out[k-1]
+ * receives the min ratio of the final basis for k, and k_out the smallest k
+ * whose ratio exceeds threshold (strictly), or -1.  All k run together: one
+ * launch per stage covers every basis.  Leaves the handle's basis unchanged.
+ */
+sap_status sap_estimate_dim(sap_handle h, const double *U0, int32_t k_max,
+                            int32_t iters, double alpha, double threshold,
+                            int32_t *k_out, double *ratios_out);
+
+/*
+ * The projected data under the current basis (Sec. V shows such projections):
+ * Y_out[i*k + c] = <x_i - mean(X), u_c>, N x k row-major FP32, computed by
+ * the tensor-core product of the restructured form (split 16-bit operands,
+ * FP32 accumulation).  Rows are translated by -mean(X) U, so differences of
+ * rows are the projected secants U^T (x_i - x_j); each entry is within
+ * sap_stats.y_error_unit * ||x_i - mean(X)|| of the exact value.
+ * FP32/BF16 datasets only.  Synchronises.
+ */
+sap_status sap_project(sap_handle h, float *Y_out, int out_is_device);
+
+/* Read the handle's statistics. */
+sap_status sap_get_stats(sap_handle h, sap_stats *out);
+
+/*
+ * Kernel timing for measurement: while enabled, sap_step and sap_run launch
+ * kernels one by one (no graph) with CUDA events around each launch on the
+ * handle's stream; sap_get_kernel_time returns the accumulated device time
+ * (ms) and launch count of one kernel class.  Classes: 0 Y = XU product,
+ * 1 restructured all-pairs pass, 2 plain all-pairs pass, 3 explicit-difference
+ * recheck, 4 FP64 recheck, 5 update.  Enabling resets the accumulators.
+ */
+sap_status sap_set_profiling(sap_handle h, int enable);
+sap_status sap_get_kernel_time(sap_handle h, int32_t kernel_class,
+                               double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAP_H */

@@ -1,0 +1,356 @@
+"""ctypes binding of libsap (include/sap.h).
+
+Module-level functions carry the C names (``sap_create``, ``sap_step`` ...)
+and only marshal arguments; ``Sap`` is a small handle wrapper on top.  Arrays
+may be NumPy (host) or torch CUDA tensors (device; passed by pointer, no
+copy).  A basis is handled as a (k, n) C-contiguous FP64 array, which is the
+n x k column-major layout of the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libsap.so")
+_lib = None
+
+F32, BF16, F64 = 0, 1, 2
+PLAIN, RESTRUCTURED = 0, 1
+UPDATE_LITERAL, UPDATE_ANGLE = 0, 1
+SPLIT_FP16, SPLIT_BF16 = 0, 1
+KERNEL_CLASSES = {"gemm_y": 0, "restructured_pass": 1, "plain_pass": 2,
+                  "explicit_recheck": 3, "fp64_recheck": 4, "update": 5}
+
+STATUS = {0: "SAP_OK", 1: "SAP_E_ARG", 2: "SAP_E_STATE", 3: "SAP_E_NOT_ORTHONORMAL",
+          4: "SAP_E_NO_SECANT", 5: "SAP_E_OOM", 6: "SAP_E_CUDA", 7: "SAP_E_TIMEOUT",
+          8: "SAP_E_NO_DEVICE", 9: "SAP_E_UNSUPPORTED"}
+
+
+class SapError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        self.name = STATUS.get(code, "SAP_E_%d" % code)
+        super().__init__("%s%s" % (self.name, (": " + msg) if msg else ""))
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_dim", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("n_pairs", ctypes.c_int64),
+                ("n_excluded", ctypes.c_int64), ("n_near", ctypes.c_int64),
+                ("last_tier1", ctypes.c_int64), ("last_tier2", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("cert_bound", ctypes.c_double),
+                ("y_error_unit", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libsap.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError("libsap.so is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    i64p, f64p, i32p = (ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(ctypes.c_int32))
+    sig = {
+        "sap_version": ([], ctypes.c_char_p),
+        "sap_status_str": ([i32], ctypes.c_char_p),
+        "sap_last_error": ([vp], ctypes.c_char_p),
+        "sap_create": ([vp, i64, i32, i32, i32, ctypes.POINTER(vp)], i32),
+        "sap_destroy": ([vp], i32),
+        "sap_set_stream": ([vp, vp], i32),
+        "sap_set_path": ([vp, i32], i32),
+        "sap_set_update_mode": ([vp, i32], i32),
+        "sap_set_split": ([vp, i32], i32),
+        "sap_set_min_secant_length": ([vp, f64], i32),
+        "sap_set_basis": ([vp, vp, i32, i32], i32),
+        "sap_get_basis": ([vp, vp, i32], i32),
+        "sap_min_secant": ([vp, i64p, i64p, f64p], i32),
+        "sap_step": ([vp, f64, i64p, i64p, f64p], i32),
+        "sap_run": ([vp, f64, i32, vp, vp], i32),
+        "sap_get_history": ([vp, vp, vp, i32], i32),
+        "sap_estimate_dim": ([vp, vp, i32, i32, f64, f64, i32p, vp], i32),
+        "sap_project": ([vp, vp, i32], i32),
+        "sap_get_stats": ([vp, ctypes.POINTER(Stats)], i32),
+        "sap_set_profiling": ([vp, i32], i32),
+        "sap_get_kernel_time": ([vp, i32, f64p, i64p], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_names():
+    """Names of the C entry points this binding wraps."""
+    load_library()
+    return sorted(n for n in globals() if n.startswith("sap_") and callable(globals()[n]))
+
+
+def _ptr(a):
+    """(pointer, is_device) of a NumPy array or a torch tensor."""
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        return ctypes.c_void_p(a.data_ptr()), int(bool(a.is_cuda))
+    return a.ctypes.data_as(ctypes.c_void_p), 0
+
+
+def _check(h, code):
+    if code != 0:
+        msg = load_library().sap_last_error(h).decode() if h else ""
+        raise SapError(code, msg)
+
+
+# ----------------------------------------------------------- C entry points --
+
+def sap_version():
+    return load_library().sap_version().decode()
+
+
+def sap_status_str(code):
+    return load_library().sap_status_str(code).decode()
+
+
+def sap_last_error(h):
+    return load_library().sap_last_error(h).decode()
+
+
+def sap_create(X, dtype=None):
+    """X: (N, n) NumPy array (float32, float64, or uint16 BF16 bits) or a torch
+    CUDA tensor (float32, float64, bfloat16).  Returns a handle."""
+    lib = load_library()
+    if dtype is None:
+        dt = str(getattr(X, "dtype", ""))
+        if "float64" in dt:
+            dtype = F64
+        elif "bfloat16" in dt or "uint16" in dt:
+            dtype = BF16
+        else:
+            dtype = F32
+    if not hasattr(X, "data_ptr"):
+        want = {F32: np.float32, F64: np.float64, BF16: np.uint16}[dtype]
+        X = np.ascontiguousarray(X, dtype=want)
+    elif not X.is_contiguous():
+        raise ValueError("X must be contiguous")
+    N, n = X.shape
+    p, dev = _ptr(X)
+    h = ctypes.c_void_p()
+    code = lib.sap_create(p, N, n, dtype, dev, ctypes.byref(h))
+    if code != 0:
+        raise SapError(code, "sap_create(N=%d, n=%d)" % (N, n))
+    return h
+
+
+def sap_destroy(h):
+    _check(None, load_library().sap_destroy(h))
+
+
+def sap_set_stream(h, stream):
+    """stream: torch.cuda.Stream, an integer cudaStream_t, or None."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(h, load_library().sap_set_stream(h, ctypes.c_void_p(stream) if stream else None))
+
+
+def sap_set_path(h, path):
+    _check(h, load_library().sap_set_path(h, path))
+
+
+def sap_set_update_mode(h, mode):
+    _check(h, load_library().sap_set_update_mode(h, mode))
+
+
+def sap_set_split(h, split):
+    _check(h, load_library().sap_set_split(h, split))
+
+
+def sap_set_min_secant_length(h, eps):
+    _check(h, load_library().sap_set_min_secant_length(h, float(eps)))
+
+
+def sap_set_basis(h, U):
+    """U: (k, n) FP64 (NumPy or torch CUDA tensor), rows = basis vectors."""
+    if not hasattr(U, "data_ptr"):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+    p, dev = _ptr(U)
+    _check(h, load_library().sap_set_basis(h, p, U.shape[0], dev))
+
+
+def sap_get_basis(h, k, n, out=None):
+    if out is None:
+        out = np.empty((k, n), dtype=np.float64)
+    p, dev = _ptr(out)
+    _check(h, load_library().sap_get_basis(h, p, dev))
+    return out
+
+
+def sap_min_secant(h):
+    i, j, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    _check(h, load_library().sap_min_secant(h, ctypes.byref(i), ctypes.byref(j), ctypes.byref(r)))
+    return i.value, j.value, r.value
+
+
+def sap_step(h, alpha, sync=True):
+    lib = load_library()
+    if not sync:
+        _check(h, lib.sap_step(h, float(alpha), None, None, None))
+        return None
+    i, j, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    _check(h, lib.sap_step(h, float(alpha), ctypes.byref(i), ctypes.byref(j), ctypes.byref(r)))
+    return i.value, j.value, r.value
+
+
+def sap_run(h, alpha, iters, history=True):
+    lib = load_library()
+    if not history:
+        _check(h, lib.sap_run(h, float(alpha), int(iters), None, None))
+        return None
+    hist = np.empty(iters + 1, dtype=np.float64)
+    am = np.empty((iters + 1, 2), dtype=np.int64)
+    _check(h, lib.sap_run(h, float(alpha), int(iters), hist.ctypes.data_as(ctypes.c_void_p),
+                          am.ctypes.data_as(ctypes.c_void_p)))
+    return hist, am
+
+
+def sap_get_history(h, count):
+    hist = np.empty(count, dtype=np.float64)
+    am = np.empty((count, 2), dtype=np.int64)
+    _check(h, load_library().sap_get_history(h, hist.ctypes.data_as(ctypes.c_void_p),
+                                             am.ctypes.data_as(ctypes.c_void_p), count))
+    return hist, am
+
+
+def sap_estimate_dim(h, U0, iters, alpha, threshold):
+    """U0: (k_max, n) FP64; returns (k or -1, ratios[k_max])."""
+    U0 = np.ascontiguousarray(U0, dtype=np.float64)
+    kmax = U0.shape[0]
+    ratios = np.empty(kmax, dtype=np.float64)
+    kout = ctypes.c_int32()
+    _check(h, load_library().sap_estimate_dim(h, U0.ctypes.data_as(ctypes.c_void_p), kmax,
+                                              int(iters), float(alpha), float(threshold),
+                                              ctypes.byref(kout),
+                                              ratios.ctypes.data_as(ctypes.c_void_p)))
+    return kout.value, ratios
+
+
+def sap_project(h, out):
+    """out: (N, k) float32 NumPy array or torch CUDA tensor."""
+    p, dev = _ptr(out)
+    _check(h, load_library().sap_project(h, p, dev))
+    return out
+
+
+def sap_get_stats(h):
+    s = Stats()
+    _check(h, load_library().sap_get_stats(h, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+def sap_set_profiling(h, enable):
+    _check(h, load_library().sap_set_profiling(h, int(bool(enable))))
+
+
+def sap_get_kernel_time(h, kernel_class):
+    if isinstance(kernel_class, str):
+        kernel_class = KERNEL_CLASSES[kernel_class]
+    ms, cnt = ctypes.c_double(), ctypes.c_int64()
+    _check(h, load_library().sap_get_kernel_time(h, kernel_class, ctypes.byref(ms),
+                                                 ctypes.byref(cnt)))
+    return ms.value, cnt.value
+
+
+# ------------------------------------------------------------ handle class --
+
+class Sap:
+    """One dataset on the GPU.  Methods follow the C entry points."""
+
+    def __init__(self, X, dtype=None):
+        self.N, self.n = int(X.shape[0]), int(X.shape[1])
+        self.h = sap_create(X, dtype)
+        self.k = 0
+
+    def close(self):
+        if self.h:
+            sap_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        sap_set_stream(self.h, stream)
+
+    def set_path(self, path):
+        if isinstance(path, str):
+            path = {"plain": PLAIN, "restructured": RESTRUCTURED}[path]
+        sap_set_path(self.h, path)
+
+    def set_update_mode(self, mode):
+        if isinstance(mode, str):
+            mode = {"literal": UPDATE_LITERAL, "angle": UPDATE_ANGLE}[mode]
+        sap_set_update_mode(self.h, mode)
+
+    def set_split(self, split):
+        if isinstance(split, str):
+            split = {"fp16": SPLIT_FP16, "bf16": SPLIT_BF16}[split]
+        sap_set_split(self.h, split)
+
+    def set_min_secant_length(self, eps):
+        sap_set_min_secant_length(self.h, eps)
+
+    def set_basis(self, U):
+        sap_set_basis(self.h, U)
+        self.k = int(U.shape[0])
+
+    def get_basis(self, out=None):
+        return sap_get_basis(self.h, self.k, self.n, out)
+
+    def min_secant(self):
+        return sap_min_secant(self.h)
+
+    def step(self, alpha, sync=True):
+        return sap_step(self.h, alpha, sync)
+
+    def run(self, alpha, iters, history=True):
+        return sap_run(self.h, alpha, iters, history)
+
+    def get_history(self, count):
+        return sap_get_history(self.h, count)
+
+    def estimate_dim(self, U0, iters, alpha, threshold):
+        return sap_estimate_dim(self.h, U0, iters, alpha, threshold)
+
+    def project(self, out=None):
+        if out is None:
+            out = np.empty((self.N, self.k), dtype=np.float32)
+        return sap_project(self.h, out)
+
+    def stats(self):
+        return sap_get_stats(self.h)
+
+    def set_profiling(self, enable):
+        sap_set_profiling(self.h, enable)
+
+    def kernel_time(self, kernel_class):
+        return sap_get_kernel_time(self.h, kernel_class)

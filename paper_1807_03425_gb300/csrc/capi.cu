@@ -1,0 +1,816 @@
+// capi.cu -- the C ABI of libsap (declared in include/sap.h) and the engine
+// behind it: device buffers of a handle, the launch sequence of one SAP
+// iteration, CUDA-graph capture of the iteration loop, and kernel timing.
+//
+// One iteration (Algorithm 1 of Kvinge et al., arXiv:1807.03425):
+//   plain form:         plain pass -> FP64 recheck -> update
+//   restructured form:  Y = X U (tensor cores) -> restructured pass ->
+//                       explicit-difference recheck -> FP64 recheck -> update
+// Nothing returns to the host inside the loop; sap_run replays captured
+// graphs of `chunk` iterations.
+#include "sap_internal.cuh"
+#include "restructured.cuh"
+#include "../../include/sap.h"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace sap;
+
+namespace {
+
+constexpr int kClasses = 6;
+enum KClass { K_GEMM = 0, K_RESTR = 1, K_PLAIN = 2, K_EXPL = 3, K_FP64 = 4, K_UPDATE = 5 };
+
+struct GraphEntry {
+    cudaGraphExec_t exec;
+    double alpha;
+    int eval_only;
+    int chunk;
+};
+
+double gamma_u(double m, double u) { return m * u / (1.0 - m * u); }
+
+} // namespace
+
+struct sap_ctx {
+    int device = 0;
+    int sms = 148;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    bool sticky = false;
+
+    int64_t N = 0;
+    int n = 0;
+    sap_dtype dt = SAP_F32;
+    float *X32 = nullptr;
+    double *X64 = nullptr;
+
+    int k = 0, KP = 0;
+    double *U64 = nullptr;
+    float *U32 = nullptr;
+
+    int2 *tiles = nullptr;   // plain-form point blocks
+    int ntiles = 0;
+    int2 *cand1 = nullptr, *cand2 = nullptr;
+    long long cap = 0;
+    Partial *partials = nullptr;
+    double *work = nullptr;
+    size_t work_elems = 0;
+    ProbState *st = nullptr;
+    double *hist = nullptr;
+    int2 *am = nullptr;
+    int hist_cap = 0;
+    int last_iters = -1;
+
+    sap_path path = SAP_PLAIN;
+    sap_update_mode mode = SAP_UPDATE_LITERAL;
+    sap_split split = SAP_SPLIT_FP16;
+    double eps = 0.0;
+    double eps2_f64 = 0.0;
+    float eps2_lo = 0.f, eps2_hi = 0.f;
+    int64_t n_excluded = 0;
+
+    RestrState rs;           // restructured-form buffers (restructured.cuh)
+
+    long long launches = 0;
+    std::vector<GraphEntry> graphs;
+
+    bool profiling = false;
+    double ktime[kClasses] = {};
+    long long kcount[kClasses] = {};
+    struct Pending { int cls; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+sap_status fail(sap_handle h, sap_status s, const std::string &msg)
+{
+    if (h) {
+        h->err = msg;
+        if (s == SAP_E_CUDA) h->sticky = true;
+    }
+    return s;
+}
+
+#define CK(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? SAP_E_OOM : SAP_E_CUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+#define CHECK_HANDLE(h)                                                            \
+    do {                                                                           \
+        if (!(h)) return SAP_E_ARG;                                                \
+        if ((h)->sticky) return fail(h, SAP_E_CUDA, "handle has a sticky CUDA error: " + (h)->err); \
+        (h)->err.clear();                                                          \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+template <typename T>
+void dfree(T *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void drop_graphs(sap_handle h)
+{
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
+cudaEvent_t get_event(sap_handle h)
+{
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Certified error models (see sap_internal.cuh and plain.cu).
+Cert cert_plain_f32(int n, int k)
+{
+    const double u = std::ldexp(1.0, -24);
+    Cert c;
+    c.A = (float)(std::sqrt((double)k) * gamma_u(n + 3, u) * 1.05);
+    c.rho = (float)((gamma_u(n + 2, u) + gamma_u(k, u) + 3 * u) * 1.05);
+    return c;
+}
+
+Cert cert_plain_f64()
+{
+    Cert c;
+    c.A = 1e-12f;
+    c.rho = (float)(std::ldexp(1.0, -23) * 1.05);
+    return c;
+}
+
+sap_status sync_and_status(sap_handle h)
+{
+    CK(cudaStreamSynchronize(h->stream));
+    int status = 0;
+    CK(cudaMemcpy(&status, &h->st->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) {
+        CK(cudaMemset(&h->st->status, 0, sizeof(int)));
+        if (status & ST_NO_SECANT) return fail(h, SAP_E_NO_SECANT, "every pair is excluded");
+        if (status & ST_TIMEOUT) return fail(h, SAP_E_TIMEOUT, "a device-side wait gave up");
+        if (status & ST_OVERFLOW)
+            return fail(h, SAP_E_UNSUPPORTED, "candidate list overflow (too many near-ties)");
+    }
+    return SAP_OK;
+}
+
+// Launch bracket for kernel timing in profiling mode.
+struct Timed {
+    sap_handle h;
+    int cls;
+    cudaEvent_t a = nullptr, b = nullptr;
+    Timed(sap_handle hh, int c) : h(hh), cls(c)
+    {
+        if (h->profiling) {
+            a = get_event(h);
+            b = get_event(h);
+            cudaEventRecord(a, h->stream);
+        }
+        h->launches++;
+    }
+    ~Timed()
+    {
+        if (h->profiling) {
+            cudaEventRecord(b, h->stream);
+            h->pending.push_back({cls, a, b});
+        }
+    }
+};
+
+sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only)
+{
+    cudaStream_t s = h->stream;
+    const Cert c32 = cert_plain_f32(h->n, h->k);
+    const bool f64 = h->dt == SAP_F64;
+    int which = 1;
+    const int2 *list = h->cand1;
+    if (h->path == SAP_PLAIN) {
+        if (f64) {
+            PlainArgsF64 a;
+            a.X = h->X64; a.N = (int)h->N; a.n = h->n; a.U64 = h->U64; a.k = h->k;
+            a.tiles = h->tiles; a.ntiles = h->ntiles;
+            a.grid = std::min(h->ntiles, 4 * h->sms);
+            a.eps2 = h->eps2_f64; a.cert = cert_plain_f64(); a.st = h->st;
+            a.cand = h->cand1; a.cand_cap = h->cap;
+            Timed t(h, K_PLAIN);
+            CK(launch_plain_f64(a, s));
+        } else {
+            PlainArgsF32 a;
+            a.X = h->X32; a.N = (int)h->N; a.n = h->n; a.U32 = h->U32; a.k = h->k; a.KP = h->KP;
+            a.tiles = h->tiles; a.ntiles = h->ntiles;
+            a.grid = std::min(h->ntiles, 2 * h->sms);
+            a.eps2_lo = h->eps2_lo; a.eps2_hi = h->eps2_hi; a.cert = c32; a.st = h->st;
+            a.cand = h->cand1; a.cand_cap = h->cap;
+            Timed t(h, K_PLAIN);
+            CK(launch_plain_f32(a, s));
+        }
+    } else {
+        sap_status st = restructured_enqueue(h, alpha);
+        if (st != SAP_OK) return st;
+        which = 2;
+        list = h->cand2;
+    }
+    {
+        RecheckArgs r;
+        r.X = f64 ? (const void *)h->X64 : (const void *)h->X32;
+        r.x_is_f64 = f64; r.N = (int)h->N; r.n = h->n; r.U64 = h->U64; r.k = h->k;
+        r.eps2 = h->eps2_f64; r.list = list; r.cap = (unsigned int)h->cap; r.which = which;
+        r.st = h->st; r.partials = h->partials;
+        Timed t(h, K_FP64);
+        CK(launch_recheck_fp64(r, s));
+    }
+    {
+        UpdateArgs u;
+        u.partials = h->partials; u.nparts = kRecheckBlocks;
+        u.X = f64 ? (const void *)h->X64 : (const void *)h->X32;
+        u.x_is_f64 = f64; u.N = (int)h->N; u.n = h->n;
+        u.U64 = h->U64; u.U32 = h->U32; u.KP = h->KP;
+        u.Uhi = h->rs.Uhi; u.Ulo = h->rs.Ulo; u.KPG = h->rs.KPG; u.NP = h->rs.NP;
+        u.split_bf16 = h->split == SAP_SPLIT_BF16; u.split_scale = h->split == SAP_SPLIT_BF16 ? 256.f : 2048.f;
+        u.k = h->k; u.alpha = alpha; u.mode = (int)h->mode; u.eval_only = eval_only;
+        u.work = h->work; u.st = h->st; u.hist = h->hist; u.argmin = h->am; u.seed_cert = c32;
+        Timed t(h, K_UPDATE);
+        CK(launch_update(u, s));
+    }
+    return SAP_OK;
+}
+
+sap_status reset_state(sap_handle h)
+{
+    ProbState p;
+    std::memset(&p, 0, sizeof(p));
+    p.seed_ub = 0x7f800000u;
+    p.run_ub1 = 0x7f800000u;
+    p.run_ub2 = 0x7f800000u;
+    p.hist_cap = h->hist_cap;
+    p.last_r = INFINITY;
+    p.last_i = p.last_j = -1;
+    CK(cudaMemcpyAsync(h->st, &p, sizeof(p), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return SAP_OK;
+}
+
+sap_status ensure_hist(sap_handle h, int need)
+{
+    if (h->hist_cap >= need) return SAP_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    dfree(h->hist);
+    dfree(h->am);
+    int cap = std::max(need, 1024);
+    CK(dalloc(&h->hist, cap));
+    CK(dalloc(&h->am, cap));
+    h->hist_cap = cap;
+    CK(cudaMemcpy(&h->st->hist_cap, &cap, sizeof(int), cudaMemcpyHostToDevice));
+    return SAP_OK;
+}
+
+sap_status set_eps(sap_handle h, double eps)
+{
+    h->eps = eps;
+    h->eps2_f64 = eps * eps;
+    if (eps > 0.0) {
+        const double m = 4.0 * gamma_u(h->n + 2, std::ldexp(1.0, -24)) + 1e-6;
+        h->eps2_lo = std::nextafter((float)(h->eps2_f64 * (1.0 - m)), 0.f);
+        h->eps2_hi = std::nextafter((float)(h->eps2_f64 * (1.0 + m)), INFINITY);
+    } else {
+        h->eps2_lo = h->eps2_hi = 0.f;
+    }
+    return SAP_OK;
+}
+
+__global__ void bf16_to_f32_kernel(const uint16_t *in, float *out, size_t count)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __uint_as_float(((unsigned int)in[i]) << 16);
+}
+
+sap_status build_tiles(sap_handle h, int edge)
+{
+    const int nb = (int)((h->N + edge - 1) / edge);
+    std::vector<int2> t;
+    t.reserve((size_t)nb * (nb + 1) / 2);
+    for (int I = 0; I < nb; ++I)
+        for (int J = I; J < nb; ++J) t.push_back(make_int2(I, J));
+    dfree(h->tiles);
+    CK(dalloc(&h->tiles, t.size()));
+    CK(cudaMemcpy(h->tiles, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    h->ntiles = (int)t.size();
+    return SAP_OK;
+}
+
+} // namespace
+
+// Accessors used by restructured.cu (kept here so the handle layout stays
+// private to this file).
+namespace sap {
+RestrState &restr_state(sap_handle h) { return h->rs; }
+cudaStream_t handle_stream(sap_handle h) { return h->stream; }
+int handle_sms(sap_handle h) { return h->sms; }
+ProbState *handle_state(sap_handle h) { return h->st; }
+const float *handle_x32(sap_handle h) { return h->X32; }
+const float *handle_u32(sap_handle h) { return h->U32; }
+int2 *handle_cand1(sap_handle h) { return h->cand1; }
+int2 *handle_cand2(sap_handle h) { return h->cand2; }
+long long handle_cap(sap_handle h) { return h->cap; }
+int handle_k(sap_handle h) { return h->k; }
+int handle_kp(sap_handle h) { return h->KP; }
+int64_t handle_n_points(sap_handle h) { return h->N; }
+int handle_n_dim(sap_handle h) { return h->n; }
+int handle_split_bf16(sap_handle h) { return h->split == SAP_SPLIT_BF16; }
+double handle_eps2(sap_handle h) { return h->eps2_f64; }
+float handle_eps2_lo(sap_handle h) { return h->eps2_lo; }
+float handle_eps2_hi(sap_handle h) { return h->eps2_hi; }
+void handle_count_launch(sap_handle h, int cls, cudaEvent_t *a, cudaEvent_t *b)
+{
+    h->launches++;
+    if (h->profiling) {
+        *a = get_event(h);
+        *b = get_event(h);
+    } else {
+        *a = *b = nullptr;
+    }
+    (void)cls;
+}
+void handle_push_timing(sap_handle h, int cls, cudaEvent_t a, cudaEvent_t b)
+{
+    if (a) h->pending.push_back({cls, a, b});
+}
+sap_status handle_fail(sap_handle h, sap_status s, const char *msg) { return fail(h, s, msg); }
+} // namespace sap
+
+extern "C" {
+
+const char *sap_version(void) { return "libsap 0.1 (sm_103a)"; }
+
+const char *sap_status_str(sap_status s)
+{
+    switch (s) {
+    case SAP_OK: return "SAP_OK";
+    case SAP_E_ARG: return "SAP_E_ARG";
+    case SAP_E_STATE: return "SAP_E_STATE";
+    case SAP_E_NOT_ORTHONORMAL: return "SAP_E_NOT_ORTHONORMAL";
+    case SAP_E_NO_SECANT: return "SAP_E_NO_SECANT";
+    case SAP_E_OOM: return "SAP_E_OOM";
+    case SAP_E_CUDA: return "SAP_E_CUDA";
+    case SAP_E_TIMEOUT: return "SAP_E_TIMEOUT";
+    case SAP_E_NO_DEVICE: return "SAP_E_NO_DEVICE";
+    case SAP_E_UNSUPPORTED: return "SAP_E_UNSUPPORTED";
+    }
+    return "SAP_E_UNKNOWN";
+}
+
+const char *sap_last_error(sap_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+sap_status sap_destroy(sap_handle h)
+{
+    if (!h) return SAP_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    for (auto &p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : h->event_pool) cudaEventDestroy(e);
+    restructured_free(h);
+    dfree(h->X32); dfree(h->X64); dfree(h->U64); dfree(h->U32);
+    dfree(h->tiles); dfree(h->cand1); dfree(h->cand2); dfree(h->partials);
+    dfree(h->work); dfree(h->st); dfree(h->hist); dfree(h->am);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return SAP_OK;
+}
+
+sap_status sap_create(const void *X, int64_t N, int32_t n, sap_dtype dt, int x_is_device,
+                      sap_handle *out)
+{
+    if (!out) return SAP_E_ARG;
+    *out = nullptr;
+    if (!X || N < 2 || N > 92681 || n < 1 || n > 16384) return SAP_E_ARG;
+    if (dt != SAP_F32 && dt != SAP_BF16 && dt != SAP_F64) return SAP_E_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return SAP_E_NO_DEVICE;
+    }
+    sap_handle h = new sap_ctx();
+    h->N = N; h->n = n; h->dt = dt;
+    CK(cudaGetDevice(&h->device));
+    CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
+    if (x_is_device) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, X) != cudaSuccess || pa.type != cudaMemoryTypeDevice ||
+            pa.device != h->device) {
+            cudaGetLastError();
+            delete h;
+            return SAP_E_ARG;
+        }
+    }
+    auto cleanup_fail = [&](sap_status s) { sap_destroy(h); return s; };
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+        return cleanup_fail(SAP_E_CUDA);
+    h->own_stream = true;
+
+    const size_t cnt = (size_t)N * n;
+    sap_status st = SAP_OK;
+    auto chk = [&](cudaError_t e) {
+        if (e != cudaSuccess && st == SAP_OK)
+            st = e == cudaErrorMemoryAllocation ? SAP_E_OOM : SAP_E_CUDA;
+    };
+    const cudaMemcpyKind kind = x_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (dt == SAP_F64) {
+        chk(dalloc(&h->X64, cnt));
+        if (st == SAP_OK) chk(cudaMemcpy(h->X64, X, cnt * sizeof(double), kind));
+        h->path = SAP_PLAIN;
+    } else {
+        chk(dalloc(&h->X32, cnt));
+        if (st == SAP_OK && dt == SAP_F32) chk(cudaMemcpy(h->X32, X, cnt * sizeof(float), kind));
+        if (st == SAP_OK && dt == SAP_BF16) {
+            uint16_t *tmp = nullptr;
+            chk(dalloc(&tmp, cnt));
+            if (st == SAP_OK) chk(cudaMemcpy(tmp, X, cnt * sizeof(uint16_t), kind));
+            if (st == SAP_OK) {
+                bf16_to_f32_kernel<<<4 * h->sms, 256, 0, h->stream>>>(tmp, h->X32, cnt);
+                chk(cudaGetLastError());
+                chk(cudaStreamSynchronize(h->stream));
+            }
+            dfree(tmp);
+        }
+        h->path = SAP_RESTRUCTURED;
+    }
+    const long long P = (long long)N * (N - 1) / 2;
+    h->cap = std::min<long long>(P + 64, 1ll << 26);
+    chk(dalloc(&h->cand1, (size_t)h->cap));
+    chk(dalloc(&h->partials, kRecheckBlocks));
+    chk(dalloc(&h->st, 1));
+    if (st != SAP_OK) return cleanup_fail(st);
+    if (ensure_hist(h, 1024) != SAP_OK) return cleanup_fail(SAP_E_CUDA);
+    if (build_tiles(h, dt == SAP_F64 ? 16 : 64) != SAP_OK) return cleanup_fail(SAP_E_CUDA);
+    set_eps(h, 0.0);
+    if (dt != SAP_F64) {
+        chk(dalloc(&h->cand2, (size_t)h->cap));
+        if (st != SAP_OK) return cleanup_fail(st);
+        sap_status rs = restructured_prepare(h);
+        if (rs != SAP_OK) return cleanup_fail(rs);
+    }
+    if (reset_state(h) != SAP_OK) return cleanup_fail(SAP_E_CUDA);
+    *out = h;
+    return SAP_OK;
+}
+
+sap_status sap_set_stream(sap_handle h, void *cuda_stream)
+{
+    CHECK_HANDLE(h);
+    CK(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+        h->own_stream = false;
+    } else {
+        CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    return SAP_OK;
+}
+
+sap_status sap_set_path(sap_handle h, sap_path p)
+{
+    CHECK_HANDLE(h);
+    if (p != SAP_PLAIN && p != SAP_RESTRUCTURED) return fail(h, SAP_E_ARG, "unknown path");
+    if (p == SAP_RESTRUCTURED && h->dt == SAP_F64)
+        return fail(h, SAP_E_UNSUPPORTED, "the restructured form needs FP32 or BF16 data");
+    if (p == SAP_PLAIN && h->dt != SAP_F64 && h->k > 8)
+        return fail(h, SAP_E_UNSUPPORTED, "the FP32 plain form supports k <= 8");
+    if (p != h->path) drop_graphs(h);
+    h->path = p;
+    return SAP_OK;
+}
+
+sap_status sap_set_update_mode(sap_handle h, sap_update_mode m)
+{
+    CHECK_HANDLE(h);
+    if (m != SAP_UPDATE_LITERAL && m != SAP_UPDATE_ANGLE) return fail(h, SAP_E_ARG, "unknown mode");
+    if (m != h->mode) drop_graphs(h);
+    h->mode = m;
+    return SAP_OK;
+}
+
+sap_status sap_set_split(sap_handle h, sap_split s)
+{
+    CHECK_HANDLE(h);
+    if (s != SAP_SPLIT_FP16 && s != SAP_SPLIT_BF16) return fail(h, SAP_E_ARG, "unknown split");
+    if (h->dt == SAP_F64) return fail(h, SAP_E_UNSUPPORTED, "no tensor-core product for FP64 data");
+    if (s == h->split) return SAP_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    h->split = s;
+    sap_status st = restructured_prepare(h);
+    if (st != SAP_OK || h->k == 0) return st;
+    // re-split the current basis for the new operand type
+    std::vector<double> Uh((size_t)h->n * h->k);
+    CK(cudaMemcpy(Uh.data(), h->U64, Uh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    return restructured_upload_basis(h, Uh.data());
+}
+
+sap_status sap_set_min_secant_length(sap_handle h, double eps)
+{
+    CHECK_HANDLE(h);
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(h, SAP_E_ARG, "eps must be finite and >= 0");
+    CK(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    set_eps(h, eps);
+    if (h->dt != SAP_F64) {
+        sap_status s = restructured_prepare(h);
+        if (s != SAP_OK) return s;
+    }
+    return reset_state(h);
+}
+
+sap_status sap_set_basis(sap_handle h, const double *U, int32_t k, int u_is_device)
+{
+    CHECK_HANDLE(h);
+    if (!U || k < 1 || k > kMaxK || k > h->n) return fail(h, SAP_E_ARG, "need 1 <= k <= min(n, 32)");
+    if (h->path == SAP_PLAIN && h->dt != SAP_F64 && k > 8)
+        return fail(h, SAP_E_UNSUPPORTED, "the FP32 plain form supports k <= 8");
+    const int n = h->n;
+    std::vector<double> Uh((size_t)n * k);
+    if (u_is_device) {
+        CK(cudaMemcpy(Uh.data(), U, Uh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(Uh.data(), U, Uh.size() * sizeof(double));
+    }
+    double dev = 0.0;
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) {
+            double s = 0.0;
+            for (int l = 0; l < n; ++l) s += Uh[(size_t)a * n + l] * Uh[(size_t)b * n + l];
+            dev = std::max(dev, std::fabs(s - (a == b ? 1.0 : 0.0)));
+        }
+    if (!(dev <= 1e-10)) return fail(h, SAP_E_NOT_ORTHONORMAL, "max |U^T U - I| > 1e-10");
+    CK(cudaStreamSynchronize(h->stream));
+    if (k != h->k) {
+        drop_graphs(h);
+        dfree(h->U64); dfree(h->U32); dfree(h->work);
+        h->k = k;
+        h->KP = (k + 3) & ~3;
+        CK(dalloc(&h->U64, (size_t)n * k));
+        CK(dalloc(&h->U32, (size_t)n * h->KP));
+        h->work_elems = (size_t)(k + 2) * n;
+        CK(dalloc(&h->work, h->work_elems));
+        if (h->dt != SAP_F64) {
+            sap_status s = restructured_basis_alloc(h);
+            if (s != SAP_OK) return s;
+        }
+    }
+    CK(cudaMemcpy(h->U64, Uh.data(), Uh.size() * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<float> u32((size_t)n * h->KP, 0.f);
+    for (int l = 0; l < n; ++l)
+        for (int c = 0; c < k; ++c) u32[(size_t)l * h->KP + c] = (float)Uh[(size_t)c * n + l];
+    CK(cudaMemcpy(h->U32, u32.data(), u32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (h->dt != SAP_F64) {
+        sap_status s = restructured_upload_basis(h, Uh.data());
+        if (s != SAP_OK) return s;
+    }
+    return reset_state(h);
+}
+
+sap_status sap_get_basis(sap_handle h, double *U_out, int out_is_device)
+{
+    CHECK_HANDLE(h);
+    if (!U_out) return fail(h, SAP_E_ARG, "null output");
+    if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
+    CK(cudaMemcpyAsync(U_out, h->U64, (size_t)h->n * h->k * sizeof(double),
+                       out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return SAP_OK;
+}
+
+static sap_status read_last(sap_handle h, int64_t *i, int64_t *j, double *ratio)
+{
+    sap_status s = sync_and_status(h);
+    if (s != SAP_OK) return s;
+    ProbState p;
+    CK(cudaMemcpy(&p, h->st, sizeof(p), cudaMemcpyDeviceToHost));
+    if (i) *i = p.last_i;
+    if (j) *j = p.last_j;
+    if (ratio) *ratio = p.last_r;
+    return SAP_OK;
+}
+
+sap_status sap_min_secant(sap_handle h, int64_t *i, int64_t *j, double *ratio)
+{
+    CHECK_HANDLE(h);
+    if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
+    sap_status s = enqueue_iteration(h, 0.0, 1);
+    if (s != SAP_OK) return s;
+    return read_last(h, i, j, ratio);
+}
+
+sap_status sap_step(sap_handle h, double alpha, int64_t *i, int64_t *j, double *ratio)
+{
+    CHECK_HANDLE(h);
+    if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(h, SAP_E_ARG, "alpha must be in [0, 1]");
+    sap_status s = enqueue_iteration(h, alpha, 0);
+    if (s != SAP_OK) return s;
+    if (i || j || ratio) return read_last(h, i, j, ratio);
+    return SAP_OK;
+}
+
+static sap_status graph_for(sap_handle h, double alpha, int eval_only, int chunk, cudaGraphExec_t *out)
+{
+    for (auto &g : h->graphs)
+        if (g.alpha == alpha && g.eval_only == eval_only && g.chunk == chunk) {
+            *out = g.exec;
+            return SAP_OK;
+        }
+    cudaGraph_t graph = nullptr;
+    const long long before = h->launches;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    sap_status s = SAP_OK;
+    for (int c = 0; c < chunk && s == SAP_OK; ++c) s = enqueue_iteration(h, alpha, eval_only);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    h->launches = before;  // capture only records; replays are counted
+    if (s != SAP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    CK(e);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    h->graphs.push_back({exec, alpha, eval_only, chunk});
+    *out = exec;
+    return SAP_OK;
+}
+
+static int kernels_per_iteration(sap_handle h)
+{
+    return h->path == SAP_PLAIN ? 3 : restructured_kernels_per_iteration(h) + 2;
+}
+
+sap_status sap_run(sap_handle h, double alpha, int32_t iters, double *hist, int64_t *argmins)
+{
+    CHECK_HANDLE(h);
+    if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
+    if (iters < 0) return fail(h, SAP_E_ARG, "iters must be >= 0");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(h, SAP_E_ARG, "alpha must be in [0, 1]");
+    sap_status s = ensure_hist(h, iters + 1);
+    if (s != SAP_OK) return s;
+    CK(cudaMemsetAsync(&h->st->iter, 0, sizeof(int), h->stream));
+    if (h->profiling) {
+        for (int it = 0; it < iters && s == SAP_OK; ++it) s = enqueue_iteration(h, alpha, 0);
+        if (s == SAP_OK) s = enqueue_iteration(h, alpha, 1);
+        if (s != SAP_OK) return s;
+    } else {
+        const int chunk = std::min(iters, 32);
+        const int kpi = kernels_per_iteration(h);
+        if (chunk > 0) {
+            cudaGraphExec_t g;
+            s = graph_for(h, alpha, 0, chunk, &g);
+            if (s != SAP_OK) return s;
+            for (int r = 0; r < iters / chunk; ++r) {
+                CK(cudaGraphLaunch(g, h->stream));
+                h->launches += (long long)kpi * chunk;
+            }
+            const int rem = iters % chunk;
+            if (rem) {
+                s = graph_for(h, alpha, 0, rem, &g);
+                if (s != SAP_OK) return s;
+                CK(cudaGraphLaunch(g, h->stream));
+                h->launches += (long long)kpi * rem;
+            }
+        }
+        cudaGraphExec_t ge;
+        s = graph_for(h, 0.0, 1, 1, &ge);
+        if (s != SAP_OK) return s;
+        CK(cudaGraphLaunch(ge, h->stream));
+        h->launches += kpi;
+    }
+    h->last_iters = iters;
+    if (hist || argmins) return sap_get_history(h, hist, argmins, iters + 1);
+    return SAP_OK;
+}
+
+sap_status sap_get_history(sap_handle h, double *hist, int64_t *argmins, int32_t capacity)
+{
+    CHECK_HANDLE(h);
+    if (h->last_iters < 0) return fail(h, SAP_E_STATE, "no sap_run yet");
+    const int cnt = std::min(capacity, h->last_iters + 1);
+    if (cnt < 0) return fail(h, SAP_E_ARG, "negative capacity");
+    sap_status s = sync_and_status(h);
+    if (s != SAP_OK) return s;
+    if (hist) CK(cudaMemcpy(hist, h->hist, (size_t)cnt * sizeof(double), cudaMemcpyDeviceToHost));
+    if (argmins) {
+        std::vector<int2> tmp(cnt);
+        CK(cudaMemcpy(tmp.data(), h->am, (size_t)cnt * sizeof(int2), cudaMemcpyDeviceToHost));
+        for (int q = 0; q < cnt; ++q) {
+            argmins[2 * q] = tmp[q].x;
+            argmins[2 * q + 1] = tmp[q].y;
+        }
+    }
+    return SAP_OK;
+}
+
+sap_status sap_project(sap_handle h, float *Y_out, int out_is_device)
+{
+    CHECK_HANDLE(h);
+    if (!Y_out) return fail(h, SAP_E_ARG, "null output");
+    if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
+    if (h->dt == SAP_F64) return fail(h, SAP_E_UNSUPPORTED, "no tensor-core product for FP64 data");
+    sap_status s = restructured_project(h, Y_out, out_is_device);
+    if (s != SAP_OK) return s;
+    return sync_and_status(h);
+}
+
+sap_status sap_get_stats(sap_handle h, sap_stats *out)
+{
+    if (!h || !out) return SAP_E_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->n_points = h->N;
+    out->n_dim = h->n;
+    out->k = h->k;
+    out->n_pairs = h->N * (h->N - 1) / 2;
+    out->kernel_launches = h->launches;
+    restructured_stats(h, out);
+    if (h->sticky) return SAP_E_CUDA;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, SAP_E_CUDA, "sync failed");
+    ProbState p;
+    if (cudaMemcpy(&p, h->st, sizeof(p), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(h, SAP_E_CUDA, "copy failed");
+    out->last_tier1 = p.last_cnt1;
+    out->last_tier2 = p.last_cnt2;
+    return SAP_OK;
+}
+
+sap_status sap_set_profiling(sap_handle h, int enable)
+{
+    CHECK_HANDLE(h);
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto &p : h->pending) {
+        h->event_pool.push_back(p.a);
+        h->event_pool.push_back(p.b);
+    }
+    h->pending.clear();
+    for (int c = 0; c < kClasses; ++c) { h->ktime[c] = 0.0; h->kcount[c] = 0; }
+    h->profiling = enable != 0;
+    return SAP_OK;
+}
+
+sap_status sap_get_kernel_time(sap_handle h, int32_t kernel_class, double *total_ms, int64_t *launches)
+{
+    CHECK_HANDLE(h);
+    if (kernel_class < 0 || kernel_class >= kClasses) return fail(h, SAP_E_ARG, "unknown kernel class");
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto &p : h->pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p.a, p.b));
+        h->ktime[p.cls] += ms;
+        h->kcount[p.cls] += 1;
+        h->event_pool.push_back(p.a);
+        h->event_pool.push_back(p.b);
+    }
+    h->pending.clear();
+    if (total_ms) *total_ms = h->ktime[kernel_class];
+    if (launches) *launches = h->kcount[kernel_class];
+    return SAP_OK;
+}
+
+sap_status sap_estimate_dim(sap_handle h, const double *U0, int32_t k_max, int32_t iters,
+                            double alpha, double threshold, int32_t *k_out, double *ratios_out)
+{
+    CHECK_HANDLE(h);
+    (void)U0; (void)k_max; (void)iters; (void)alpha; (void)threshold; (void)k_out; (void)ratios_out;
+    return fail(h, SAP_E_UNSUPPORTED, "dimension sweep not built yet");
+}
+
+} // extern "C"

@@ -1,0 +1,173 @@
+// gemm_tc.cu -- Y = X U on the 5th-generation tensor cores (tcgen05), the
+// once-per-iteration product of the restructured form: since
+// U^T (x_i - x_j) = y_i - y_j, every projected secant is a difference of two
+// rows of Y.
+//
+// Precision: X (centred and scaled by a power of two) and U are each split
+// into a 16-bit high part and a low part scaled by 2^s (s = 11 for FP16,
+// 8 for BF16).  Two FP32 accumulators in TMEM collect
+//     D1 = Xhi Uhi^T   and   D2 = Xhi Ulo^T + Xlo Uhi^T,
+// and the epilogue forms Y = (D1 + 2^-s D2) / scale.  The dropped term
+// Xlo Ulo^T and the split residuals are below 3 * 2^-2s relative to
+// sum_l |x_l||u_l|; the engine adds the accumulation bound and certifies the
+// all-pairs pass with the total.
+//
+// Kernel shape: one CTA of 128 threads per 128 rows of X.  Warp 0 lane 0
+// issues TMA loads of 64-wide K blocks (128-byte swizzle) into a ring of
+// shared-memory stages; warp 1 lane 0 issues the MMAs (M = 128, N = KPG,
+// K = 16 per instruction) and releases each stage with tcgen05.commit; after
+// the last commit all four warps read their 32 TMEM lanes and write Y.
+#include "sap_internal.cuh"
+#include "tc_ptx.cuh"
+#include "gemm_tc.cuh"
+
+namespace sap {
+namespace {
+
+constexpr int GM = 128;   // rows per CTA (MMA M)
+constexpr int GK = 64;    // K elements per stage (128 bytes of 16-bit)
+constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of clock
+
+__host__ __device__ inline uint32_t tmem_cols_for(int n)
+{
+    uint32_t c = 32;
+    while (c < (uint32_t)n) c <<= 1;
+    return c;
+}
+
+__global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ GemmArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int KPG = a.KPG, S = a.stages;
+    const uint32_t a_bytes = GM * GK * 2;
+    const uint32_t b_bytes = (uint32_t)KPG * GK * 2;
+    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * stage_bytes);
+    uint64_t *empty = full + S;
+    uint64_t *done = empty + S;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    __shared__ int abort_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t ncols = tmem_cols_for(2 * KPG);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(done, 1);
+        abort_sh = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tbase = *tslot;
+    const int m0 = blockIdx.x * GM;
+
+    auto stage_a_hi = [&](int s) { return smem + (size_t)s * stage_bytes; };
+    auto stage_a_lo = [&](int s) { return smem + (size_t)s * stage_bytes + a_bytes; };
+    auto stage_b_hi = [&](int s) { return smem + (size_t)s * stage_bytes + 2 * a_bytes; };
+    auto stage_b_lo = [&](int s) { return smem + (size_t)s * stage_bytes + 2 * a_bytes + b_bytes; };
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int issued = 0;
+        for (int kb = 0; kb < a.nkb; ++kb) {
+            const int s = kb % S;
+            if (kb >= S && !tc::mbar_wait_bounded(&empty[s], ((kb / S) & 1) ^ 1, kWaitBudget)) {
+                atomicExch(&abort_sh, 1);
+                break;
+            }
+            tc::mbar_expect_tx(&full[s], stage_bytes);
+            tc::tma_load_2d(stage_a_hi(s), &a.ta_hi, kb * GK, m0, &full[s]);
+            tc::tma_load_2d(stage_a_lo(s), &a.ta_lo, kb * GK, m0, &full[s]);
+            tc::tma_load_2d(stage_b_hi(s), &a.tb_hi, kb * GK, 0, &full[s]);
+            tc::tma_load_2d(stage_b_lo(s), &a.tb_lo, kb * GK, 0, &full[s]);
+            ++issued;
+        }
+        // make sure no copy of ours is still in flight before the CTA exits
+        for (int kb = issued > S ? issued - S : 0; kb < issued; ++kb)
+            tc::mbar_wait_bounded(&full[kb % S], (kb / S) & 1, kWaitBudget);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = tc::idesc_f16(GM, KPG, a.ab_bf16);
+        for (int kb = 0; kb < a.nkb; ++kb) {
+            const int s = kb % S;
+            if (!tc::mbar_wait_bounded(&full[s], (kb / S) & 1, kWaitBudget)) {
+                atomicExch(&abort_sh, 1);
+                break;
+            }
+            tc::tc_fence_after();
+            const uint32_t ah = tc::smem_u32(stage_a_hi(s)), al = tc::smem_u32(stage_a_lo(s));
+            const uint32_t bh = tc::smem_u32(stage_b_hi(s)), bl = tc::smem_u32(stage_b_lo(s));
+#pragma unroll
+            for (int kk = 0; kk < GK / 16; ++kk) {
+                const uint32_t off = kk * 32;
+                const uint32_t acc = (kb | kk) != 0;
+                tc::mma_f16(tbase, tc::desc_k_sw128(ah + off), tc::desc_k_sw128(bh + off), idesc, acc);
+                tc::mma_f16(tbase + KPG, tc::desc_k_sw128(ah + off), tc::desc_k_sw128(bl + off), idesc, acc);
+                tc::mma_f16(tbase + KPG, tc::desc_k_sw128(al + off), tc::desc_k_sw128(bh + off), idesc, 1u);
+            }
+            tc::mma_commit(&empty[s]);
+        }
+        tc::mma_commit(done);
+    }
+    __syncwarp();
+
+    const bool ok = tc::mbar_wait_bounded(done, 0, kWaitBudget);
+    tc::tc_fence_after();
+    // the TMEM loads below are warp-collective: decide for the whole block
+    const int good = __syncthreads_and(ok ? 1 : 0) && !abort_sh;
+    if (good) {
+        const int row = m0 + warp * 32 + lane;
+        const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < a.KY; c0 += 8) {
+            float d1[8], d2[8];
+            tc::tmem_ld8(lane_base + c0, d1);
+            tc::tmem_ld8(lane_base + KPG + c0, d2);
+            if (row < a.Npad) {
+                float *yr = a.Y + (size_t)row * a.KY;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (c0 + q < a.KY) yr[c0 + q] = fmaf(d2[q], a.lo_scale, d1[q]) * a.out_scale;
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicOr(&a.st->status, ST_TIMEOUT);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, ncols);
+}
+
+} // namespace
+
+size_t gemm_smem_bytes(int KPG, int stages)
+{
+    const size_t stage = 2 * (size_t)GM * GK * 2 + 2 * (size_t)KPG * GK * 2;
+    return 1024 + stages * stage + (2 * stages + 1) * 8 + 16;
+}
+
+int gemm_pick_stages(int KPG, int nkb)
+{
+    int s = 4;
+    while (s > 1 && gemm_smem_bytes(KPG, s) > 200 * 1024) --s;
+    return s < nkb ? s : (nkb > 0 ? nkb : 1);
+}
+
+cudaError_t gemm_configure()
+{
+    return cudaFuncSetAttribute(gemm_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+}
+
+cudaError_t launch_gemm_y(const GemmArgs &a, cudaStream_t s)
+{
+    const size_t shm = gemm_smem_bytes(a.KPG, a.stages);
+    gemm_y_kernel<<<a.Npad / GM, 128, shm, s>>>(a);
+    return cudaGetLastError();
+}
+
+} // namespace sap

@@ -1,0 +1,29 @@
+// gemm_tc.cuh -- launcher interface of the tensor-core product Y = X U.
+#pragma once
+
+#include <cuda.h>
+#include "sap_internal.cuh"
+
+namespace sap {
+
+struct GemmArgs {
+    CUtensorMap ta_hi, ta_lo;   // X split parts: Npad x NP, 16-bit, box 64 x 128
+    CUtensorMap tb_hi, tb_lo;   // U split parts: KPG x NP, 16-bit, box 64 x KPG
+    float *Y;                   // Npad x KY, FP32
+    int KY;                     // columns of Y written (multiple of 4, <= KPG)
+    int Npad;                   // rows (multiple of 128)
+    int nkb;                    // K blocks of 64
+    int KPG;                    // MMA N: multiple of 16, 16..256
+    int ab_bf16;                // operand type: 1 BF16, 0 FP16
+    int stages;                 // shared-memory ring depth
+    float lo_scale;             // 2^-s: weight of the low-part accumulator
+    float out_scale;            // 1/scale of X
+    ProbState *st;              // receives ST_TIMEOUT if a wait gives up
+};
+
+size_t gemm_smem_bytes(int KPG, int stages);
+int gemm_pick_stages(int KPG, int nkb);
+cudaError_t gemm_configure();
+cudaError_t launch_gemm_y(const GemmArgs &a, cudaStream_t s);
+
+} // namespace sap

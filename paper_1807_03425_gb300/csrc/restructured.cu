@@ -1,0 +1,850 @@
+// restructured.cu -- the restructured form of the SAP argmin step.
+//
+// For a basis U and Y = X U, U^T (x_i - x_j) = y_i - y_j, so
+//     r_ij^2 = ||y_i - y_j||^2 * w_ij,   w_ij = 1 / ||x_i - x_j||^2.
+// The lengths are computed once per dataset (and threshold eps, Sec. VII)
+// from explicit FP32 differences; each iteration then costs one tensor-core
+// product and one pass over the stored w (4 bytes per pair).
+//
+// Precision.  The rows of Y carry absolute errors of order eps_Y ||x - mean||
+// (split-operand product, FP32 accumulation), so y_i - y_j cancels for close
+// pairs.  Per pair the pass's error is bounded by
+//     beta_ij = sqrt(k) eps_Y (nu_i + nu_j) / d_ij  (+ a relative FP32 term),
+// with nu_i = ||x_i - mean||.  Pairs with beta_ij above a cap are "near": the
+// pass skips them (w = NaN) and every iteration re-evaluates them from
+// explicit differences instead.  All other pairs are certified to within the
+// cap, so the pass emits every pair that can still be the argmin (selection
+// scheme of sap_internal.cuh); the explicit-difference tier narrows the list
+// and the FP64 tier decides.
+//
+// Layout.  w is stored tile-major over the upper triangle: tile t = (I, J),
+// I <= J, holds the 128 x 128 pairs (I*128 + a, J*128 + b) row-major at
+// w + t*128*128; entries with i >= j, with an index beyond N, excluded pairs
+// and near pairs hold NaN.
+#include "restructured.cuh"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace sap {
+namespace {
+
+constexpr int T = kTile;       // 128
+constexpr int WLC = 16;        // coordinates per chunk in the length prep
+
+// ------------------------------------------------------------------ prep ---
+
+__global__ void colmean_kernel(const float *X, int N, int n, float *center)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) acc += (double)X[(size_t)i * n + l];
+    center[l] = (float)(acc / N);
+}
+
+__global__ void absmax_kernel(const float *X, size_t count, int n, const float *center,
+                              unsigned int *out)
+{
+    float m = 0.f;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < count;
+         idx += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(X[idx] - center[idx % n]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+template <typename H>
+__device__ __forceinline__ H to16(float v);
+template <>
+__device__ __forceinline__ __half to16<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ float from16(__half v) { return __half2float(v); }
+__device__ __forceinline__ float from16(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// hi = 16-bit(xs), lo = 16-bit((xs - hi) * lo_mul), xs = (x - mean) * scale;
+// zero outside N x n.  The difference xs - hi is exact in FP32 and the
+// scalings are powers of two.
+template <typename H>
+__global__ void split_kernel(const float *X, int N, int n, const float *center, float scale,
+                             float lo_mul, H *hi, H *lo, int Npad, int NP)
+{
+    const size_t count = (size_t)Npad * NP;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < count;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / NP), l = (int)(idx % NP);
+        const float x = (r < N && l < n) ? X[(size_t)r * n + l] - center[l] : 0.f;
+        const float xs = x * scale;
+        const H h = to16<H>(xs);
+        hi[idx] = h;
+        lo[idx] = to16<H>((xs - from16(h)) * lo_mul);
+    }
+}
+
+// nu_i = ||fl(x_i - mean)||_2, rounded up (one warp per row; 0 for pad rows).
+__global__ void rownorm_kernel(const float *X, int N, int n, const float *center, float *nu, int Npad)
+{
+    const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= Npad) return;
+    double acc = 0.0;
+    if (row < N)
+        for (int l = lane; l < n; l += 32) {
+            const double v = (double)(X[(size_t)row * n + l] - center[l]);
+            acc = fma(v, v, acc);
+        }
+    acc = warp_sum(acc);
+    if (lane == 0) nu[row] = row < N ? __double2float_ru(sqrt(acc)) * (1.0f + 1e-6f) : 0.f;
+}
+
+struct WPrepArgs {
+    const float *X;
+    int N, n;
+    const float *nu;
+    const int2 *wtiles;
+    float *w;
+    float eps2_lo, eps2_hi;  // FP32 window around eps^2 (0,0: no threshold)
+    double eps2;
+    float beta_coef;         // sqrt(k) * eps_Y, rounded up
+    float b_cap;
+    int2 *near;
+    unsigned int near_cap;
+    unsigned int *counters;  // [0] near count, [1] excluded count (low), [2] status
+};
+
+// Exact decision in FP64 for pairs too close to call in FP32.
+__device__ bool excluded_fp64(const float *X, int n, int i, int j, double eps2)
+{
+    double d2 = 0.0;
+    for (int l = 0; l < n; ++l) {
+        const double D = (double)X[(size_t)i * n + l] - (double)X[(size_t)j * n + l];
+        d2 = fma(D, D, d2);
+    }
+    return d2 == 0.0 || d2 < eps2;
+}
+
+// One 128 x 128 tile of lengths per block: 256 threads, 8 x 8 pairs each.
+__global__ void __launch_bounds__(256) wprep_kernel(WPrepArgs a)
+{
+    __shared__ __align__(16) float xsI[WLC][T + 4];
+    __shared__ __align__(16) float xsJ[WLC][T + 4];
+    __shared__ int scan[33];
+    __shared__ int base_sh;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int2 IJ = a.wtiles[blockIdx.x];
+    const int i0 = IJ.x * T, j0 = IJ.y * T;
+    float d2[8][8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) d2[p][q] = 0.f;
+    for (int l0 = 0; l0 < a.n; l0 += WLC) {
+        __syncthreads();
+        for (int idx = tid; idx < T * WLC; idx += 256) {
+            const int r = idx / WLC, l = idx % WLC, gl = l0 + l;
+            xsI[l][r] = (i0 + r < a.N && gl < a.n) ? a.X[(size_t)(i0 + r) * a.n + gl] : 0.f;
+            xsJ[l][r] = (j0 + r < a.N && gl < a.n) ? a.X[(size_t)(j0 + r) * a.n + gl] : 0.f;
+        }
+        __syncthreads();
+        const int lc = min(WLC, a.n - l0);
+        for (int l = 0; l < lc; ++l) {
+            const float4 i4a = *reinterpret_cast<const float4 *>(&xsI[l][ty * 8]);
+            const float4 i4b = *reinterpret_cast<const float4 *>(&xsI[l][ty * 8 + 4]);
+            const float4 j4a = *reinterpret_cast<const float4 *>(&xsJ[l][tx * 8]);
+            const float4 j4b = *reinterpret_cast<const float4 *>(&xsJ[l][tx * 8 + 4]);
+            const float xi[8] = {i4a.x, i4a.y, i4a.z, i4a.w, i4b.x, i4b.y, i4b.z, i4b.w};
+            const float xj[8] = {j4a.x, j4a.y, j4a.z, j4a.w, j4b.x, j4b.y, j4b.z, j4b.w};
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float D = xi[p] - xj[q];
+                    d2[p][q] = fmaf(D, D, d2[p][q]);
+                }
+        }
+    }
+    const bool epson = a.eps2_hi > 0.f;
+    int nnear = 0, nexcl = 0;
+    unsigned long long near_bits = 0ull;  // bit p*8+q marks a near pair
+    float *wt = a.w + (size_t)blockIdx.x * T * T;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const int i = i0 + ty * 8 + p;
+        float out[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = j0 + tx * 8 + q;
+            const float dd = d2[p][q];
+            float wv = __int_as_float(0x7fc00000);  // NaN: skipped by the pass
+            if (i < j && j < a.N) {
+                int cls;  // 0 excluded, 1 near, 2 stored
+                if (epson && dd < a.eps2_lo) cls = 0;
+                else if ((epson && dd < a.eps2_hi) || dd < 1e-30f)
+                    cls = excluded_fp64(a.X, a.n, i, j, a.eps2) ? 0 : 1;
+                else {
+                    const float inv = 1.0f / dd;
+                    const float beta = a.beta_coef * (a.nu[i] + a.nu[j]) * sqrtf(inv);
+                    if (beta > a.b_cap) cls = 1;
+                    else { cls = 2; wv = inv; }
+                }
+                if (cls == 0) ++nexcl;
+                if (cls == 1) { ++nnear; near_bits |= 1ull << (p * 8 + q); }
+            }
+            out[q] = wv;
+        }
+        float4 *dst = reinterpret_cast<float4 *>(wt + (size_t)(ty * 8 + p) * T + tx * 8);
+        dst[0] = make_float4(out[0], out[1], out[2], out[3]);
+        dst[1] = make_float4(out[4], out[5], out[6], out[7]);
+    }
+    int total;
+    const int off = block_exclusive_scan(nnear, scan, &total);
+    if (tid == 0 && total > 0) base_sh = (int)atomicAdd(&a.counters[0], (unsigned int)total);
+    __syncthreads();
+    if (total > 0) {
+        unsigned int pos = (unsigned int)base_sh + off;
+        for (int b = 0; b < 64; ++b)
+            if (near_bits >> b & 1ull) {
+                if (pos < a.near_cap)
+                    a.near[pos] = make_int2(i0 + ty * 8 + b / 8, j0 + tx * 8 + b % 8);
+                else
+                    atomicOr(&a.counters[2], 1u);
+                ++pos;
+            }
+    }
+    int ex_total;
+    block_exclusive_scan(nexcl, scan, &ex_total);
+    if (tid == 0 && ex_total > 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.counters[4]), (unsigned long long)ex_total);
+}
+
+// ------------------------------------------------------- all-pairs pass ---
+
+struct PassArgs {
+    const float *w;
+    const int2 *wtiles;
+    const float *Y;
+    int KY;
+    Cert cert;
+    ProbState *st;
+    int2 *cand;
+    long long cap;
+};
+
+// One 128 x 128 tile per block of 256 threads.  Each thread owns CPT
+// adjacent columns (j) of rows spaced 8/(4/CPT) apart; K = compute width
+// (k, or k rounded up for large k: Y's pad columns are zero).  The tile's
+// w values are loaded first (many loads in flight), then turned into
+// q = ||y_i - y_j||^2 w in place; the block minimum sets the selection
+// threshold and a second pass over the registers emits the candidates.
+template <int K, int CPT>
+__global__ void __launch_bounds__(256) restr_pass_kernel(PassArgs a)
+{
+    constexpr int SR = 4 / CPT;        // warps sharing one row
+    constexpr int RSTEP = 8 / SR;      // row step of one warp
+    constexpr int RPW = T / RSTEP;     // rows per warp
+    __shared__ float red[32];
+    __shared__ int scan[33];
+    __shared__ int base_sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = warp % SR, row0 = warp / SR;
+    const int2 IJ = a.wtiles[blockIdx.x];
+    const int i0 = IJ.x * T, j0 = IJ.y * T;
+    const float *wt = a.w + (size_t)blockIdx.x * T * T;
+    const int col0 = seg * 32 * CPT + lane * CPT;
+
+    float v[RPW][CPT];
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+        const float *src = wt + (size_t)(row0 + r * RSTEP) * T + col0;
+        if (CPT == 4) {
+            const float4 t = __ldcs(reinterpret_cast<const float4 *>(src));
+            v[r][0] = t.x; v[r][CPT > 1 ? 1 : 0] = t.y; v[r][CPT > 2 ? 2 : 0] = t.z; v[r][CPT > 3 ? 3 : 0] = t.w;
+        } else if (CPT == 2) {
+            const float2 t = __ldcs(reinterpret_cast<const float2 *>(src));
+            v[r][0] = t.x; v[r][CPT > 1 ? 1 : 0] = t.y;
+        } else {
+            v[r][0] = __ldcs(src);
+        }
+    }
+    float yj[CPT][K];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const float *yr = a.Y + (size_t)(j0 + col0 + q) * a.KY;
+#pragma unroll
+        for (int c = 0; c < K; ++c) yj[q][c] = __ldg(yr + c);
+    }
+    float mymin = INFINITY;
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+        const float *yr = a.Y + (size_t)(i0 + row0 + r * RSTEP) * a.KY;
+        float yi[K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) yi[c] = __ldg(yr + c);
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            float s = 0.f;
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                const float e = yi[c] - yj[q][c];
+                s = fmaf(e, e, s);
+            }
+            v[r][q] = s * v[r][q];
+            mymin = fminf(mymin, v[r][q]);
+        }
+    }
+    const float bmin = block_min(mymin, red);
+    float U = load_pos_float(&a.st->seed_ub);
+    if (bmin < INFINITY) {
+        const float ub = cert_upper(sqrtf(bmin), a.cert);
+        if (threadIdx.x == 0) atomic_min_pos_float(&a.st->run_ub1, ub);
+        U = fminf(U, ub);
+    }
+    U = fminf(U, load_pos_float(&a.st->run_ub1));
+    const float th = cert_emit_threshold(U, a.cert);
+    const float th2 = th * th * 1.000001f;
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) cnt += v[r][q] <= th2 ? 1 : 0;
+    int total;
+    const int off = block_exclusive_scan(cnt, scan, &total);
+    if (total == 0) return;
+    if (threadIdx.x == 0) base_sh = (int)atomicAdd((unsigned int *)&a.st->cnt1, (unsigned int)total);
+    __syncthreads();
+    long long pos = (long long)(unsigned int)base_sh + off;
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+        for (int q = 0; q < CPT; ++q)
+            if (v[r][q] <= th2) {
+                if (pos < a.cap) a.cand[pos] = make_int2(i0 + row0 + r * RSTEP, j0 + col0 + q);
+                else atomicOr(&a.st->status, ST_OVERFLOW);
+                ++pos;
+            }
+}
+
+// ------------------------------------------- explicit-difference recheck ---
+
+struct ExplArgs {
+    const float *X;
+    int N, n;
+    const float *U32;  // n x KP
+    int k, KP;
+    const int2 *cand1;
+    unsigned int cap1;
+    const int2 *near;
+    int n_near;
+    Cert cert;
+    ProbState *st;
+    int2 *cand2;
+    long long cap2;
+};
+
+constexpr int EPW = 4;  // entries per warp per round
+
+// Re-evaluates the pass's candidates and the near pairs from explicit FP32
+// differences (error model of plain.cu), one warp per pair, and emits the
+// pairs that can still be the argmin for the FP64 tier.
+__global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
+{
+    __shared__ float red[32];
+    __shared__ int scan[33];
+    __shared__ int base_sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned int c1 = (unsigned int)a.st->cnt1;
+    if (c1 > a.cap1) c1 = a.cap1;
+    const long long total = (long long)c1 + a.n_near;
+    for (long long base = (long long)blockIdx.x * 8 * EPW; base < total;
+         base += (long long)gridDim.x * 8 * EPW) {
+        float rr[EPW];
+        int code[EPW];
+        int2 pr[EPW];
+        float mymin = INFINITY;
+#pragma unroll
+        for (int e = 0; e < EPW; ++e) {
+            const long long idx = base + warp * EPW + e;
+            code[e] = 0;
+            rr[e] = INFINITY;
+            pr[e] = make_int2(0, 0);
+            if (idx >= total) continue;
+            const int2 ij = idx < c1 ? a.cand1[idx] : a.near[idx - c1];
+            pr[e] = ij;
+            const float *xi = a.X + (size_t)ij.x * a.n;
+            const float *xj = a.X + (size_t)ij.y * a.n;
+            float dd = 0.f, z[kMaxK];
+#pragma unroll
+            for (int c = 0; c < kMaxK; ++c) z[c] = 0.f;
+            for (int l = lane; l < a.n; l += 32) {
+                const float D = xi[l] - xj[l];
+                dd = fmaf(D, D, dd);
+                const float *ur = a.U32 + (size_t)l * a.KP;
+#pragma unroll
+                for (int c = 0; c < kMaxK; ++c)
+                    if (c < a.k) z[c] = fmaf(ur[c], D, z[c]);
+            }
+            dd = warp_sumf(dd);
+            float zz = 0.f;
+#pragma unroll
+            for (int c = 0; c < kMaxK; ++c)
+                if (c < a.k) {
+                    const float zc = warp_sumf(z[c]);
+                    zz = fmaf(zc, zc, zz);
+                }
+            if (dd < 1e-30f) {
+                code[e] = 2;  // too short for FP32: always passed on
+            } else {
+                code[e] = 1;
+                rr[e] = sqrtf(zz / dd);
+                mymin = fminf(mymin, rr[e]);
+            }
+        }
+        const float bmin = block_min(mymin, red);
+        float U = load_pos_float(&a.st->seed_ub);
+        if (bmin < INFINITY) {
+            const float ub = cert_upper(bmin, a.cert);
+            if (threadIdx.x == 0) atomic_min_pos_float(&a.st->run_ub2, ub);
+            U = fminf(U, ub);
+        }
+        U = fminf(U, load_pos_float(&a.st->run_ub2));
+        const float th = cert_emit_threshold(U, a.cert);
+        int cnt = 0;
+        if (lane == 0)
+#pragma unroll
+            for (int e = 0; e < EPW; ++e) cnt += (code[e] == 2 || (code[e] == 1 && rr[e] <= th)) ? 1 : 0;
+        int tot;
+        const int off = block_exclusive_scan(cnt, scan, &tot);
+        if (tot == 0) continue;
+        if (threadIdx.x == 0) base_sh = (int)atomicAdd((unsigned int *)&a.st->cnt2, (unsigned int)tot);
+        __syncthreads();
+        if (lane == 0) {
+            long long pos = (long long)(unsigned int)base_sh + off;
+#pragma unroll
+            for (int e = 0; e < EPW; ++e)
+                if (code[e] == 2 || (code[e] == 1 && rr[e] <= th)) {
+                    if (pos < a.cap2) a.cand2[pos] = pr[e];
+                    else atomicOr(&a.st->status, ST_OVERFLOW);
+                    ++pos;
+                }
+        }
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------------- host side --
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 2-D map of a row-major [outer x inner] 16-bit matrix, box [box_outer x 64]
+// with 128-byte swizzling (the K-major operand layout of the product).
+bool make_map(CUtensorMap *m, void *base, bool bf16, uint64_t inner, uint64_t outer, uint32_t box_outer)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {64, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims,
+              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename T_>
+void dfree(T_ *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+#define RCK(call)                                                                            \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return handle_fail(h, e_ == cudaErrorMemoryAllocation ? SAP_E_OOM : SAP_E_CUDA,  \
+                               cudaGetErrorString(e_));                                      \
+    } while (0)
+
+// Bound on |y~_c - y_c| per unit ||fl(x - mean)|| (see gemm_tc.cu):
+// centring and epilogue roundings, the split residuals and dropped low
+// product, and the FP32 accumulation chain of the high product
+// (ceil(NP/16) MMAs, plus slack for the in-instruction adder tree), each
+// accumulation step bounded by 2^-23 (truncation) of twice the running
+// magnitude.  Times 1.25 for margin.
+double y_error_unit(int NP, bool bf16)
+{
+    const double u = std::ldexp(1.0, -24);
+    const double split = bf16 ? 3.0 * std::ldexp(1.0, -16) : 3.0 * std::ldexp(1.0, -22);
+    const double acc = (std::ceil(NP / 16.0) + 4.0) * 2.0 * std::ldexp(1.0, -23);
+    return (3.0 * u + split + acc) * 1.25;
+}
+
+Cert cert_pass(int n, int k, double b_cap)
+{
+    const double u = std::ldexp(1.0, -24);
+    auto g = [&](double m) { return m * u / (1.0 - m * u); };
+    Cert c;
+    c.A = (float)b_cap;
+    c.rho = (float)((g(n + 2) + g(k) + 6 * u) * 1.05);
+    return c;
+}
+
+Cert cert_explicit(int n, int k)
+{
+    const double u = std::ldexp(1.0, -24);
+    auto g = [&](double m) { return m * u / (1.0 - m * u); };
+    Cert c;
+    c.A = (float)(std::sqrt((double)k) * g(n + 3) * 1.05);
+    c.rho = (float)((g(n + 2) + g(k) + 3 * u) * 1.05);
+    return c;
+}
+
+sap_status classify(sap_handle h, int k)
+{
+    RestrState &r = restr_state(h);
+    cudaStream_t s = handle_stream(h);
+    RCK(cudaMemsetAsync(r.counters, 0, 8 * sizeof(unsigned int), s));
+    WPrepArgs a;
+    a.X = handle_x32(h);
+    a.N = (int)handle_n_points(h);
+    a.n = handle_n_dim(h);
+    a.nu = r.nu;
+    a.wtiles = r.wtiles;
+    a.w = r.w;
+    a.eps2_lo = handle_eps2_lo(h);
+    a.eps2_hi = handle_eps2_hi(h);
+    a.eps2 = handle_eps2(h);
+    a.beta_coef = (float)(std::sqrt((double)k) * r.y_eps * 1.02);
+    a.b_cap = (float)r.b_cap;
+    a.near = r.near;
+    a.near_cap = r.near_cap;
+    a.counters = r.counters;
+    wprep_kernel<<<r.nwtiles, 256, 0, s>>>(a);
+    RCK(cudaGetLastError());
+    unsigned int cnt[8];
+    RCK(cudaMemcpyAsync(cnt, r.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    RCK(cudaStreamSynchronize(s));
+    if (cnt[2]) return handle_fail(h, SAP_E_UNSUPPORTED, "near-pair list overflow; raise the pass bound");
+    r.n_near = (int)cnt[0];
+    unsigned long long ex;
+    std::memcpy(&ex, &cnt[4], sizeof(ex));
+    r.n_excluded = (long long)ex;
+    r.k_cls = k;
+    return SAP_OK;
+}
+
+template <int K, int CPT>
+cudaError_t launch_pass_k(const PassArgs &a, int grid, cudaStream_t s)
+{
+    restr_pass_kernel<K, CPT><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Columns of Y the pass reads per row: k itself up to 8, else k rounded up
+// to the next instantiated width (Y's extra columns are zero).
+int pass_width(int k)
+{
+    if (k <= 8) return k;
+    if (k <= 12) return 12;
+    if (k <= 16) return 16;
+    if (k <= 24) return 24;
+    return 32;
+}
+
+cudaError_t launch_pass(const PassArgs &a, int k, int grid, cudaStream_t s)
+{
+    switch (k) {
+    case 1: return launch_pass_k<1, 4>(a, grid, s);
+    case 2: return launch_pass_k<2, 4>(a, grid, s);
+    case 3: return launch_pass_k<3, 4>(a, grid, s);
+    case 4: return launch_pass_k<4, 4>(a, grid, s);
+    case 5: return launch_pass_k<5, 4>(a, grid, s);
+    case 6: return launch_pass_k<6, 4>(a, grid, s);
+    case 7: return launch_pass_k<7, 4>(a, grid, s);
+    case 8: return launch_pass_k<8, 4>(a, grid, s);
+    default: break;
+    }
+    if (k <= 12) return launch_pass_k<12, 2>(a, grid, s);
+    if (k <= 16) return launch_pass_k<16, 2>(a, grid, s);
+    if (k <= 24) return launch_pass_k<24, 1>(a, grid, s);
+    return launch_pass_k<32, 1>(a, grid, s);
+}
+
+} // namespace
+
+sap_status restructured_prepare(sap_handle h)
+{
+    RestrState &r = restr_state(h);
+    cudaStream_t s = handle_stream(h);
+    const int N = (int)handle_n_points(h), n = handle_n_dim(h);
+    const bool bf16 = handle_split_bf16(h) != 0;
+    const float *X = handle_x32(h);
+    RCK(cudaStreamSynchronize(s));
+    if (!r.center) {
+        r.Npad = (N + T - 1) / T * T;
+        r.NP = (n + 63) / 64 * 64;
+        RCK(cudaMalloc(&r.center, n * sizeof(float)));
+        RCK(cudaMalloc(&r.nu, r.Npad * sizeof(float)));
+        RCK(cudaMalloc(&r.Xhi, (size_t)r.Npad * r.NP * 2));
+        RCK(cudaMalloc(&r.Xlo, (size_t)r.Npad * r.NP * 2));
+        RCK(cudaMalloc(&r.counters, 8 * sizeof(unsigned int)));
+        const int nb = r.Npad / T;
+        std::vector<int2> t;
+        for (int I = 0; I < nb; ++I)
+            for (int J = I; J < nb; ++J) t.push_back(make_int2(I, J));
+        r.nwtiles = (int)t.size();
+        RCK(cudaMalloc(&r.wtiles, t.size() * sizeof(int2)));
+        RCK(cudaMemcpy(r.wtiles, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        RCK(cudaMalloc(&r.w, (size_t)r.nwtiles * T * T * sizeof(float)));
+        const long long P = (long long)N * (N - 1) / 2;
+        r.near_cap = (unsigned int)std::min<long long>(P + 64, 1ll << 26);
+        RCK(cudaMalloc(&r.near, (size_t)r.near_cap * sizeof(int2)));
+        RCK(gemm_configure());
+    }
+    const int sms = handle_sms(h);
+    colmean_kernel<<<(n + 127) / 128, 128, 0, s>>>(X, N, n, r.center);
+    RCK(cudaGetLastError());
+    RCK(cudaMemsetAsync(r.counters, 0, 8 * sizeof(unsigned int), s));
+    absmax_kernel<<<4 * sms, 256, 0, s>>>(X, (size_t)N * n, n, r.center, r.counters);
+    RCK(cudaGetLastError());
+    unsigned int mbits = 0;
+    RCK(cudaMemcpyAsync(&mbits, r.counters, sizeof(mbits), cudaMemcpyDeviceToHost, s));
+    RCK(cudaStreamSynchronize(s));
+    float mx;
+    std::memcpy(&mx, &mbits, sizeof(mx));
+    int e = 0;
+    if (mx > 0.f) e = (int)std::ceil(std::log2((double)mx));
+    r.xscale = (float)std::ldexp(1.0, -e);
+    const float lo_mul = bf16 ? 256.f : 2048.f;
+    if (bf16)
+        split_kernel<__nv_bfloat16><<<4 * sms, 256, 0, s>>>(X, N, n, r.center, r.xscale, lo_mul,
+                                                          (__nv_bfloat16 *)r.Xhi, (__nv_bfloat16 *)r.Xlo,
+                                                          r.Npad, r.NP);
+    else
+        split_kernel<__half><<<4 * sms, 256, 0, s>>>(X, N, n, r.center, r.xscale, lo_mul, (__half *)r.Xhi,
+                                                     (__half *)r.Xlo, r.Npad, r.NP);
+    RCK(cudaGetLastError());
+    rownorm_kernel<<<(r.Npad + 7) / 8, 256, 0, s>>>(X, N, n, r.center, r.nu, r.Npad);
+    RCK(cudaGetLastError());
+    r.y_eps = y_error_unit(r.NP, bf16);
+    if (!make_map(&r.gemm.ta_hi, r.Xhi, bf16, r.NP, r.Npad, 128) ||
+        !make_map(&r.gemm.ta_lo, r.Xlo, bf16, r.NP, r.Npad, 128))
+        return handle_fail(h, SAP_E_CUDA, "cuTensorMapEncodeTiled failed for X");
+    r.maps_x = true;
+    if (r.Uhi) {
+        if (!make_map(&r.gemm.tb_hi, r.Uhi, bf16, r.NP, r.KPG, r.KPG) ||
+            !make_map(&r.gemm.tb_lo, r.Ulo, bf16, r.NP, r.KPG, r.KPG))
+            return handle_fail(h, SAP_E_CUDA, "cuTensorMapEncodeTiled failed for U");
+    }
+    r.k_cls = 0;
+    const int k = handle_k(h);
+    if (k > 0) return classify(h, k);
+    RCK(cudaStreamSynchronize(s));
+    return SAP_OK;
+}
+
+sap_status restructured_basis_alloc(sap_handle h)
+{
+    RestrState &r = restr_state(h);
+    const int k = handle_k(h);
+    const bool bf16 = handle_split_bf16(h) != 0;
+    dfree(r.Uhi);
+    dfree(r.Ulo);
+    dfree(r.Y);
+    r.KPG = (k + 15) / 16 * 16;
+    r.KY = (pass_width(k) + 3) / 4 * 4;   // <= KPG; columns >= k are zero
+    RCK(cudaMalloc(&r.Uhi, (size_t)r.KPG * r.NP * 2));
+    RCK(cudaMalloc(&r.Ulo, (size_t)r.KPG * r.NP * 2));
+    RCK(cudaMalloc(&r.Y, (size_t)r.Npad * r.KY * sizeof(float)));
+    RCK(cudaMemset(r.Y, 0, (size_t)r.Npad * r.KY * sizeof(float)));
+    if (!make_map(&r.gemm.tb_hi, r.Uhi, bf16, r.NP, r.KPG, r.KPG) ||
+        !make_map(&r.gemm.tb_lo, r.Ulo, bf16, r.NP, r.KPG, r.KPG))
+        return handle_fail(h, SAP_E_CUDA, "cuTensorMapEncodeTiled failed for U");
+    r.maps_u = true;
+    return SAP_OK;
+}
+
+sap_status restructured_upload_basis(sap_handle h, const double *U)
+{
+    RestrState &r = restr_state(h);
+    const int k = handle_k(h), n = handle_n_dim(h);
+    const bool bf16 = handle_split_bf16(h) != 0;
+    const double lo_mul = bf16 ? 256.0 : 2048.0;
+    std::vector<uint16_t> hi((size_t)r.KPG * r.NP, 0), lo((size_t)r.KPG * r.NP, 0);
+    for (int c = 0; c < k; ++c)
+        for (int l = 0; l < n; ++l) {
+            const double v = U[(size_t)c * n + l];
+            const size_t idx = (size_t)c * r.NP + l;
+            if (bf16) {
+                const __nv_bfloat16 hv = __double2bfloat16(v);
+                const __nv_bfloat16 lv = __double2bfloat16((v - (double)__bfloat162float(hv)) * lo_mul);
+                std::memcpy(&hi[idx], &hv, 2);
+                std::memcpy(&lo[idx], &lv, 2);
+            } else {
+                const __half hv = __double2half(v);
+                const __half lv = __double2half((v - (double)__half2float(hv)) * lo_mul);
+                std::memcpy(&hi[idx], &hv, 2);
+                std::memcpy(&lo[idx], &lv, 2);
+            }
+        }
+    RCK(cudaMemcpy(r.Uhi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice));
+    RCK(cudaMemcpy(r.Ulo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice));
+    if (r.k_cls != k) return classify(h, k);
+    return SAP_OK;
+}
+
+sap_status restructured_set_bound(sap_handle h, double b_cap)
+{
+    RestrState &r = restr_state(h);
+    r.b_cap = b_cap;
+    const int k = handle_k(h);
+    if (k > 0) return classify(h, k);
+    return SAP_OK;
+}
+
+sap_status restructured_enqueue(sap_handle h, double alpha)
+{
+    (void)alpha;
+    RestrState &r = restr_state(h);
+    cudaStream_t s = handle_stream(h);
+    const int k = handle_k(h), n = handle_n_dim(h);
+    ProbState *st = handle_state(h);
+    cudaEvent_t ea, eb;
+    {
+        GemmArgs g = r.gemm;
+        g.Y = r.Y;
+        g.KY = r.KY;
+        g.Npad = r.Npad;
+        g.nkb = r.NP / 64;
+        g.KPG = r.KPG;
+        g.ab_bf16 = handle_split_bf16(h);
+        g.stages = gemm_pick_stages(r.KPG, g.nkb);
+        g.lo_scale = g.ab_bf16 ? 1.0f / 256.f : 1.0f / 2048.f;
+        g.out_scale = 1.0f / r.xscale;
+        g.st = st;
+        handle_count_launch(h, 0, &ea, &eb);
+        if (ea) cudaEventRecord(ea, s);
+        RCK(launch_gemm_y(g, s));
+        if (eb) cudaEventRecord(eb, s);
+        handle_push_timing(h, 0, ea, eb);
+    }
+    {
+        PassArgs p;
+        p.w = r.w;
+        p.wtiles = r.wtiles;
+        p.Y = r.Y;
+        p.KY = r.KY;
+        p.cert = cert_pass(n, k, r.b_cap);
+        p.st = st;
+        p.cand = handle_cand1(h);
+        p.cap = handle_cap(h);
+        handle_count_launch(h, 1, &ea, &eb);
+        if (ea) cudaEventRecord(ea, s);
+        RCK(launch_pass(p, k, r.nwtiles, s));
+        if (eb) cudaEventRecord(eb, s);
+        handle_push_timing(h, 1, ea, eb);
+    }
+    {
+        ExplArgs x;
+        x.X = handle_x32(h);
+        x.N = (int)handle_n_points(h);
+        x.n = n;
+        x.U32 = handle_u32(h);
+        x.k = k;
+        x.KP = handle_kp(h);
+        x.cand1 = handle_cand1(h);
+        x.cap1 = (unsigned int)handle_cap(h);
+        x.near = r.near;
+        x.n_near = r.n_near;
+        x.cert = cert_explicit(n, k);
+        x.st = st;
+        x.cand2 = handle_cand2(h);
+        x.cap2 = handle_cap(h);
+        handle_count_launch(h, 3, &ea, &eb);
+        if (ea) cudaEventRecord(ea, s);
+        explicit_recheck_kernel<<<2 * handle_sms(h), 256, 0, s>>>(x);
+        RCK(cudaGetLastError());
+        if (eb) cudaEventRecord(eb, s);
+        handle_push_timing(h, 3, ea, eb);
+    }
+    return SAP_OK;
+}
+
+sap_status restructured_project(sap_handle h, float *Y_out, int out_is_device)
+{
+    RestrState &r = restr_state(h);
+    cudaStream_t s = handle_stream(h);
+    const int k = handle_k(h);
+    const int N = (int)handle_n_points(h);
+    GemmArgs g = r.gemm;
+    g.Y = r.Y;
+    g.KY = r.KY;
+    g.Npad = r.Npad;
+    g.nkb = r.NP / 64;
+    g.KPG = r.KPG;
+    g.ab_bf16 = handle_split_bf16(h);
+    g.stages = gemm_pick_stages(r.KPG, g.nkb);
+    g.lo_scale = g.ab_bf16 ? 1.0f / 256.f : 1.0f / 2048.f;
+    g.out_scale = 1.0f / r.xscale;
+    g.st = handle_state(h);
+    cudaEvent_t ea, eb;
+    handle_count_launch(h, 0, &ea, &eb);
+    if (ea) cudaEventRecord(ea, s);
+    RCK(launch_gemm_y(g, s));
+    if (eb) cudaEventRecord(eb, s);
+    handle_push_timing(h, 0, ea, eb);
+    RCK(cudaMemcpy2DAsync(Y_out, (size_t)k * sizeof(float), r.Y, (size_t)r.KY * sizeof(float),
+                          (size_t)k * sizeof(float), N,
+                          out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    RCK(cudaStreamSynchronize(s));
+    return SAP_OK;
+}
+
+int restructured_kernels_per_iteration(sap_handle h)
+{
+    (void)h;
+    return 3;
+}
+
+void restructured_free(sap_handle h)
+{
+    RestrState &r = restr_state(h);
+    dfree(r.Xhi); dfree(r.Xlo); dfree(r.center); dfree(r.nu); dfree(r.w); dfree(r.wtiles);
+    dfree(r.near); dfree(r.counters); dfree(r.Uhi); dfree(r.Ulo); dfree(r.Y);
+}
+
+void restructured_stats(sap_handle h, sap_stats *out)
+{
+    RestrState &r = restr_state(h);
+    out->n_near = r.n_near;
+    out->n_excluded = r.n_excluded;
+    out->cert_bound = r.b_cap;
+    out->y_error_unit = r.y_eps;
+}
+
+} // namespace sap

@@ -1,0 +1,75 @@
+// restructured.cuh -- buffers and entry points of the restructured form
+// (Y = X U on tensor cores, then an all-pairs pass over stored inverse squared
+// lengths), used by the engine in capi.cu.
+#pragma once
+
+#include "sap_internal.cuh"
+#include "gemm_tc.cuh"
+#include "../../include/sap.h"
+
+namespace sap {
+
+struct RestrState {
+    // centred, scaled, split copy of X: Npad x NP 16-bit, hi and lo parts
+    void *Xhi = nullptr, *Xlo = nullptr;
+    int Npad = 0;         // N rounded up to the tile (128)
+    int NP = 0;           // n rounded up to the GEMM k-block (64)
+    float xscale = 1.f;   // power of two applied to (x - mean) before splitting
+    float *center = nullptr;  // column means (n), FP32
+    float *nu = nullptr;  // ||fl(x_i - mean)||, rounded up (Npad)
+    // inverse squared lengths, tile-major upper triangle (kTile x kTile tiles);
+    // NaN marks a pair the pass skips (invalid, excluded, or near)
+    float *w = nullptr;
+    int2 *wtiles = nullptr;   // (I, J) per tile, I <= J
+    int nwtiles = 0;
+    int2 *near = nullptr;     // pairs re-evaluated from explicit differences
+    unsigned int near_cap = 0;
+    unsigned int *counters = nullptr;  // [0] near count, [1..2] excluded (u64)
+    int n_near = 0;
+    long long n_excluded = 0;
+    int k_cls = 0;            // k the near classification was made for
+    double y_eps = 0.0;       // bound on |y~ - y| per unit ||x - mean||
+    double b_cap = 5e-4;      // absolute ratio bound of the all-pairs pass
+    // basis operands
+    void *Uhi = nullptr, *Ulo = nullptr;  // KPG x NP 16-bit
+    int KPG = 0;              // k rounded up to the MMA N granule (16)
+    float *Y = nullptr;       // Npad x KY
+    int KY = 0;               // k rounded up to 4
+    GemmArgs gemm;            // tensor maps and shapes of the product
+    bool maps_x = false, maps_u = false;
+};
+
+// Engine accessors (capi.cu).
+RestrState &restr_state(sap_handle h);
+cudaStream_t handle_stream(sap_handle h);
+int handle_sms(sap_handle h);
+ProbState *handle_state(sap_handle h);
+const float *handle_x32(sap_handle h);
+const float *handle_u32(sap_handle h);
+int2 *handle_cand1(sap_handle h);
+int2 *handle_cand2(sap_handle h);
+long long handle_cap(sap_handle h);
+int handle_k(sap_handle h);
+int handle_kp(sap_handle h);
+int64_t handle_n_points(sap_handle h);
+int handle_n_dim(sap_handle h);
+int handle_split_bf16(sap_handle h);
+double handle_eps2(sap_handle h);
+float handle_eps2_lo(sap_handle h);
+float handle_eps2_hi(sap_handle h);
+void handle_count_launch(sap_handle h, int cls, cudaEvent_t *a, cudaEvent_t *b);
+void handle_push_timing(sap_handle h, int cls, cudaEvent_t a, cudaEvent_t b);
+sap_status handle_fail(sap_handle h, sap_status s, const char *msg);
+
+// Restructured-form entry points (restructured.cu).
+sap_status restructured_prepare(sap_handle h);          // X split, norms, lengths, near list
+sap_status restructured_basis_alloc(sap_handle h);      // U operands and Y for k
+sap_status restructured_upload_basis(sap_handle h, const double *U); // n x k col-major
+sap_status restructured_enqueue(sap_handle h, double alpha);
+int restructured_kernels_per_iteration(sap_handle h);
+void restructured_free(sap_handle h);
+void restructured_stats(sap_handle h, sap_stats *out);
+sap_status restructured_set_bound(sap_handle h, double b_cap);
+sap_status restructured_project(sap_handle h, float *Y_out, int out_is_device);
+
+} // namespace sap

@@ -1,0 +1,243 @@
+// sap_internal.cuh -- device-side state, constants and helpers shared by the
+// library's translation units (not part of the public C ABI).
+//
+// Method: Secant-Avoidance Projection (SAP), Kvinge et al., arXiv:1807.03425,
+// Sec. IV and Algorithm 1.  Notation: N points x_i in R^n (row-major X), an
+// orthonormal basis U (n x k), unit secants s_ij = (x_i - x_j)/d_ij and ratios
+// r_ij = ||U^T s_ij||.
+//
+// Selection scheme used by every all-pairs pass.  A pass evaluates r~ for all
+// pairs in some fast arithmetic whose error is certified:
+//     |r~ - r| <= A + rho * r          (A absolute, rho relative)
+// so  r >= lower(r~) = (r~ - A)/(1 + rho)  and  r <= upper(r~) = (r~ + A)/(1 - rho).
+// Any upper(r~_g) of an evaluated pair, and any exact ratio, bounds the true
+// minimum R* from above.  A pair can be the argmin only if lower(r~_p) <= R*,
+// i.e. r~_p <= U (1 + rho) + A for every valid upper bound U, so the pass
+// emits exactly those pairs against the tightest U it knows.  The next tier
+// re-evaluates the emitted list more precisely; the last tier is FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sap {
+
+constexpr int kMaxK = 32;          // largest target dimension
+constexpr int kWatch = 8;          // recent argmin pairs re-evaluated as seeds
+constexpr int kTile = 128;         // edge of a w tile (restructured form)
+constexpr int kRecheckBlocks = 304; // FP64 recheck grid (2 x 152 SMs)
+
+enum StatusBits : int {
+    ST_NO_SECANT = 1,
+    ST_TIMEOUT = 2,
+    ST_OVERFLOW = 4,
+};
+
+// Per-problem device state (one basis over one dataset).
+struct ProbState {
+    unsigned int seed_ub;   // float bits: upper bound on R* from the watch list
+    unsigned int run_ub1;   // float bits: running upper bound, all-pairs pass
+    unsigned int run_ub2;   // float bits: running upper bound, explicit recheck
+    int cnt1;               // entries emitted by the all-pairs pass
+    int cnt2;               // entries emitted by the explicit recheck
+    int iter;               // evaluations recorded in the history
+    int status;             // StatusBits
+    int watch_n;            // filled entries of watch[]
+    int watch_pos;          // next ring slot
+    int last_cnt1, last_cnt2;
+    int hist_cap;           // capacity of the history arrays
+    int pad0;
+    int2 watch[kWatch];
+    double last_r;          // result of the latest evaluation
+    int last_i, last_j;
+};
+
+// Best pair of one recheck block (FP64).
+struct Partial {
+    double r;
+    int i, j;
+};
+
+// Certified error model of one tier (see the header comment).
+struct Cert {
+    float A;
+    float rho;
+};
+
+__device__ __forceinline__ float cert_upper(float rt, Cert c)
+{
+    // rounded outward by a relative 1e-6 so the fp32 evaluation stays an
+    // upper bound
+    return (rt + c.A) / (1.0f - c.rho) * 1.000001f;
+}
+
+__device__ __forceinline__ float cert_emit_threshold(float U, Cert c)
+{
+    return (U * (1.0f + c.rho) + c.A) * 1.000001f;
+}
+
+// Non-negative floats order like their bit patterns.
+__device__ __forceinline__ void atomic_min_pos_float(unsigned int *addr, float v)
+{
+    atomicMin(addr, __float_as_uint(v));
+}
+
+__device__ __forceinline__ float load_pos_float(const unsigned int *addr)
+{
+    return __uint_as_float(*(volatile const unsigned int *)addr);
+}
+
+__device__ __forceinline__ bool better(double r, int i, int j, double rb, int ib, int jb)
+{
+    // lexicographic (ratio, i, j): ties go to the smallest pair index
+    if (r < rb) return true;
+    if (r > rb) return false;
+    if (i != ib) return i < ib;
+    return j < jb;
+}
+
+__device__ __forceinline__ float warp_min(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide minimum of a float; all threads get the result.  scratch holds
+// at least blockDim.x/32 floats.
+__device__ __forceinline__ float block_min(float v, float *scratch)
+{
+    v = warp_min(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) scratch[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    float r = (l < nw) ? scratch[l] : INFINITY;
+    r = warp_min(r);
+    return r;
+}
+
+// Exclusive prefix of per-thread counts over the block; returns the block
+// total through *total.  scratch holds at least 33 ints.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *scratch, int *total)
+{
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (l >= o) x += y;
+    }
+    __syncthreads();
+    if (l == 31) scratch[w] = x;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (w == 0) {
+        int s = (l < nw) ? scratch[l] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (l >= o) s += y;
+        }
+        if (l < nw) scratch[l] = s;          // inclusive prefix of warp sums
+        if (l == nw - 1) scratch[32] = s;    // block total
+    }
+    __syncthreads();
+    *total = scratch[32];
+    return (w > 0 ? scratch[w - 1] : 0) + x - v;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (implemented in the .cu files, called by the engine).
+
+struct PlainArgsF32 {
+    const float *X;        // N x n row-major
+    int N, n;
+    const float *U32;      // n x KP row-major (l, c)
+    int k, KP;
+    const int2 *tiles;     // (I, J) 64-point blocks, I <= J
+    int ntiles;
+    int grid;              // persistent grid size
+    float eps2_lo, eps2_hi; // d^2 window decided in FP64 downstream (0,0: none)
+    Cert cert;
+    ProbState *st;
+    int2 *cand;            // output list
+    long long cand_cap;
+};
+
+struct PlainArgsF64 {
+    const double *X;
+    int N, n;
+    const double *U64;     // n x k column-major
+    int k;
+    const int2 *tiles;     // (I, J) 16-point blocks, I <= J
+    int ntiles;
+    int grid;
+    double eps2;
+    Cert cert;
+    ProbState *st;
+    int2 *cand;
+    long long cand_cap;
+};
+
+cudaError_t launch_plain_f32(const PlainArgsF32 &a, cudaStream_t s);
+cudaError_t launch_plain_f64(const PlainArgsF64 &a, cudaStream_t s);
+
+// FP64 recheck of a candidate list; count read from st->cnt1 (which == 1) or
+// st->cnt2 (which == 2).
+struct RecheckArgs {
+    const void *X;         // float or double, N x n
+    int x_is_f64;
+    int N, n;
+    const double *U64;     // n x k column-major
+    int k;
+    double eps2;
+    const int2 *list;
+    unsigned int cap;      // capacity of list
+    int which;
+    const ProbState *st;
+    Partial *partials;     // kRecheckBlocks entries
+};
+cudaError_t launch_recheck_fp64(const RecheckArgs &a, cudaStream_t s);
+
+struct UpdateArgs {
+    const Partial *partials;
+    int nparts;
+    const void *X;
+    int x_is_f64;
+    int N, n;
+    double *U64;           // n x k column-major, updated in place
+    float *U32;            // n x KP row-major, written
+    int KP;
+    void *Uhi, *Ulo;       // tensor-core operands (KPG x NP, 16-bit), or null
+    int KPG, NP;
+    int split_bf16;        // 0: FP16 split, 1: BF16 split
+    float split_scale;     // multiplier of the low part (2^11 FP16, 2^8 BF16)
+    int k;
+    double alpha;
+    int mode;              // 0 literal, 1 angle
+    int eval_only;
+    double *work;          // (k + 2) * n doubles of scratch
+    ProbState *st;
+    double *hist;          // hist_cap entries
+    int2 *argmin;          // hist_cap entries
+    Cert seed_cert;        // error model of the seed evaluation
+};
+cudaError_t launch_update(const UpdateArgs &a, cudaStream_t s);
+
+} // namespace sap

@@ -219,7 +219,8 @@ sap_status sap_get_stats(sap_handle h, sap_stats *out);
  * handle's stream; sap_get_kernel_time returns the accumulated device time
  * (ms) and launch count of one kernel class.  Classes: 0 Y = XU product,
  * 1 restructured all-pairs pass, 2 plain all-pairs pass, 3 explicit-difference
- * recheck, 4 FP64 recheck, 5 update.  Enabling resets the accumulators.
+ * recheck, 5 FP64 recheck fused with the update (4 is unused).  Enabling
+ * resets the accumulators.
  */
 sap_status sap_set_profiling(sap_handle h, int enable);
 sap_status sap_get_kernel_time(sap_handle h, int32_t kernel_class,

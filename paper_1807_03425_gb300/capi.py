@@ -22,7 +22,7 @@ PLAIN, RESTRUCTURED = 0, 1
 UPDATE_LITERAL, UPDATE_ANGLE = 0, 1
 SPLIT_FP16, SPLIT_BF16 = 0, 1
 KERNEL_CLASSES = {"gemm_y": 0, "restructured_pass": 1, "plain_pass": 2,
-                  "explicit_recheck": 3, "fp64_recheck": 4, "update": 5}
+                  "explicit_recheck": 3, "select_update": 5, "update": 5}
 
 STATUS = {0: "SAP_OK", 1: "SAP_E_ARG", 2: "SAP_E_STATE", 3: "SAP_E_NOT_ORTHONORMAL",
           4: "SAP_E_NO_SECANT", 5: "SAP_E_OOM", 6: "SAP_E_CUDA", 7: "SAP_E_TIMEOUT",

@@ -240,26 +240,18 @@ sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only)
         list = h->cand2;
     }
     {
-        RecheckArgs r;
-        r.X = f64 ? (const void *)h->X64 : (const void *)h->X32;
-        r.x_is_f64 = f64; r.N = (int)h->N; r.n = h->n; r.U64 = h->U64; r.k = h->k;
-        r.eps2 = h->eps2_f64; r.list = list; r.cap = (unsigned int)h->cap; r.which = which;
-        r.st = h->st; r.partials = h->partials;
-        Timed t(h, K_FP64);
-        CK(launch_recheck_fp64(r, s));
-    }
-    {
-        UpdateArgs u;
-        u.partials = h->partials; u.nparts = kRecheckBlocks;
+        SelectUpdateArgs u;
         u.X = f64 ? (const void *)h->X64 : (const void *)h->X32;
         u.x_is_f64 = f64; u.N = (int)h->N; u.n = h->n;
         u.U64 = h->U64; u.U32 = h->U32; u.KP = h->KP;
-        u.Uhi = h->rs.Uhi; u.Ulo = h->rs.Ulo; u.KPG = h->rs.KPG; u.NP = h->rs.NP;
+        u.Uhi = h->rs.Uhi; u.Ulo = h->rs.Ulo; u.NP = h->rs.NP;
         u.split_bf16 = h->split == SAP_SPLIT_BF16; u.split_scale = h->split == SAP_SPLIT_BF16 ? 256.f : 2048.f;
         u.k = h->k; u.alpha = alpha; u.mode = (int)h->mode; u.eval_only = eval_only;
+        u.eps2 = h->eps2_f64; u.list = list; u.cap = (unsigned int)h->cap; u.which = which;
+        u.partials = h->partials; u.grid = std::min(h->sms, 64);
         u.work = h->work; u.st = h->st; u.hist = h->hist; u.argmin = h->am; u.seed_cert = c32;
         Timed t(h, K_UPDATE);
-        CK(launch_update(u, s));
+        CK(launch_select_update(u, s));
     }
     return SAP_OK;
 }
@@ -580,10 +572,10 @@ sap_status sap_set_basis(sap_handle h, const double *U, int32_t k, int u_is_devi
         drop_graphs(h);
         dfree(h->U64); dfree(h->U32); dfree(h->work);
         h->k = k;
-        h->KP = (k + 3) & ~3;
+        h->KP = padded_stride(k);  // pad columns stay zero
         CK(dalloc(&h->U64, (size_t)n * k));
         CK(dalloc(&h->U32, (size_t)n * h->KP));
-        h->work_elems = (size_t)(k + 2) * n;
+        h->work_elems = (size_t)(kMaxK + 1) * n;
         CK(dalloc(&h->work, h->work_elems));
         if (h->dt != SAP_F64) {
             sap_status s = restructured_basis_alloc(h);
@@ -675,7 +667,7 @@ static sap_status graph_for(sap_handle h, double alpha, int eval_only, int chunk
 
 static int kernels_per_iteration(sap_handle h)
 {
-    return h->path == SAP_PLAIN ? 3 : restructured_kernels_per_iteration(h) + 2;
+    return h->path == SAP_PLAIN ? 2 : restructured_kernels_per_iteration(h) + 1;
 }
 
 sap_status sap_run(sap_handle h, double alpha, int32_t iters, double *hist, int64_t *argmins)

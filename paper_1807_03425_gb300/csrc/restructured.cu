@@ -22,6 +22,7 @@
 // w + t*128*128; entries with i >= j, with an index beyond N, excluded pairs
 // and near pairs hold NaN.
 #include "restructured.cuh"
+#include "tc_ptx.cuh"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -227,109 +228,190 @@ __global__ void __launch_bounds__(256) wprep_kernel(WPrepArgs a)
 
 // ------------------------------------------------------- all-pairs pass ---
 
+constexpr int kPassStagesMax = 3;
+constexpr int kPassThreads = 256;
+
 struct PassArgs {
     const float *w;
     const int2 *wtiles;
+    int ntiles;
     const float *Y;
     int KY;
+    int stages;
     Cert cert;
     ProbState *st;
     int2 *cand;
     long long cap;
 };
 
-// One 128 x 128 tile per block of 256 threads.  Each thread owns CPT
-// adjacent columns (j) of rows spaced 8/(4/CPT) apart; K = compute width
-// (k, or k rounded up for large k: Y's pad columns are zero).  The tile's
-// w values are loaded first (many loads in flight), then turned into
-// q = ||y_i - y_j||^2 w in place; the block minimum sets the selection
-// threshold and a second pass over the registers emits the candidates.
+__host__ __device__ inline uint32_t pass_stage_bytes(int KY)
+{
+    return (uint32_t)T * T * 4 + 2u * T * KY * 4;
+}
+
+// Persistent pass: one block of 256 threads per SM walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Thread 0 keeps a ring of
+// `stages` shared-memory buffers filled by 1-D TMA bulk copies (the 64 KB
+// w tile plus the 128 rows of Y for each side), so the next tiles stream in
+// while the current one is evaluated.  Each thread owns CPT adjacent columns
+// of rows spaced 8/(4/CPT) apart; K = compute width (k, or k rounded up for
+// large k: Y's pad columns are zero).  q = ||y_i - y_j||^2 w is formed with
+// packed FP32 pairs and kept in registers; the block minimum sets the
+// selection threshold and a second pass over the registers emits the
+// candidates.  The global running bound is read at the start of a tile and
+// tightened with a fire-and-forget atomic, so no thread waits on it.
 template <int K, int CPT>
-__global__ void __launch_bounds__(256) restr_pass_kernel(PassArgs a)
+__global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
 {
     constexpr int SR = 4 / CPT;        // warps sharing one row
     constexpr int RSTEP = 8 / SR;      // row step of one warp
     constexpr int RPW = T / RSTEP;     // rows per warp
+    constexpr int NPR = CPT / 2;       // column pairs per thread
+    // indexed directly (no integer round trip) so reads stay shared-memory loads
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ __align__(8) uint64_t full[kPassStagesMax];
+    __shared__ int2 sIJ[kPassStagesMax];
     __shared__ float red[32];
     __shared__ int scan[33];
     __shared__ int base_sh;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int seg = warp % SR, row0 = warp / SR;
-    const int2 IJ = a.wtiles[blockIdx.x];
-    const int i0 = IJ.x * T, j0 = IJ.y * T;
-    const float *wt = a.w + (size_t)blockIdx.x * T * T;
-    const int col0 = seg * 32 * CPT + lane * CPT;
 
-    float v[RPW][CPT];
-#pragma unroll
-    for (int r = 0; r < RPW; ++r) {
-        const float *src = wt + (size_t)(row0 + r * RSTEP) * T + col0;
-        if (CPT == 4) {
-            const float4 t = __ldcs(reinterpret_cast<const float4 *>(src));
-            v[r][0] = t.x; v[r][CPT > 1 ? 1 : 0] = t.y; v[r][CPT > 2 ? 2 : 0] = t.z; v[r][CPT > 3 ? 3 : 0] = t.w;
-        } else if (CPT == 2) {
-            const float2 t = __ldcs(reinterpret_cast<const float2 *>(src));
-            v[r][0] = t.x; v[r][CPT > 1 ? 1 : 0] = t.y;
-        } else {
-            v[r][0] = __ldcs(src);
-        }
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int seg = warp % SR, row0 = warp / SR;
+    const int col0 = seg * 32 * CPT + lane * CPT;
+    const int KY = a.KY, S = a.stages;
+    const uint32_t wbytes = T * T * 4, ybytes = T * KY * 4, sbytes = wbytes + 2 * ybytes;
+    const int nmine = blockIdx.x < (unsigned)a.ntiles ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) tc::mbar_init(&full[s], 1);
+        tc::fence_mbar_init();
     }
-    float yj[CPT][K];
-#pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-        const float *yr = a.Y + (size_t)(j0 + col0 + q) * a.KY;
-#pragma unroll
-        for (int c = 0; c < K; ++c) yj[q][c] = __ldg(yr + c);
-    }
-    float mymin = INFINITY;
-#pragma unroll
-    for (int r = 0; r < RPW; ++r) {
-        const float *yr = a.Y + (size_t)(i0 + row0 + r * RSTEP) * a.KY;
-        float yi[K];
-#pragma unroll
-        for (int c = 0; c < K; ++c) yi[c] = __ldg(yr + c);
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            float s = 0.f;
-#pragma unroll
-            for (int c = 0; c < K; ++c) {
-                const float e = yi[c] - yj[q][c];
-                s = fmaf(e, e, s);
-            }
-            v[r][q] = s * v[r][q];
-            mymin = fminf(mymin, v[r][q]);
-        }
-    }
-    const float bmin = block_min(mymin, red);
-    float U = load_pos_float(&a.st->seed_ub);
-    if (bmin < INFINITY) {
-        const float ub = cert_upper(sqrtf(bmin), a.cert);
-        if (threadIdx.x == 0) atomic_min_pos_float(&a.st->run_ub1, ub);
-        U = fminf(U, ub);
-    }
-    U = fminf(U, load_pos_float(&a.st->run_ub1));
-    const float th = cert_emit_threshold(U, a.cert);
-    const float th2 = th * th * 1.000001f;
-    int cnt = 0;
-#pragma unroll
-    for (int r = 0; r < RPW; ++r)
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) cnt += v[r][q] <= th2 ? 1 : 0;
-    int total;
-    const int off = block_exclusive_scan(cnt, scan, &total);
-    if (total == 0) return;
-    if (threadIdx.x == 0) base_sh = (int)atomicAdd((unsigned int *)&a.st->cnt1, (unsigned int)total);
     __syncthreads();
-    long long pos = (long long)(unsigned int)base_sh + off;
+    int issued = 0;
+    auto issue = [&](int it) {
+        const int s = it % S;
+        const int t = blockIdx.x + it * gridDim.x;
+        const int2 IJ = a.wtiles[t];
+        sIJ[s] = IJ;
+        unsigned char *base = sm + (size_t)s * sbytes;
+        tc::mbar_expect_tx(&full[s], sbytes);
+        tc::bulk_g2s(base, a.w + (size_t)t * T * T, wbytes, &full[s]);
+        tc::bulk_g2s(base + wbytes, a.Y + (size_t)IJ.x * T * KY, ybytes, &full[s]);
+        tc::bulk_g2s(base + wbytes + ybytes, a.Y + (size_t)IJ.y * T * KY, ybytes, &full[s]);
+    };
+    if (tid == 0)
+        for (; issued < S && issued < nmine; ++issued) issue(issued);
+
+    const float seed = load_pos_float(&a.st->seed_ub);
+    float ublock = INFINITY;
+    for (int it = 0; it < nmine; ++it) {
+        const int s = it % S;
+        const bool ok = tc::mbar_wait_bounded(&full[s], (it / S) & 1, 4000000000ll);
+        if (!__syncthreads_and(ok ? 1 : 0)) {
+            if (tid == 0) atomicOr(&a.st->status, ST_TIMEOUT);
+            break;
+        }
+        const float gnow = load_pos_float(&a.st->run_ub1);  // consumed after the tile
+        const int2 IJ = sIJ[s];
+        const float *ws = reinterpret_cast<const float *>(sm + (size_t)s * sbytes);
+        const float *yI = ws + T * T;
+        const float *yJ = yI + T * KY;
+
+        float v[RPW][CPT];
+        float mymin = INFINITY;
+        if (NPR > 0) {
+            uint64_t yj2[NPR > 0 ? NPR : 1][K];
 #pragma unroll
-    for (int r = 0; r < RPW; ++r)
+            for (int p = 0; p < NPR; ++p)
 #pragma unroll
-        for (int q = 0; q < CPT; ++q)
-            if (v[r][q] <= th2) {
-                if (pos < a.cap) a.cand[pos] = make_int2(i0 + row0 + r * RSTEP, j0 + col0 + q);
-                else atomicOr(&a.st->status, ST_OVERFLOW);
-                ++pos;
+                for (int c = 0; c < K; ++c)
+                    yj2[p][c] = tc::pk2(yJ[(col0 + 2 * p) * KY + c], yJ[(col0 + 2 * p + 1) * KY + c]);
+#pragma unroll
+            for (int r = 0; r < RPW; ++r) {
+                const int row = row0 + r * RSTEP;
+                const float *yi = yI + row * KY;
+                const float *wr = ws + row * T + col0;
+                uint64_t s2[NPR > 0 ? NPR : 1];
+#pragma unroll
+                for (int p = 0; p < NPR; ++p) s2[p] = 0ull;
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    const float yc = yi[c];
+                    const uint64_t yy = tc::pk2(yc, yc);
+#pragma unroll
+                    for (int p = 0; p < NPR; ++p) {
+                        const uint64_t e = tc::sub2(yy, yj2[p][c]);
+                        s2[p] = tc::fma2(e, e, s2[p]);
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < NPR; ++p) {
+                    const float2 wv = *reinterpret_cast<const float2 *>(wr + 2 * p);
+                    const float2 q = tc::upk2(tc::mul2(s2[p], tc::pk2(wv.x, wv.y)));
+                    v[r][(2 * p) % CPT] = q.x;
+                    v[r][(2 * p + 1) % CPT] = q.y;
+                    mymin = fminf(mymin, fminf(q.x, q.y));
+                }
             }
+        } else {
+            float yj[K];
+#pragma unroll
+            for (int c = 0; c < K; ++c) yj[c] = yJ[col0 * KY + c];
+#pragma unroll
+            for (int r = 0; r < RPW; ++r) {
+                const int row = row0 + r * RSTEP;
+                const float *yi = yI + row * KY;
+                float sacc = 0.f;
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    const float e = yi[c] - yj[c];
+                    sacc = fmaf(e, e, sacc);
+                }
+                v[r][0] = sacc * ws[row * T + col0];
+                mymin = fminf(mymin, v[r][0]);
+            }
+        }
+        const float bmin = block_min(mymin, red);  // all reads of stage s are done
+        if (tid == 0 && issued < nmine) issue(issued++);
+        float U = fminf(fminf(seed, gnow), ublock);
+        if (bmin < INFINITY) {
+            const float ub = cert_upper(sqrtf(bmin), a.cert);
+            if (tid == 0) atomic_min_pos_float(&a.st->run_ub1, ub);
+            U = fminf(U, ub);
+            ublock = fminf(ublock, ub);
+        }
+        const float th = cert_emit_threshold(U, a.cert);
+        const float th2 = th * th * 1.000001f;
+        int cnt = 0;
+        if (mymin <= th2)
+#pragma unroll
+            for (int r = 0; r < RPW; ++r)
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) cnt += v[r][q] <= th2 ? 1 : 0;
+        int total;
+        const int off = block_exclusive_scan(cnt, scan, &total);
+        if (total == 0) continue;
+        if (tid == 0) base_sh = (int)atomicAdd((unsigned int *)&a.st->cnt1, (unsigned int)total);
+        __syncthreads();
+        if (cnt) {
+            long long pos = (long long)(unsigned int)base_sh + off;
+            const int i0 = IJ.x * T, j0 = IJ.y * T;
+#pragma unroll
+            for (int r = 0; r < RPW; ++r)
+#pragma unroll
+                for (int q = 0; q < CPT; ++q)
+                    if (v[r][q] <= th2) {
+                        if (pos < a.cap) a.cand[pos] = make_int2(i0 + row0 + r * RSTEP, j0 + col0 + q);
+                        else atomicOr(&a.st->status, ST_OVERFLOW);
+                        ++pos;
+                    }
+        }
+    }
+    // no copy of ours may still be in flight when the block exits
+    if (tid == 0)
+        for (int it = issued > S ? issued - S : 0; it < issued; ++it)
+            tc::mbar_wait_bounded(&full[it % S], (it / S) & 1, 4000000000ll);
 }
 
 // ------------------------------------------- explicit-difference recheck ---
@@ -353,9 +435,14 @@ constexpr int EPW = 4;  // entries per warp per round
 
 // Re-evaluates the pass's candidates and the near pairs from explicit FP32
 // differences (error model of plain.cu), one warp per pair, and emits the
-// pairs that can still be the argmin for the FP64 tier.
+// pairs that can still be the argmin for the FP64 tier.  A warp handles EPW
+// pairs per round with their loads interleaved, so a round costs one memory
+// latency; the EPW*(K+1) warp sums are reduced together.  K is the compute
+// width (k, or k rounded up; U32's pad columns are zero).
+template <int K>
 __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
 {
+    constexpr int KU = (K + 3) / 4 * 4;
     __shared__ float red[32];
     __shared__ int scan[33];
     __shared__ int base_sh;
@@ -363,58 +450,60 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
     unsigned int c1 = (unsigned int)a.st->cnt1;
     if (c1 > a.cap1) c1 = a.cap1;
     const long long total = (long long)c1 + a.n_near;
+    const float seed = load_pos_float(&a.st->seed_ub);
     for (long long base = (long long)blockIdx.x * 8 * EPW; base < total;
          base += (long long)gridDim.x * 8 * EPW) {
-        float rr[EPW];
-        int code[EPW];
         int2 pr[EPW];
-        float mymin = INFINITY;
+        bool valid[EPW];
 #pragma unroll
         for (int e = 0; e < EPW; ++e) {
             const long long idx = base + warp * EPW + e;
-            code[e] = 0;
-            rr[e] = INFINITY;
-            pr[e] = make_int2(0, 0);
-            if (idx >= total) continue;
-            const int2 ij = idx < c1 ? a.cand1[idx] : a.near[idx - c1];
-            pr[e] = ij;
-            const float *xi = a.X + (size_t)ij.x * a.n;
-            const float *xj = a.X + (size_t)ij.y * a.n;
-            float dd = 0.f, z[kMaxK];
+            valid[e] = idx < total;
+            pr[e] = valid[e] ? (idx < c1 ? a.cand1[idx] : a.near[idx - c1]) : make_int2(0, 0);
+        }
+        float acc[EPW * (K + 1)];
 #pragma unroll
-            for (int c = 0; c < kMaxK; ++c) z[c] = 0.f;
-            for (int l = lane; l < a.n; l += 32) {
-                const float D = xi[l] - xj[l];
-                dd = fmaf(D, D, dd);
-                const float *ur = a.U32 + (size_t)l * a.KP;
+        for (int q = 0; q < EPW * (K + 1); ++q) acc[q] = 0.f;
+#pragma unroll 2
+        for (int l = lane; l < a.n; l += 32) {
+            float u[KU];
 #pragma unroll
-                for (int c = 0; c < kMaxK; ++c)
-                    if (c < a.k) z[c] = fmaf(ur[c], D, z[c]);
+            for (int c = 0; c < KU; c += 4) {
+                const float4 t = *reinterpret_cast<const float4 *>(a.U32 + (size_t)l * a.KP + c);
+                u[c] = t.x; u[c + 1] = t.y; u[c + 2] = t.z; u[c + 3] = t.w;
             }
-            dd = warp_sumf(dd);
-            float zz = 0.f;
 #pragma unroll
-            for (int c = 0; c < kMaxK; ++c)
-                if (c < a.k) {
-                    const float zc = warp_sumf(z[c]);
-                    zz = fmaf(zc, zc, zz);
-                }
-            if (dd < 1e-30f) {
-                code[e] = 2;  // too short for FP32: always passed on
-            } else {
-                code[e] = 1;
-                rr[e] = sqrtf(zz / dd);
-                mymin = fminf(mymin, rr[e]);
+            for (int e = 0; e < EPW; ++e) {
+                const float D = a.X[(size_t)pr[e].x * a.n + l] - a.X[(size_t)pr[e].y * a.n + l];
+                acc[e * (K + 1) + K] = fmaf(D, D, acc[e * (K + 1) + K]);
+#pragma unroll
+                for (int c = 0; c < K; ++c) acc[e * (K + 1) + c] = fmaf(u[c], D, acc[e * (K + 1) + c]);
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < EPW * (K + 1); ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        float rr[EPW];
+        int code[EPW];
+        float mymin = INFINITY;
+#pragma unroll
+        for (int e = 0; e < EPW; ++e) {
+            const float dd = acc[e * (K + 1) + K];
+            float zz = 0.f;
+#pragma unroll
+            for (int c = 0; c < K; ++c) zz = fmaf(acc[e * (K + 1) + c], acc[e * (K + 1) + c], zz);
+            code[e] = !valid[e] ? 0 : (dd < 1e-30f ? 2 : 1);  // 2: too short for FP32
+            rr[e] = code[e] == 1 ? sqrtf(zz / dd) : INFINITY;
+            mymin = fminf(mymin, rr[e]);
+        }
         const float bmin = block_min(mymin, red);
-        float U = load_pos_float(&a.st->seed_ub);
+        float U = fminf(seed, load_pos_float(&a.st->run_ub2));
         if (bmin < INFINITY) {
             const float ub = cert_upper(bmin, a.cert);
             if (threadIdx.x == 0) atomic_min_pos_float(&a.st->run_ub2, ub);
             U = fminf(U, ub);
         }
-        U = fminf(U, load_pos_float(&a.st->run_ub2));
         const float th = cert_emit_threshold(U, a.cert);
         int cnt = 0;
         if (lane == 0)
@@ -437,6 +526,32 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
         }
         __syncthreads();
     }
+}
+
+template <int K>
+cudaError_t launch_expl_k(const ExplArgs &x, int grid, cudaStream_t s)
+{
+    explicit_recheck_kernel<K><<<grid, 256, 0, s>>>(x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_explicit(const ExplArgs &x, int grid, cudaStream_t s)
+{
+    switch (x.k) {
+    case 1: return launch_expl_k<1>(x, grid, s);
+    case 2: return launch_expl_k<2>(x, grid, s);
+    case 3: return launch_expl_k<3>(x, grid, s);
+    case 4: return launch_expl_k<4>(x, grid, s);
+    case 5: return launch_expl_k<5>(x, grid, s);
+    case 6: return launch_expl_k<6>(x, grid, s);
+    case 7: return launch_expl_k<7>(x, grid, s);
+    case 8: return launch_expl_k<8>(x, grid, s);
+    default: break;
+    }
+    if (x.k <= 12) return launch_expl_k<12>(x, grid, s);
+    if (x.k <= 16) return launch_expl_k<16>(x, grid, s);
+    if (x.k <= 24) return launch_expl_k<24>(x, grid, s);
+    return launch_expl_k<32>(x, grid, s);
 }
 
 // -------------------------------------------------------------- host side --
@@ -558,11 +673,37 @@ sap_status classify(sap_handle h, int k)
     return SAP_OK;
 }
 
+size_t pass_smem_bytes(int KY, int stages) { return (size_t)stages * pass_stage_bytes(KY); }
+
+int pass_pick_stages(int KY)
+{
+    int s = kPassStagesMax;
+    while (s > 2 && pass_smem_bytes(KY, s) > 222 * 1024) --s;
+    return s;
+}
+
 template <int K, int CPT>
 cudaError_t launch_pass_k(const PassArgs &a, int grid, cudaStream_t s)
 {
-    restr_pass_kernel<K, CPT><<<grid, 256, 0, s>>>(a);
+    restr_pass_kernel<K, CPT><<<grid, kPassThreads, pass_smem_bytes(a.KY, a.stages), s>>>(a);
     return cudaGetLastError();
+}
+
+template <int K, int CPT>
+cudaError_t config_pass_k()
+{
+    return cudaFuncSetAttribute(restr_pass_kernel<K, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                224 * 1024);
+}
+
+cudaError_t configure_pass_kernels()
+{
+    cudaError_t e = cudaSuccess;
+    auto f = [&](cudaError_t x) { if (x != cudaSuccess) e = x; };
+    f(config_pass_k<1, 4>()); f(config_pass_k<2, 4>()); f(config_pass_k<3, 4>()); f(config_pass_k<4, 4>());
+    f(config_pass_k<5, 4>()); f(config_pass_k<6, 4>()); f(config_pass_k<7, 4>()); f(config_pass_k<8, 4>());
+    f(config_pass_k<12, 2>()); f(config_pass_k<16, 2>()); f(config_pass_k<24, 1>()); f(config_pass_k<32, 1>());
+    return e;
 }
 
 // Columns of Y the pass reads per row: k itself up to 8, else k rounded up
@@ -625,6 +766,7 @@ sap_status restructured_prepare(sap_handle h)
         r.near_cap = (unsigned int)std::min<long long>(P + 64, 1ll << 26);
         RCK(cudaMalloc(&r.near, (size_t)r.near_cap * sizeof(int2)));
         RCK(gemm_configure());
+        RCK(configure_pass_kernels());
     }
     const int sms = handle_sms(h);
     colmean_kernel<<<(n + 127) / 128, 128, 0, s>>>(X, N, n, r.center);
@@ -677,7 +819,7 @@ sap_status restructured_basis_alloc(sap_handle h)
     dfree(r.Ulo);
     dfree(r.Y);
     r.KPG = (k + 15) / 16 * 16;
-    r.KY = (pass_width(k) + 3) / 4 * 4;   // <= KPG; columns >= k are zero
+    r.KY = padded_stride(k);   // <= KPG; columns >= k are zero
     RCK(cudaMalloc(&r.Uhi, (size_t)r.KPG * r.NP * 2));
     RCK(cudaMalloc(&r.Ulo, (size_t)r.KPG * r.NP * 2));
     RCK(cudaMalloc(&r.Y, (size_t)r.Npad * r.KY * sizeof(float)));
@@ -757,15 +899,17 @@ sap_status restructured_enqueue(sap_handle h, double alpha)
         PassArgs p;
         p.w = r.w;
         p.wtiles = r.wtiles;
+        p.ntiles = r.nwtiles;
         p.Y = r.Y;
         p.KY = r.KY;
+        p.stages = pass_pick_stages(r.KY);
         p.cert = cert_pass(n, k, r.b_cap);
         p.st = st;
         p.cand = handle_cand1(h);
         p.cap = handle_cap(h);
         handle_count_launch(h, 1, &ea, &eb);
         if (ea) cudaEventRecord(ea, s);
-        RCK(launch_pass(p, k, r.nwtiles, s));
+        RCK(launch_pass(p, k, std::min(r.nwtiles, handle_sms(h)), s));
         if (eb) cudaEventRecord(eb, s);
         handle_push_timing(h, 1, ea, eb);
     }
@@ -787,8 +931,7 @@ sap_status restructured_enqueue(sap_handle h, double alpha)
         x.cap2 = handle_cap(h);
         handle_count_launch(h, 3, &ea, &eb);
         if (ea) cudaEventRecord(ea, s);
-        explicit_recheck_kernel<<<2 * handle_sms(h), 256, 0, s>>>(x);
-        RCK(cudaGetLastError());
+        RCK(launch_explicit(x, 2 * handle_sms(h), s));
         if (eb) cudaEventRecord(eb, s);
         handle_push_timing(h, 3, ea, eb);
     }

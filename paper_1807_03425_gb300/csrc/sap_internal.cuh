@@ -27,6 +27,15 @@ constexpr int kWatch = 8;          // recent argmin pairs re-evaluated as seeds
 constexpr int kTile = 128;         // edge of a w tile (restructured form)
 constexpr int kRecheckBlocks = 304; // FP64 recheck grid (2 x 152 SMs)
 
+// Compute width of the kernels templated on k: k itself up to 8, else k
+// rounded up to 12, 16, 24 or 32.  Row strides of Y and of the FP32 basis
+// are this width rounded up to 4, with zero pad columns.
+__host__ __device__ inline int padded_k(int k)
+{
+    return k <= 8 ? k : k <= 12 ? 12 : k <= 16 ? 16 : k <= 24 ? 24 : 32;
+}
+__host__ __device__ inline int padded_stride(int k) { return (padded_k(k) + 3) / 4 * 4; }
+
 enum StatusBits : int {
     ST_NO_SECANT = 1,
     ST_TIMEOUT = 2,
@@ -46,7 +55,7 @@ struct ProbState {
     int watch_pos;          // next ring slot
     int last_cnt1, last_cnt2;
     int hist_cap;           // capacity of the history arrays
-    int pad0;
+    unsigned int ticket;    // blocks of the select/update launch that finished
     int2 watch[kWatch];
     double last_r;          // result of the latest evaluation
     int last_i, last_j;
@@ -198,46 +207,36 @@ struct PlainArgsF64 {
 cudaError_t launch_plain_f32(const PlainArgsF32 &a, cudaStream_t s);
 cudaError_t launch_plain_f64(const PlainArgsF64 &a, cudaStream_t s);
 
-// FP64 recheck of a candidate list; count read from st->cnt1 (which == 1) or
-// st->cnt2 (which == 2).
-struct RecheckArgs {
+// FP64 recheck of a candidate list (count read from st->cnt1 when which == 1,
+// st->cnt2 when which == 2) fused with the basis update, which the last
+// block to finish performs (select_update.cu).
+struct SelectUpdateArgs {
     const void *X;         // float or double, N x n
-    int x_is_f64;
-    int N, n;
-    const double *U64;     // n x k column-major
-    int k;
-    double eps2;
-    const int2 *list;
-    unsigned int cap;      // capacity of list
-    int which;
-    const ProbState *st;
-    Partial *partials;     // kRecheckBlocks entries
-};
-cudaError_t launch_recheck_fp64(const RecheckArgs &a, cudaStream_t s);
-
-struct UpdateArgs {
-    const Partial *partials;
-    int nparts;
-    const void *X;
     int x_is_f64;
     int N, n;
     double *U64;           // n x k column-major, updated in place
     float *U32;            // n x KP row-major, written
     int KP;
     void *Uhi, *Ulo;       // tensor-core operands (KPG x NP, 16-bit), or null
-    int KPG, NP;
+    int NP;
     int split_bf16;        // 0: FP16 split, 1: BF16 split
     float split_scale;     // multiplier of the low part (2^11 FP16, 2^8 BF16)
     int k;
     double alpha;
     int mode;              // 0 literal, 1 angle
     int eval_only;
-    double *work;          // (k + 2) * n doubles of scratch
+    double eps2;
+    const int2 *list;
+    unsigned int cap;
+    int which;
+    Partial *partials;     // grid entries
+    int grid;
+    double *work;          // (kMaxK + 1) * n doubles of scratch
     ProbState *st;
     double *hist;          // hist_cap entries
     int2 *argmin;          // hist_cap entries
     Cert seed_cert;        // error model of the seed evaluation
 };
-cudaError_t launch_update(const UpdateArgs &a, cudaStream_t s);
+cudaError_t launch_select_update(const SelectUpdateArgs &a, cudaStream_t s);
 
 } // namespace sap

@@ -35,8 +35,9 @@
  *    FP64 evaluation on the device from explicit differences; faster
  *    low-precision tiers only select candidates, under certified error
  *    bounds, so both paths return the same pair as an FP64 evaluation of all
- *    pairs (up to FP64 rounding on exact ties).  The basis update and its
- *    re-orthonormalisation are FP64.
+ *    pairs (up to FP64 rounding on exact ties).  The pivot, Gram-Schmidt and
+ *    rotation of the update run in the data's precision (FP32 or FP64); the
+ *    re-orthonormalisation that follows is FP64.
  */
 #ifndef SAP_H
 #define SAP_H

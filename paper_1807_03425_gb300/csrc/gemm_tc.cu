@@ -129,10 +129,11 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
             tc::tmem_ld8(lane_base + c0, d1);
             tc::tmem_ld8(lane_base + KPG + c0, d2);
             if (row < a.Npad) {
-                float *yr = a.Y + (size_t)row * a.KY;
+                // component-major (Y^T): consecutive lanes write consecutive rows
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    if (c0 + q < a.KY) yr[c0 + q] = fmaf(d2[q], a.lo_scale, d1[q]) * a.out_scale;
+                    if (c0 + q < a.KY)
+                        a.Y[(size_t)(c0 + q) * a.Npad + row] = fmaf(d2[q], a.lo_scale, d1[q]) * a.out_scale;
             }
         }
     } else if (threadIdx.x == 0) {

@@ -9,8 +9,8 @@ namespace sap {
 struct GemmArgs {
     CUtensorMap ta_hi, ta_lo;   // X split parts: Npad x NP, 16-bit, box 64 x 128
     CUtensorMap tb_hi, tb_lo;   // U split parts: KPG x NP, 16-bit, box 64 x KPG
-    float *Y;                   // Npad x KY, FP32
-    int KY;                     // columns of Y written (multiple of 4, <= KPG)
+    float *Y;                   // Y^T: KY x Npad, FP32, component-major
+    int KY;                     // components written (multiple of 4, <= KPG)
     int Npad;                   // rows (multiple of 128)
     int nkb;                    // K blocks of 64
     int KPG;                    // MMA N: multiple of 16, 16..256

@@ -235,8 +235,9 @@ struct PassArgs {
     const float *w;
     const int2 *wtiles;
     int ntiles;
-    const float *Y;
+    const float *Y;   // Y^T, KY x Npad
     int KY;
+    int Npad;
     int stages;
     Cert cert;
     ProbState *st;
@@ -297,8 +298,12 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
         unsigned char *base = sm + (size_t)s * sbytes;
         tc::mbar_expect_tx(&full[s], sbytes);
         tc::bulk_g2s(base, a.w + (size_t)t * T * T, wbytes, &full[s]);
-        tc::bulk_g2s(base + wbytes, a.Y + (size_t)IJ.x * T * KY, ybytes, &full[s]);
-        tc::bulk_g2s(base + wbytes + ybytes, a.Y + (size_t)IJ.y * T * KY, ybytes, &full[s]);
+        // Y^T is component-major: one 512-byte row segment per component and side
+        for (int c = 0; c < KY; ++c) {
+            tc::bulk_g2s(base + wbytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.x * T, T * 4, &full[s]);
+            tc::bulk_g2s(base + wbytes + ybytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.y * T, T * 4,
+                         &full[s]);
+        }
     };
     if (tid == 0)
         for (; issued < S && issued < nmine; ++issued) issue(issued);
@@ -315,29 +320,36 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
         const float gnow = load_pos_float(&a.st->run_ub1);  // consumed after the tile
         const int2 IJ = sIJ[s];
         const float *ws = reinterpret_cast<const float *>(sm + (size_t)s * sbytes);
-        const float *yI = ws + T * T;
+        const float *yI = ws + T * T;   // yI[c * T + a]: component c of point I*T + a
         const float *yJ = yI + T * KY;
 
         float v[RPW][CPT];
         float mymin = INFINITY;
         if (NPR > 0) {
+            // this thread's CPT columns of every component: one conflict-free
+            // 8- or 16-byte load per component
             uint64_t yj2[NPR > 0 ? NPR : 1][K];
 #pragma unroll
-            for (int p = 0; p < NPR; ++p)
-#pragma unroll
-                for (int c = 0; c < K; ++c)
-                    yj2[p][c] = tc::pk2(yJ[(col0 + 2 * p) * KY + c], yJ[(col0 + 2 * p + 1) * KY + c]);
+            for (int c = 0; c < K; ++c) {
+                if (CPT == 4) {
+                    const float4 t = *reinterpret_cast<const float4 *>(yJ + c * T + col0);
+                    yj2[0][c] = tc::pk2(t.x, t.y);
+                    yj2[NPR > 1 ? 1 : 0][c] = tc::pk2(t.z, t.w);
+                } else {
+                    const float2 t = *reinterpret_cast<const float2 *>(yJ + c * T + col0);
+                    yj2[0][c] = tc::pk2(t.x, t.y);
+                }
+            }
 #pragma unroll
             for (int r = 0; r < RPW; ++r) {
                 const int row = row0 + r * RSTEP;
-                const float *yi = yI + row * KY;
                 const float *wr = ws + row * T + col0;
                 uint64_t s2[NPR > 0 ? NPR : 1];
 #pragma unroll
                 for (int p = 0; p < NPR; ++p) s2[p] = 0ull;
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
-                    const float yc = yi[c];
+                    const float yc = yI[c * T + row];  // broadcast
                     const uint64_t yy = tc::pk2(yc, yc);
 #pragma unroll
                     for (int p = 0; p < NPR; ++p) {
@@ -345,10 +357,17 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                         s2[p] = tc::fma2(e, e, s2[p]);
                     }
                 }
+                float wv[CPT];
+                if (CPT == 4) {
+                    const float4 t = *reinterpret_cast<const float4 *>(wr);
+                    wv[0] = t.x; wv[1 % CPT] = t.y; wv[2 % CPT] = t.z; wv[3 % CPT] = t.w;
+                } else {
+                    const float2 t = *reinterpret_cast<const float2 *>(wr);
+                    wv[0] = t.x; wv[1 % CPT] = t.y;
+                }
 #pragma unroll
                 for (int p = 0; p < NPR; ++p) {
-                    const float2 wv = *reinterpret_cast<const float2 *>(wr + 2 * p);
-                    const float2 q = tc::upk2(tc::mul2(s2[p], tc::pk2(wv.x, wv.y)));
+                    const float2 q = tc::upk2(tc::mul2(s2[p], tc::pk2(wv[2 * p], wv[(2 * p + 1) % CPT])));
                     v[r][(2 * p) % CPT] = q.x;
                     v[r][(2 * p + 1) % CPT] = q.y;
                     mymin = fminf(mymin, fminf(q.x, q.y));
@@ -357,15 +376,14 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
         } else {
             float yj[K];
 #pragma unroll
-            for (int c = 0; c < K; ++c) yj[c] = yJ[col0 * KY + c];
+            for (int c = 0; c < K; ++c) yj[c] = yJ[c * T + col0];
 #pragma unroll
             for (int r = 0; r < RPW; ++r) {
                 const int row = row0 + r * RSTEP;
-                const float *yi = yI + row * KY;
                 float sacc = 0.f;
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
-                    const float e = yi[c] - yj[c];
+                    const float e = yI[c * T + row] - yj[c];
                     sacc = fmaf(e, e, sacc);
                 }
                 v[r][0] = sacc * ws[row * T + col0];
@@ -588,6 +606,14 @@ bool make_map(CUtensorMap *m, void *base, bool bf16, uint64_t inner, uint64_t ou
     return fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims,
               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+__global__ void transpose_y_kernel(const float *Yt, int Npad, int N, int k, float *out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * k) return;
+    const int i = e / k, c = e % k;
+    out[e] = Yt[(size_t)c * Npad + i];
 }
 
 template <typename T_>
@@ -902,6 +928,7 @@ sap_status restructured_enqueue(sap_handle h, double alpha)
         p.ntiles = r.nwtiles;
         p.Y = r.Y;
         p.KY = r.KY;
+        p.Npad = r.Npad;
         p.stages = pass_pick_stages(r.KY);
         p.cert = cert_pass(n, k, r.b_cap);
         p.st = st;
@@ -961,10 +988,18 @@ sap_status restructured_project(sap_handle h, float *Y_out, int out_is_device)
     RCK(launch_gemm_y(g, s));
     if (eb) cudaEventRecord(eb, s);
     handle_push_timing(h, 0, ea, eb);
-    RCK(cudaMemcpy2DAsync(Y_out, (size_t)k * sizeof(float), r.Y, (size_t)r.KY * sizeof(float),
-                          (size_t)k * sizeof(float), N,
-                          out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-    RCK(cudaStreamSynchronize(s));
+    // Y^T (component-major) -> N x k row-major
+    if (out_is_device) {
+        transpose_y_kernel<<<(N * k + 255) / 256, 256, 0, s>>>(r.Y, r.Npad, N, k, Y_out);
+        RCK(cudaGetLastError());
+        RCK(cudaStreamSynchronize(s));
+    } else {
+        std::vector<float> yt((size_t)k * r.Npad);
+        RCK(cudaMemcpyAsync(yt.data(), r.Y, yt.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+        RCK(cudaStreamSynchronize(s));
+        for (int i = 0; i < N; ++i)
+            for (int c = 0; c < k; ++c) Y_out[(size_t)i * k + c] = yt[(size_t)c * r.Npad + i];
+    }
     return SAP_OK;
 }
 

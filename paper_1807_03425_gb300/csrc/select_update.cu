@@ -75,7 +75,7 @@ __device__ __forceinline__ void block_sum_multi(V (&v)[M], V *scratch /* NW*M */
     __syncthreads();
 }
 
-template <int K>
+template <typename WT, int K>
 struct Shared {
     double red_d[NW * (K + 1)];
     float red_f[NW * (K + 1)];
@@ -83,10 +83,12 @@ struct Shared {
     int last;
     int alive0;
     double cvec[K + 1];            // U^T D and |D|^2 (data precision, widened)
-    double cw[K];                  // c = U^T s
-    double B[K][K];                // coefficient MGS result (column m = q_m), then R^-1
+    WT cw[K];                      // c = U^T s
+    WT Bw[K][K];                   // coefficient MGS result, column m = q_m
+    WT av, asd, dnorm, nd2;        // direction coefficients, |D|, |dir|^2
     double G[K][K];                // Gram matrix, then R (upper)
-    double av, asd, dnorm, nd2;    // direction coefficients, |D|, |dir|^2
+    double Rd[K];                  // 1 / R_jj
+    double Ri[K][K];               // R^-1 (upper)
     float seed[NW];
 };
 
@@ -94,7 +96,7 @@ template <typename TX, int K>
 __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
 {
     extern __shared__ double dyn[];
-    __shared__ Shared<K> sh;
+    __shared__ Shared<TX, K> sh;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int n = a.n;
     const int kk = a.k;            // actual k (<= K)
@@ -145,80 +147,77 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
     }
 
     // ---------------- phase 2: argmin, record, update ----------------------
-    Partial b = {INFINITY, 0x7fffffff, 0x7fffffff};
-    for (int p = tid; p < (int)gridDim.x; p += SB) {
-        const volatile Partial *vp = &a.partials[p];
-        const Partial q = {vp->r, vp->i, vp->j};
-        if (better(q.r, q.i, q.j, b.r, b.i, b.j)) b = q;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        Partial q;
-        q.r = __shfl_xor_sync(0xffffffffu, b.r, o);
-        q.i = __shfl_xor_sync(0xffffffffu, b.i, o);
-        q.j = __shfl_xor_sync(0xffffffffu, b.j, o);
-        if (better(q.r, q.i, q.j, b.r, b.i, b.j)) b = q;
-    }
-    if (lane == 0) sh.wb[w] = b;
-    __syncthreads();
-    if (tid == 0) {
-        for (int q = 1; q < NW; ++q)
-            if (better(sh.wb[q].r, sh.wb[q].i, sh.wb[q].j, b.r, b.i, b.j)) b = sh.wb[q];
-        sh.wb[0] = b;
-        const int it = st->iter;
-        const bool none = !(b.r < INFINITY);
-        if (none) atomicOr(&st->status, ST_NO_SECANT);
-        if (it < st->hist_cap) {
-            a.hist[it] = none ? __longlong_as_double(0x7ff8000000000000ll) : b.r;
-            a.argmin[it] = none ? make_int2(-1, -1) : make_int2(b.i, b.j);
+    using WT = TX;  // working precision of the pivot, MGS and rotation
+    if (w == 0) {
+        Partial b = {INFINITY, 0x7fffffff, 0x7fffffff};
+        for (int p = lane; p < (int)gridDim.x; p += 32) {
+            const volatile Partial *vp = &a.partials[p];
+            const Partial q = {vp->r, vp->i, vp->j};
+            if (better(q.r, q.i, q.j, b.r, b.i, b.j)) b = q;
         }
-        st->iter = it + 1;
-        st->last_r = b.r;
-        st->last_i = none ? -1 : b.i;
-        st->last_j = none ? -1 : b.j;
-        st->last_cnt1 = st->cnt1;
-        st->last_cnt2 = st->cnt2;
-        st->cnt1 = 0;
-        st->cnt2 = 0;
-        st->ticket = 0;
-        st->run_ub1 = 0x7f800000u;
-        st->run_ub2 = 0x7f800000u;
-        if (!none) {
-            bool present = false;
-            for (int q = 0; q < st->watch_n; ++q)
-                present |= (st->watch[q].x == b.i && st->watch[q].y == b.j);
-            if (!present) {
-                st->watch[st->watch_pos] = make_int2(b.i, b.j);
-                st->watch_pos = (st->watch_pos + 1) % kWatch;
-                if (st->watch_n < kWatch) ++st->watch_n;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            Partial q;
+            q.r = __shfl_xor_sync(0xffffffffu, b.r, o);
+            q.i = __shfl_xor_sync(0xffffffffu, b.i, o);
+            q.j = __shfl_xor_sync(0xffffffffu, b.j, o);
+            if (better(q.r, q.i, q.j, b.r, b.i, b.j)) b = q;
+        }
+        if (lane == 0) {
+            sh.wb[0] = b;
+            const int it = st->iter;
+            const bool none = !(b.r < INFINITY);
+            if (none) atomicOr(&st->status, ST_NO_SECANT);
+            if (it < st->hist_cap) {
+                a.hist[it] = none ? __longlong_as_double(0x7ff8000000000000ll) : b.r;
+                a.argmin[it] = none ? make_int2(-1, -1) : make_int2(b.i, b.j);
+            }
+            st->iter = it + 1;
+            st->last_r = b.r;
+            st->last_i = none ? -1 : b.i;
+            st->last_j = none ? -1 : b.j;
+            st->last_cnt1 = st->cnt1;
+            st->last_cnt2 = st->cnt2;
+            st->cnt1 = 0;
+            st->cnt2 = 0;
+            st->ticket = 0;
+            st->run_ub1 = 0x7f800000u;
+            st->run_ub2 = 0x7f800000u;
+            if (!none) {
+                bool present = false;
+                for (int q = 0; q < st->watch_n; ++q)
+                    present |= (st->watch[q].x == b.i && st->watch[q].y == b.j);
+                if (!present) {
+                    st->watch[st->watch_pos] = make_int2(b.i, b.j);
+                    st->watch_pos = (st->watch_pos + 1) % kWatch;
+                    if (st->watch_n < kWatch) ++st->watch_n;
+                }
+                if (a.eval_only)  // the basis stays: the exact minimum bounds the next one
+                    st->seed_ub = __float_as_uint(__double2float_ru(b.r) * 1.000001f);
             }
         }
     }
     __syncthreads();
-    b = sh.wb[0];
-    if (!(b.r < INFINITY)) return;
-    if (a.eval_only) {
-        if (tid == 0) st->seed_ub = __float_as_uint(__double2float_ru(b.r) * 1.000001f);
-        return;
-    }
+    const Partial b = sh.wb[0];
+    if (!(b.r < INFINITY) || a.eval_only) return;
 
-    using WT = TX;  // working precision of steps 2-4
-    const bool in_smem = (size_t)n * (K + 1) * sizeof(double) <= kDynSmem;
-    double *Up = in_smem ? dyn : a.work;           // n x K, the new basis before QR
-    double *Ds = Up + (size_t)n * K;               // n: D = x_i - x_j
+    const bool in_smem = (size_t)n * (K + 1) * sizeof(WT) <= kDynSmem;
+    WT *Up = in_smem ? reinterpret_cast<WT *>(dyn) : reinterpret_cast<WT *>(a.work);  // n x K
+    WT *Ds = Up + (size_t)n * K;                                                       // n
 
-    // 2. D, |D|^2 and U^T D in one reduction
+    // 2. D = x_i - x_j, |D|^2 and U^T D in one multi-value reduction
     {
         WT v[K + 1];
 #pragma unroll
         for (int q = 0; q <= K; ++q) v[q] = 0;
+#pragma unroll 1
         for (int l = tid; l < n; l += SB) {
             const WT D = ld_x<TX>(a.X, (size_t)b.i * n + l) - ld_x<TX>(a.X, (size_t)b.j * n + l);
-            Ds[l] = (double)D;
+            Ds[l] = D;
             v[K] += D * D;
 #pragma unroll
             for (int c = 0; c < K; ++c)
-                if (c < kk) v[c] += (WT)a.U64[(size_t)c * n + l] * D;
+                if (c < kk) v[c] += (sizeof(WT) == 8 ? (WT)a.U64[(size_t)c * n + l] : (WT)a.U32[(size_t)l * a.KP + c]) * D;
         }
         WT *scr = sizeof(WT) == 8 ? (WT *)sh.red_d : (WT *)sh.red_f;
         warp_sum_multi<WT, K + 1>(v);
@@ -234,7 +233,8 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         __syncthreads();
     }
 
-    // 3-4. pivot, coefficient MGS and the rotation coefficients (one thread)
+    // 3-4. pivot, coefficient MGS on [c, e_l (l != t)] and the rotation
+    //      coefficients, in one thread (k x k work)
     if (tid == 0) {
         const WT d = sqrt((WT)sh.cvec[K]);
         WT c[K];
@@ -248,19 +248,15 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         WT cmax = fabs(c[0]);
         for (int q = 1; q < kk; ++q)
             if (fabs(c[q]) > cmax) { cmax = fabs(c[q]); t = q; }
-        // MGS in coefficient space on [c, e_l (l != t)]
         WT Q[K][K];
         int alive[K];
+#pragma unroll 1
         for (int m = 0; m < kk; ++m) {
             WT x[K];
-            if (m == 0) {
+            const int l = (m - 1) < t ? (m - 1) : m;  // list entry m >= 1 is column l
 #pragma unroll
-                for (int q = 0; q < K; ++q) x[q] = c[q];
-            } else {
-                const int l = (m - 1) < t ? (m - 1) : m;  // m-th entry of the list
-#pragma unroll
-                for (int q = 0; q < K; ++q) x[q] = (q == l) ? (WT)1 : (WT)0;
-            }
+            for (int q = 0; q < K; ++q) x[q] = m == 0 ? c[q] : (q == l ? (WT)1 : (WT)0);
+#pragma unroll 1
             for (int p = 0; p < m; ++p) {
                 if (!alive[p]) continue;
                 WT h = 0;
@@ -272,153 +268,158 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             WT nn = 0;
 #pragma unroll
             for (int q = 0; q < K; ++q) nn += x[q] * x[q];
-            const WT nrm = sqrt(nn);
-            alive[m] = nrm > (WT)0;
+            alive[m] = nn > (WT)0;
+            const WT inv = alive[m] ? (WT)1 / sqrt(nn) : (WT)0;
 #pragma unroll
-            for (int q = 0; q < K; ++q) Q[m][q] = alive[m] ? x[q] / nrm : (WT)0;
+            for (int q = 0; q < K; ++q) Q[m][q] = x[q] * inv;
         }
         for (int m = 0; m < kk; ++m)
-            for (int q = 0; q < kk; ++q) sh.B[q][m] = (double)Q[m][q];
-        for (int q = 0; q < K; ++q) sh.cw[q] = (double)c[q];
+            for (int q = 0; q < K; ++q) sh.Bw[q][m] = Q[m][q];
+        for (int q = 0; q < K; ++q) sh.cw[q] = c[q];
         sh.alive0 = alive[0];
-        // direction: av * (U c) + as * s; s = D / d
         const WT al = (WT)a.alpha;
         WT av, as;
-        if (a.mode == 1) {
+        if (a.mode == 1) {  // angle reading
             const WT nv = sqrt(r2);
             const WT ne = sqrt(r2 < (WT)1 ? (WT)1 - r2 : (WT)0);
             av = (nv > 0 ? (1 - al) / nv : (WT)0) - (ne > 0 ? al / ne : (WT)0);
             as = ne > 0 ? al / ne : (WT)0;
-        } else {
+        } else {            // literal reading: (1-a) v + a (s - v)
             av = 1 - 2 * al;
             as = al;
         }
-        sh.av = (double)av;
-        sh.asd = (double)(as / d);  // applied to D
-        sh.dnorm = (double)d;
+        sh.av = av;
+        sh.asd = as / d;  // applied to D = d s
+        sh.dnorm = d;
     }
     __syncthreads();
 
-    // new basis before QR: column 0 = av U c + as s, column m = U q_m
+    // new basis before QR: column 0 = av U c + as s, column m >= 1 = U q_m
     {
-        const WT av = (WT)sh.av, asd = (WT)sh.asd;
-        WT cw[K];
-#pragma unroll
-        for (int c = 0; c < K; ++c) cw[c] = (WT)sh.cw[c];
-        __shared__ WT Bw[K][K];
-        for (int e = tid; e < K * K; e += SB) {
-            const int c = e / K, m = e % K;
-            Bw[c][m] = (c < kk && m < kk) ? (WT)sh.B[c][m] : (WT)0;
-        }
-        __syncthreads();
-        double p0 = 0.0;
+        const WT av = sh.av, asd = sh.asd;
+        WT p0 = 0;
+#pragma unroll 1
         for (int l = tid; l < n; l += SB) {
             WT u[K];
 #pragma unroll
-            for (int c = 0; c < K; ++c) u[c] = c < kk ? (WT)a.U64[(size_t)c * n + l] : (WT)0;
+            for (int c = 0; c < K; ++c)
+                u[c] = c < kk ? (sizeof(WT) == 8 ? (WT)a.U64[(size_t)c * n + l] : (WT)a.U32[(size_t)l * a.KP + c]) : (WT)0;
             WT v0 = 0;
 #pragma unroll
-            for (int c = 0; c < K; ++c) v0 += u[c] * cw[c];
-            const WT d0 = av * v0 + asd * (WT)Ds[l];
-            Up[(size_t)l * K + 0] = (double)d0;
-            p0 += (double)d0 * (double)d0;
+            for (int c = 0; c < K; ++c) v0 += u[c] * sh.cw[c];
+            const WT d0 = av * v0 + asd * Ds[l];
+            Up[(size_t)l * K] = d0;
+            p0 += d0 * d0;
 #pragma unroll
             for (int m = 1; m < K; ++m) {
                 WT s = 0;
 #pragma unroll
-                for (int c = 0; c < K; ++c) s += u[c] * Bw[c][m];
-                Up[(size_t)l * K + m] = (double)s;
+                for (int c = 0; c < K; ++c) s += u[c] * sh.Bw[c][m];
+                Up[(size_t)l * K + m] = s;
             }
         }
-        double pv[1] = {p0};
-        block_sum_multi<double, 1>(pv, sh.red_d, &sh.nd2);
-        const double nd = sqrt(sh.nd2);
+        WT pv[1] = {p0};
+        WT *scr = sizeof(WT) == 8 ? (WT *)sh.red_d : (WT *)sh.red_f;
+        block_sum_multi<WT, 1>(pv, scr, &sh.nd2);
+        const WT nd = sqrt(sh.nd2);
         const bool keep_q1 = sh.alive0 != 0;
+#pragma unroll 1
         for (int l = tid; l < n; l += SB) {
-            if (nd > 0.0) {
+            if (nd > 0) {
                 Up[(size_t)l * K] /= nd;
-            } else if (keep_q1) {
+            } else if (keep_q1) {  // alpha = 1 with s in the span: keep q1
                 WT s = 0;
 #pragma unroll
                 for (int c = 0; c < K; ++c)
-                    if (c < kk) s += (WT)a.U64[(size_t)c * n + l] * Bw[c][0];
-                Up[(size_t)l * K] = (double)s;
-            } else {
+                    if (c < kk)
+                        s += (sizeof(WT) == 8 ? (WT)a.U64[(size_t)c * n + l] : (WT)a.U32[(size_t)l * a.KP + c]) *
+                             sh.Bw[c][0];
+                Up[(size_t)l * K] = s;
+            } else {               // P P^T s = 0: the new column is s
                 Up[(size_t)l * K] = Ds[l] / sh.dnorm;
             }
         }
         __syncthreads();
     }
 
-    // 5. FP64 Cholesky QR: G = Up^T Up (entries spread over warps)
+    // 5. FP64 Cholesky QR of Up: Gram entries spread over the warps
+#pragma unroll 1
     for (int e = w; e < kk * kk; e += NW) {
         const int p = e / kk, q = e % kk;
         if (q < p) continue;
         double s = 0.0;
-        for (int l = lane; l < n; l += 32) s = fma(Up[(size_t)l * K + p], Up[(size_t)l * K + q], s);
+        for (int l = lane; l < n; l += 32) s = fma((double)Up[(size_t)l * K + p], (double)Up[(size_t)l * K + q], s);
         s = warp_sum(s);
         if (lane == 0) sh.G[p][q] = s;
     }
     __syncthreads();
     if (w == 0) {
-        // lane m owns column m of the upper triangle; R overwrites G
+        // right-looking Cholesky G = R^T R on the upper triangle, lane m owns
+        // column m; 1/R_jj from one reciprocal square root per step
+        double rinv_own = 0.0;
+#pragma unroll 1
         for (int j = 0; j < kk; ++j) {
-            double gjj = __shfl_sync(0xffffffffu, lane == j ? sh.G[j][j] : 0.0, j);
-            const double rinv = 1.0 / sqrt(gjj);
+            const double gjj = sh.G[j][j];
+            const double rinv = rsqrt(gjj);
+            if (lane == j) { sh.G[j][j] = gjj * rinv; rinv_own = rinv; }
             if (lane > j && lane < kk) sh.G[j][lane] *= rinv;
-            if (lane == j) sh.G[j][j] = gjj * rinv;
             __syncwarp();
             if (lane > j && lane < kk)
                 for (int p = j + 1; p <= lane; ++p) sh.G[p][lane] = fma(-sh.G[j][p], sh.G[j][lane], sh.G[p][lane]);
             __syncwarp();
         }
-        // R^-1 (upper triangular), column by column: lane m solves R x = e_m
+        if (lane < kk) sh.Rd[lane] = rinv_own;
+        __syncwarp();
+        // R^-1 (upper): lane m solves R x = e_m by back substitution
         if (lane < kk) {
             double x[K];
 #pragma unroll
             for (int q = 0; q < K; ++q) x[q] = 0.0;
+#pragma unroll 1
             for (int i = lane; i >= 0; --i) {
                 double s = (i == lane) ? 1.0 : 0.0;
-                for (int p = i + 1; p <= lane; ++p) s = fma(-sh.G[i][p], x[p < K ? p : 0], s);
-                x[i < K ? i : 0] = s / sh.G[i][i];
+                for (int p = i + 1; p <= lane; ++p) s = fma(-sh.G[i][p], x[p], s);
+                x[i] = s * sh.Rd[i];
             }
-            for (int i = 0; i <= lane; ++i) sh.B[i][lane] = x[i < K ? i : 0];  // B := R^-1
+            for (int i = 0; i <= lane; ++i) sh.Ri[i][lane] = x[i];
         }
     }
     __syncthreads();
 
     // 6. U'' = Up R^-1, written in every form the kernels read
+#pragma unroll 1
     for (int l = tid; l < n; l += SB) {
         double row[K];
 #pragma unroll
-        for (int m = 0; m < K; ++m) row[m] = m < kk ? Up[(size_t)l * K + m] : 0.0;
+        for (int m = 0; m < K; ++m) row[m] = m < kk ? (double)Up[(size_t)l * K + m] : 0.0;
 #pragma unroll
         for (int m = 0; m < K; ++m) {
             if (m >= kk) break;
             double s = 0.0;
 #pragma unroll
             for (int p = 0; p < K; ++p)
-                if (p <= m) s = fma(row[p], sh.B[p][m], s);
+                if (p <= m) s = fma(row[p], sh.Ri[p][m], s);
             a.U64[(size_t)m * n + l] = s;
-            a.U32[(size_t)l * a.KP + m] = (float)s;
+            const float sf = (float)s;
+            a.U32[(size_t)l * a.KP + m] = sf;
             if (a.Uhi) {
+                // hi + lo * 2^-s of the FP32 value (the FP32 rounding adds 2^-24
+                // relative to the split residual)
                 const size_t idx = (size_t)m * a.NP + l;
                 if (a.split_bf16) {
-                    const __nv_bfloat16 h = __double2bfloat16(s);
+                    const __nv_bfloat16 h = __float2bfloat16_rn(sf);
                     static_cast<__nv_bfloat16 *>(a.Uhi)[idx] = h;
                     static_cast<__nv_bfloat16 *>(a.Ulo)[idx] =
-                        __double2bfloat16((s - (double)__bfloat162float(h)) * (double)a.split_scale);
+                        __float2bfloat16_rn((sf - __bfloat162float(h)) * a.split_scale);
                 } else {
-                    const __half h = __double2half(s);
+                    const __half h = __float2half_rn(sf);
                     static_cast<__half *>(a.Uhi)[idx] = h;
-                    static_cast<__half *>(a.Ulo)[idx] =
-                        __double2half((s - (double)__half2float(h)) * (double)a.split_scale);
+                    static_cast<__half *>(a.Ulo)[idx] = __float2half_rn((sf - __half2float(h)) * a.split_scale);
                 }
             }
         }
     }
     __syncthreads();
-
     // seeds: the recent argmin pairs under the new basis
     const int nwatch = st->watch_n;
     if (w < nwatch) {

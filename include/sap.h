@@ -211,6 +211,31 @@ sap_status sap_estimate_dim(sap_handle h, const double *U0, int32_t k_max,
  */
 sap_status sap_project(sap_handle h, float *Y_out, int out_is_device);
 
+/*
+ * The argmin step without any device allocation, for callers that cannot
+ * allocate GPU memory: code running while a stream is captured into a CUDA
+ * graph, code whose device memory belongs to another allocator's pool, or
+ * loops that cannot afford an allocation's synchronisation or failure.  The
+ * paper has no counterpart; it is a deployment variant of sap_min_secant in
+ * the plain form, and returns the same pair and ratio.
+ *
+ * X: device pointer, N x n row-major FP32; U: device pointer, n x k
+ * column-major FP64 with orthonormal columns (not checked); eps: the Sec. VII
+ * threshold (0 for none); cuda_stream: the stream to run on (NULL: the legacy
+ * default stream); i, j, ratio: host outputs (nullable).  Synchronises the
+ * stream.  Limits: 2 <= N <= 1024, 1 <= n <= 1024, 1 <= k <= min(n, 8);
+ * anything larger returns SAP_E_ARG.
+ *
+ * Working memory is one fixed file-scope device array of about 4.2 MB that
+ * every GPU loading the library holds until exit.  The first call on a
+ * device looks up its address and must come before any stream capture.
+ * All calls share the array and reset it on entry; calls that overlap on the
+ * GPU race, so the caller must serialise them.
+ */
+sap_status sap_min_secant_noalloc(const float *X, int64_t N, int32_t n, const double *U, int32_t k,
+                                  double eps, void *cuda_stream, int64_t *i, int64_t *j,
+                                  double *ratio);
+
 /* Read the handle's statistics. */
 sap_status sap_get_stats(sap_handle h, sap_stats *out);
 

@@ -80,6 +80,7 @@ def load_library():
         "sap_get_history": ([vp, vp, vp, i32], i32),
         "sap_estimate_dim": ([vp, vp, i32, i32, f64, f64, i32p, vp], i32),
         "sap_project": ([vp, vp, i32], i32),
+        "sap_min_secant_noalloc": ([vp, i64, i32, vp, i32, f64, vp, i64p, i64p, f64p], i32),
         "sap_get_stats": ([vp, ctypes.POINTER(Stats)], i32),
         "sap_set_profiling": ([vp, i32], i32),
         "sap_get_kernel_time": ([vp, i32, f64p, i64p], i32),
@@ -250,6 +251,23 @@ def sap_project(h, out):
     p, dev = _ptr(out)
     _check(h, load_library().sap_project(h, p, dev))
     return out
+
+
+def sap_min_secant_noalloc(X, U, eps=0.0, stream=None):
+    """Allocation-free argmin for callers that must not allocate device
+    memory: X (N, n) float32 and U (k, n) float64 torch CUDA tensors; returns
+    (i, j, ratio).  Limits N <= 1024, n <= 1024, k <= 8; concurrent calls on
+    one device must be serialised (they share a fixed scratch array)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    i, j, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    code = load_library().sap_min_secant_noalloc(
+        ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], ctypes.c_void_p(U.data_ptr()),
+        U.shape[0], float(eps), ctypes.c_void_p(stream) if stream else None,
+        ctypes.byref(i), ctypes.byref(j), ctypes.byref(r))
+    if code != 0:
+        raise SapError(code, "sap_min_secant_noalloc")
+    return i.value, j.value, r.value
 
 
 def sap_get_stats(h):

@@ -248,7 +248,7 @@ sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only)
         u.split_bf16 = h->split == SAP_SPLIT_BF16; u.split_scale = h->split == SAP_SPLIT_BF16 ? 256.f : 2048.f;
         u.k = h->k; u.alpha = alpha; u.mode = (int)h->mode; u.eval_only = eval_only;
         u.eps2 = h->eps2_f64; u.list = list; u.cap = (unsigned int)h->cap; u.which = which;
-        u.partials = h->partials; u.grid = std::min(h->sms, 64);
+        u.partials = h->partials; u.grid = std::min(h->sms, kRecheckBlocks);
         u.work = h->work; u.st = h->st; u.hist = h->hist; u.argmin = h->am; u.seed_cert = c32;
         Timed t(h, K_UPDATE);
         CK(launch_select_update(u, s));

@@ -229,7 +229,6 @@ __global__ void __launch_bounds__(256) wprep_kernel(WPrepArgs a)
 // ------------------------------------------------------- all-pairs pass ---
 
 constexpr int kPassStagesMax = 3;
-constexpr int kPassThreads = 256;
 
 struct PassArgs {
     const float *w;
@@ -250,71 +249,89 @@ __host__ __device__ inline uint32_t pass_stage_bytes(int KY)
     return (uint32_t)T * T * 4 + 2u * T * KY * 4;
 }
 
-// Persistent pass: one block of 256 threads per SM walks the tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...  Thread 0 keeps a ring of
-// `stages` shared-memory buffers filled by 1-D TMA bulk copies (the 64 KB
-// w tile plus the 128 rows of Y for each side), so the next tiles stream in
-// while the current one is evaluated.  Each thread owns CPT adjacent columns
-// of rows spaced 8/(4/CPT) apart; K = compute width (k, or k rounded up for
-// large k: Y's pad columns are zero).  q = ||y_i - y_j||^2 w is formed with
-// packed FP32 pairs and kept in registers; the block minimum sets the
-// selection threshold and a second pass over the registers emits the
-// candidates.  The global running bound is read at the start of a tile and
-// tightened with a fire-and-forget atomic, so no thread waits on it.
+// Persistent, warp-specialised pass: one block per SM walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  A producer warp keeps a ring of
+// `stages` shared-memory buffers filled by 1-D TMA bulk copies (the 64 KB w
+// tile and, for each side, one 512-byte segment per component of Y^T); 16
+// consumer warps evaluate the tiles.  Full/empty mbarriers hand the buffers
+// over, so the loop has no block-wide barrier.  Each consumer thread owns CPT
+// adjacent columns (j) of rows spaced 16/(4/CPT) apart (32 pairs per tile);
+// K = compute width (k, or k rounded up for large k: Y's pad components are
+// zero).  q = ||y_i - y_j||^2 w is formed with packed FP32 pairs.  Every warp
+// bounds the minimum from its own pairs (a valid upper bound like any other),
+// tightens the global running bound with a fire-and-forget atomic, and
+// emits its candidates with one atomic per warp when it has any.
+constexpr int kConsumerWarps = 16;
+constexpr int kPassThreads = (kConsumerWarps + 1) * 32;
+
 template <int K, int CPT>
 __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
 {
-    constexpr int SR = 4 / CPT;        // warps sharing one row
-    constexpr int RSTEP = 8 / SR;      // row step of one warp
-    constexpr int RPW = T / RSTEP;     // rows per warp
-    constexpr int NPR = CPT / 2;       // column pairs per thread
+    constexpr int SR = 4 / CPT;                  // warps sharing one row
+    constexpr int RSTEP = kConsumerWarps / SR;   // row step of one warp
+    constexpr int RPW = T / RSTEP;               // rows per warp
+    constexpr int NPR = CPT / 2;                 // column pairs per thread
     // indexed directly (no integer round trip) so reads stay shared-memory loads
     extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ __align__(8) uint64_t full[kPassStagesMax];
+    __shared__ __align__(8) uint64_t full[kPassStagesMax], empty[kPassStagesMax];
     __shared__ int2 sIJ[kPassStagesMax];
-    __shared__ float red[32];
-    __shared__ int scan[33];
-    __shared__ int base_sh;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int seg = warp % SR, row0 = warp / SR;
-    const int col0 = seg * 32 * CPT + lane * CPT;
     const int KY = a.KY, S = a.stages;
     const uint32_t wbytes = T * T * 4, ybytes = T * KY * 4, sbytes = wbytes + 2 * ybytes;
     const int nmine = blockIdx.x < (unsigned)a.ntiles ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const long long budget = 4000000000ll;
 
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) tc::mbar_init(&full[s], 1);
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], kConsumerWarps);
+        }
         tc::fence_mbar_init();
     }
     __syncthreads();
-    int issued = 0;
-    auto issue = [&](int it) {
-        const int s = it % S;
-        const int t = blockIdx.x + it * gridDim.x;
-        const int2 IJ = a.wtiles[t];
-        sIJ[s] = IJ;
-        unsigned char *base = sm + (size_t)s * sbytes;
-        tc::mbar_expect_tx(&full[s], sbytes);
-        tc::bulk_g2s(base, a.w + (size_t)t * T * T, wbytes, &full[s]);
-        // Y^T is component-major: one 512-byte row segment per component and side
-        for (int c = 0; c < KY; ++c) {
-            tc::bulk_g2s(base + wbytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.x * T, T * 4, &full[s]);
-            tc::bulk_g2s(base + wbytes + ybytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.y * T, T * 4,
-                         &full[s]);
-        }
-    };
-    if (tid == 0)
-        for (; issued < S && issued < nmine; ++issued) issue(issued);
 
+    if (warp == kConsumerWarps) {
+        // ---------------- producer warp ----------------
+        if (lane == 0) {
+            int issued = 0;
+            for (int it = 0; it < nmine; ++it) {
+                const int s = it % S;
+                if (it >= S && !tc::mbar_wait_bounded(&empty[s], ((it / S) - 1) & 1, budget)) {
+                    atomicOr(&a.st->status, ST_TIMEOUT);
+                    break;
+                }
+                const int t = blockIdx.x + it * gridDim.x;
+                const int2 IJ = a.wtiles[t];
+                sIJ[s] = IJ;  // published by the mbarrier completion below
+                unsigned char *base = sm + (size_t)s * sbytes;
+                tc::mbar_expect_tx(&full[s], sbytes);
+                tc::bulk_g2s(base, a.w + (size_t)t * T * T, wbytes, &full[s]);
+                for (int c = 0; c < KY; ++c) {
+                    tc::bulk_g2s(base + wbytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.x * T, T * 4,
+                                 &full[s]);
+                    tc::bulk_g2s(base + wbytes + ybytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.y * T,
+                                 T * 4, &full[s]);
+                }
+                ++issued;
+            }
+            // no copy of ours may still be in flight when the block exits
+            for (int it = issued > S ? issued - S : 0; it < issued; ++it)
+                tc::mbar_wait_bounded(&full[it % S], (it / S) & 1, budget);
+        }
+        return;
+    }
+
+    // ---------------- consumer warps ----------------
+    const int seg = warp % SR, row0 = warp / SR;
+    const int col0 = seg * 32 * CPT + lane * CPT;
     const float seed = load_pos_float(&a.st->seed_ub);
-    float ublock = INFINITY;
+    float uwarp = INFINITY;  // best upper bound this warp has produced
     for (int it = 0; it < nmine; ++it) {
         const int s = it % S;
-        const bool ok = tc::mbar_wait_bounded(&full[s], (it / S) & 1, 4000000000ll);
-        if (!__syncthreads_and(ok ? 1 : 0)) {
-            if (tid == 0) atomicOr(&a.st->status, ST_TIMEOUT);
+        if (!tc::mbar_wait_bounded(&full[s], (it / S) & 1, budget)) {
+            if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
             break;
         }
         const float gnow = load_pos_float(&a.st->run_ub1);  // consumed after the tile
@@ -326,8 +343,6 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
         float v[RPW][CPT];
         float mymin = INFINITY;
         if (NPR > 0) {
-            // this thread's CPT columns of every component: one conflict-free
-            // 8- or 16-byte load per component
             uint64_t yj2[NPR > 0 ? NPR : 1][K];
 #pragma unroll
             for (int c = 0; c < K; ++c) {
@@ -390,14 +405,17 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 mymin = fminf(mymin, v[r][0]);
             }
         }
-        const float bmin = block_min(mymin, red);  // all reads of stage s are done
-        if (tid == 0 && issued < nmine) issue(issued++);
-        float U = fminf(fminf(seed, gnow), ublock);
-        if (bmin < INFINITY) {
-            const float ub = cert_upper(sqrtf(bmin), a.cert);
-            if (tid == 0) atomic_min_pos_float(&a.st->run_ub1, ub);
+        // the warp's reads of stage s are done
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&empty[s]);
+
+        const float wmin = warp_min(mymin);
+        float U = fminf(fminf(seed, gnow), uwarp);
+        if (wmin < INFINITY) {
+            const float ub = cert_upper(sqrtf(wmin), a.cert);
+            if (lane == 0 && ub < gnow) atomic_min_pos_float(&a.st->run_ub1, ub);
             U = fminf(U, ub);
-            ublock = fminf(ublock, ub);
+            uwarp = fminf(uwarp, ub);
         }
         const float th = cert_emit_threshold(U, a.cert);
         const float th2 = th * th * 1.000001f;
@@ -407,29 +425,32 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
             for (int r = 0; r < RPW; ++r)
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) cnt += v[r][q] <= th2 ? 1 : 0;
-        int total;
-        const int off = block_exclusive_scan(cnt, scan, &total);
-        if (total == 0) continue;
-        if (tid == 0) base_sh = (int)atomicAdd((unsigned int *)&a.st->cnt1, (unsigned int)total);
-        __syncthreads();
-        if (cnt) {
-            long long pos = (long long)(unsigned int)base_sh + off;
-            const int i0 = IJ.x * T, j0 = IJ.y * T;
+        if (__any_sync(0xffffffffu, cnt > 0)) {
+            int incl = cnt;
 #pragma unroll
-            for (int r = 0; r < RPW; ++r)
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned int base = 0;
+            if (lane == 31) base = atomicAdd((unsigned int *)&a.st->cnt1, (unsigned int)total);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            if (cnt) {
+                long long pos = (long long)base + incl - cnt;
+                const int i0 = IJ.x * T, j0 = IJ.y * T;
 #pragma unroll
-                for (int q = 0; q < CPT; ++q)
-                    if (v[r][q] <= th2) {
-                        if (pos < a.cap) a.cand[pos] = make_int2(i0 + row0 + r * RSTEP, j0 + col0 + q);
-                        else atomicOr(&a.st->status, ST_OVERFLOW);
-                        ++pos;
-                    }
+                for (int r = 0; r < RPW; ++r)
+#pragma unroll
+                    for (int q = 0; q < CPT; ++q)
+                        if (v[r][q] <= th2) {
+                            if (pos < a.cap) a.cand[pos] = make_int2(i0 + row0 + r * RSTEP, j0 + col0 + q);
+                            else atomicOr(&a.st->status, ST_OVERFLOW);
+                            ++pos;
+                        }
+            }
         }
     }
-    // no copy of ours may still be in flight when the block exits
-    if (tid == 0)
-        for (int it = issued > S ? issued - S : 0; it < issued; ++it)
-            tc::mbar_wait_bounded(&full[it % S], (it / S) & 1, 4000000000ll);
 }
 
 // ------------------------------------------- explicit-difference recheck ---
@@ -730,17 +751,6 @@ cudaError_t configure_pass_kernels()
     f(config_pass_k<5, 4>()); f(config_pass_k<6, 4>()); f(config_pass_k<7, 4>()); f(config_pass_k<8, 4>());
     f(config_pass_k<12, 2>()); f(config_pass_k<16, 2>()); f(config_pass_k<24, 1>()); f(config_pass_k<32, 1>());
     return e;
-}
-
-// Columns of Y the pass reads per row: k itself up to 8, else k rounded up
-// to the next instantiated width (Y's extra columns are zero).
-int pass_width(int k)
-{
-    if (k <= 8) return k;
-    if (k <= 12) return 12;
-    if (k <= 16) return 16;
-    if (k <= 24) return 24;
-    return 32;
 }
 
 cudaError_t launch_pass(const PassArgs &a, int k, int grid, cudaStream_t s)

@@ -3,14 +3,18 @@
 // et al., arXiv:1807.03425), fused into one launch.
 //
 // Phase 1 (all blocks): one warp per candidate forms the explicit FP64
-// difference D = x_i - x_j, d^2 = |D|^2 and z = U^T D, r = sqrt(|z|^2/d^2),
-// applies the exclusion rules exactly (d^2 == 0: not distinct, Sec. II;
-// d^2 < eps^2: shorter than the threshold, Sec. VII) and keeps the best
-// (r, i, j), ties to the smallest pair index.  Each block publishes its best;
-// the last block to finish (ticket counter) continues with phase 2.
+// difference D = x_i - x_j, d^2 = |D|^2 and z = U^T D, applies the exclusion
+// rules exactly (d^2 == 0: not distinct, Sec. II; d^2 < eps^2: shorter than
+// the threshold, Sec. VII) and keeps the best squared ratio q = |z|^2/d^2
+// (the square root is monotone, so the argmin is the same; ties go to the
+// smallest pair index).  Candidates are dealt to blocks first and to warps
+// second, so each SM's FP64 pipe serves as few warps as possible (FP64
+// throughput per SM, not latency, is what limits this phase on this part).
+// Each block publishes its best; the last block to finish (ticket counter)
+// continues with phase 2.
 //
 // Phase 2 (last block):
-//   1. argmin over the block results; record it in the history;
+//   1. argmin over the block results; record r = sqrt(q) in the history;
 //   2. s = D/|D|, c = U^T s (one multi-value block reduction);
 //   3. pivot t = argmax_l |c_l| (first on ties; the first column if all are
 //      zero), then modified Gram-Schmidt on [c, e_l (l != t)] in the
@@ -18,9 +22,13 @@
 //      MGS of [U c, u_l (l != t)] in R^n is U times MGS of [c, e_l] in R^k;
 //   4. new first column along (1-a) v + a (s - v) (literal reading) or
 //      (1-a) v/|v| + a e/|e| (angle reading), v = U c, e = s - v;
-//   5. re-orthonormalisation in FP64: Cholesky QR of the new basis
-//      (G = U'^T U', G = R^T R, U'' = U' R^-1), the QR factor that one MGS
-//      re-pass produces in exact arithmetic;
+//   5. re-orthonormalisation in FP64, as a Cholesky QR of the new basis U':
+//      G = U'^T U' = (I + R)^T (I + R), U'' = U' (I + R)^-1, the QR factor one
+//      MGS re-pass gives in exact arithmetic.  When max|G - I| <= 1e-6 (the
+//      usual case: U' is orthonormal to working precision) R and (I + R)^-1
+//      are taken from their series in E = G - I to second order, whose
+//      truncation error (order |E|^3) is below FP64 rounding; otherwise the
+//      Cholesky factor is computed directly;
 //   6. U'' written in FP64, FP32 and as the split 16-bit operands of the
 //      tensor-core product; the recent argmin pairs are re-evaluated under
 //      U'' (FP32 explicit differences) to seed the next evaluation's bound.
@@ -36,7 +44,8 @@ namespace {
 
 constexpr int SB = 256;          // threads per block
 constexpr int NW = SB / 32;
-constexpr size_t kDynSmem = 24 * 1024;  // vectors kept in shared memory up to this size
+constexpr size_t kDynSmem = 24 * 1024;  // U' kept in shared memory up to this size
+constexpr int kSeedRegs = 4;     // watch-pair coordinates prefetched per lane (n <= 128)
 
 template <typename TX>
 __device__ __forceinline__ TX ld_x(const void *X, size_t idx)
@@ -80,15 +89,18 @@ struct Shared {
     double red_d[NW * (K + 1)];
     float red_f[NW * (K + 1)];
     Partial wb[NW];
-    int last;
-    int alive0;
+    int last, alive0, series;
+    // problem state prefetched at the start of phase 2
+    int iter, hist_cap, cnt1, cnt2, watch_n, watch_pos;
+    int2 watch[kWatch];
     double cvec[K + 1];            // U^T D and |D|^2 (data precision, widened)
     WT cw[K];                      // c = U^T s
     WT Bw[K][K];                   // coefficient MGS result, column m = q_m
     WT av, asd, dnorm, nd2;        // direction coefficients, |D|, |dir|^2
-    double G[K][K];                // Gram matrix, then R (upper)
-    double Rd[K];                  // 1 / R_jj
-    double Ri[K][K];               // R^-1 (upper)
+    double G[K][K];                // Gram matrix (upper), then R (upper)
+    double T1[K][K], T2[K][K];     // series terms
+    double Ri[K][K];               // (I + R)^-1 (upper)
+    double Rd[K];                  // 1 / R_jj (direct path)
     float seed[NW];
 };
 
@@ -107,7 +119,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         unsigned int cnt = a.which == 1 ? (unsigned int)st->cnt1 : (unsigned int)st->cnt2;
         if (cnt > a.cap) cnt = a.cap;
         Partial best = {INFINITY, 0x7fffffff, 0x7fffffff};
-        for (unsigned int e = blockIdx.x * NW + w; e < cnt; e += gridDim.x * NW) {
+        for (unsigned int e = blockIdx.x + gridDim.x * w; e < cnt; e += gridDim.x * NW) {
             const int2 ij = a.list[e];
             double v[K + 1];
 #pragma unroll
@@ -127,8 +139,8 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             double zz = 0.0;
 #pragma unroll
             for (int c = 0; c < K; ++c) zz = fma(v[c], v[c], zz);
-            const double r = sqrt(zz / d2);
-            if (better(r, ij.x, ij.y, best.r, best.i, best.j)) best = Partial{r, ij.x, ij.y};
+            const double q = zz / d2;  // squared ratio
+            if (better(q, ij.x, ij.y, best.r, best.i, best.j)) best = Partial{q, ij.x, ij.y};
         }
         if (lane == 0) sh.wb[w] = best;
         __syncthreads();
@@ -163,47 +175,78 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             q.j = __shfl_xor_sync(0xffffffffu, b.j, o);
             if (better(q.r, q.i, q.j, b.r, b.i, b.j)) b = q;
         }
+        if (lane == 0) sh.wb[0] = b;
+    } else if (w == 1) {
+        // prefetch the problem state while warp 0 reduces
         if (lane == 0) {
-            sh.wb[0] = b;
-            const int it = st->iter;
-            const bool none = !(b.r < INFINITY);
-            if (none) atomicOr(&st->status, ST_NO_SECANT);
-            if (it < st->hist_cap) {
-                a.hist[it] = none ? __longlong_as_double(0x7ff8000000000000ll) : b.r;
-                a.argmin[it] = none ? make_int2(-1, -1) : make_int2(b.i, b.j);
-            }
-            st->iter = it + 1;
-            st->last_r = b.r;
-            st->last_i = none ? -1 : b.i;
-            st->last_j = none ? -1 : b.j;
-            st->last_cnt1 = st->cnt1;
-            st->last_cnt2 = st->cnt2;
-            st->cnt1 = 0;
-            st->cnt2 = 0;
-            st->ticket = 0;
-            st->run_ub1 = 0x7f800000u;
-            st->run_ub2 = 0x7f800000u;
-            if (!none) {
-                bool present = false;
-                for (int q = 0; q < st->watch_n; ++q)
-                    present |= (st->watch[q].x == b.i && st->watch[q].y == b.j);
-                if (!present) {
-                    st->watch[st->watch_pos] = make_int2(b.i, b.j);
-                    st->watch_pos = (st->watch_pos + 1) % kWatch;
-                    if (st->watch_n < kWatch) ++st->watch_n;
-                }
-                if (a.eval_only)  // the basis stays: the exact minimum bounds the next one
-                    st->seed_ub = __float_as_uint(__double2float_ru(b.r) * 1.000001f);
-            }
+            sh.iter = st->iter;
+            sh.hist_cap = st->hist_cap;
+            sh.cnt1 = st->cnt1;
+            sh.cnt2 = st->cnt2;
+            sh.watch_n = st->watch_n;
+            sh.watch_pos = st->watch_pos;
         }
+        if (lane < kWatch) sh.watch[lane] = st->watch[lane];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        Partial b = sh.wb[0];
+        const bool none = !(b.r < INFINITY);
+        const double r = none ? b.r : sqrt(b.r);
+        const int it = sh.iter;
+        if (none) atomicOr(&st->status, ST_NO_SECANT);
+        if (it < sh.hist_cap) {
+            a.hist[it] = none ? __longlong_as_double(0x7ff8000000000000ll) : r;
+            a.argmin[it] = none ? make_int2(-1, -1) : make_int2(b.i, b.j);
+        }
+        st->iter = it + 1;
+        st->last_r = r;
+        st->last_i = none ? -1 : b.i;
+        st->last_j = none ? -1 : b.j;
+        st->last_cnt1 = sh.cnt1;
+        st->last_cnt2 = sh.cnt2;
+        st->cnt1 = 0;
+        st->cnt2 = 0;
+        st->ticket = 0;
+        st->run_ub1 = 0x7f800000u;
+        st->run_ub2 = 0x7f800000u;
+        if (!none) {
+            bool present = false;
+            for (int q = 0; q < sh.watch_n; ++q) present |= (sh.watch[q].x == b.i && sh.watch[q].y == b.j);
+            if (!present) {
+                sh.watch[sh.watch_pos] = make_int2(b.i, b.j);
+                st->watch[sh.watch_pos] = make_int2(b.i, b.j);
+                sh.watch_pos = (sh.watch_pos + 1) % kWatch;
+                if (sh.watch_n < kWatch) ++sh.watch_n;
+                st->watch_pos = sh.watch_pos;
+                st->watch_n = sh.watch_n;
+            }
+            if (a.eval_only)  // the basis stays: the exact minimum bounds the next one
+                st->seed_ub = __float_as_uint(__double2float_ru(r) * 1.000001f);
+        }
+        sh.wb[0].r = r;
     }
     __syncthreads();
     const Partial b = sh.wb[0];
     if (!(b.r < INFINITY) || a.eval_only) return;
 
-    const bool in_smem = (size_t)n * (K + 1) * sizeof(WT) <= kDynSmem;
-    WT *Up = in_smem ? reinterpret_cast<WT *>(dyn) : reinterpret_cast<WT *>(a.work);  // n x K
-    WT *Ds = Up + (size_t)n * K;                                                       // n
+    // the watch pairs' coordinates, loaded now and used at the very end
+    const int nwatch = sh.watch_n;
+    const bool prefetch = n <= 32 * kSeedRegs;
+    float wxi[kSeedRegs], wxj[kSeedRegs];
+    if (prefetch && w < nwatch) {
+        const int2 pr = sh.watch[w];
+#pragma unroll
+        for (int q = 0; q < kSeedRegs; ++q) {
+            const int l = lane + 32 * q;
+            wxi[q] = l < n ? (float)ld_x<TX>(a.X, (size_t)pr.x * n + l) : 0.f;
+            wxj[q] = l < n ? (float)ld_x<TX>(a.X, (size_t)pr.y * n + l) : 0.f;
+        }
+    }
+
+    const bool in_smem = K <= 8 && (size_t)n * K * sizeof(double) <= kDynSmem;
+    double *Up = in_smem ? dyn : a.work;           // n x K: the new basis before QR
+    WT *Ds = reinterpret_cast<WT *>(Up + (size_t)n * K);  // n
 
     // 2. D = x_i - x_j, |D|^2 and U^T D in one multi-value reduction
     {
@@ -234,7 +277,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
     }
 
     // 3-4. pivot, coefficient MGS on [c, e_l (l != t)] and the rotation
-    //      coefficients, in one thread (k x k work)
+    //      coefficients, in one thread (k x k work, unrolled for small k)
     if (tid == 0) {
         const WT d = sqrt((WT)sh.cvec[K]);
         WT c[K];
@@ -246,19 +289,20 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         }
         int t = 0;
         WT cmax = fabs(c[0]);
-        for (int q = 1; q < kk; ++q)
-            if (fabs(c[q]) > cmax) { cmax = fabs(c[q]); t = q; }
+#pragma unroll
+        for (int q = 1; q < K; ++q)
+            if (q < kk && fabs(c[q]) > cmax) { cmax = fabs(c[q]); t = q; }
         WT Q[K][K];
-        int alive[K];
-#pragma unroll 1
-        for (int m = 0; m < kk; ++m) {
+        bool alive[K];
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
             WT x[K];
             const int l = (m - 1) < t ? (m - 1) : m;  // list entry m >= 1 is column l
 #pragma unroll
             for (int q = 0; q < K; ++q) x[q] = m == 0 ? c[q] : (q == l ? (WT)1 : (WT)0);
-#pragma unroll 1
-            for (int p = 0; p < m; ++p) {
-                if (!alive[p]) continue;
+#pragma unroll
+            for (int p = 0; p < K; ++p) {
+                if (p >= m || !alive[p]) continue;
                 WT h = 0;
 #pragma unroll
                 for (int q = 0; q < K; ++q) h += Q[p][q] * x[q];
@@ -268,13 +312,16 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             WT nn = 0;
 #pragma unroll
             for (int q = 0; q < K; ++q) nn += x[q] * x[q];
-            alive[m] = nn > (WT)0;
+            alive[m] = m < kk && nn > (WT)0;
             const WT inv = alive[m] ? (WT)1 / sqrt(nn) : (WT)0;
 #pragma unroll
             for (int q = 0; q < K; ++q) Q[m][q] = x[q] * inv;
         }
-        for (int m = 0; m < kk; ++m)
+#pragma unroll
+        for (int m = 0; m < K; ++m)
+#pragma unroll
             for (int q = 0; q < K; ++q) sh.Bw[q][m] = Q[m][q];
+#pragma unroll
         for (int q = 0; q < K; ++q) sh.cw[q] = c[q];
         sh.alive0 = alive[0];
         const WT al = (WT)a.alpha;
@@ -308,90 +355,118 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
 #pragma unroll
             for (int c = 0; c < K; ++c) v0 += u[c] * sh.cw[c];
             const WT d0 = av * v0 + asd * Ds[l];
-            Up[(size_t)l * K] = d0;
             p0 += d0 * d0;
+            WT col[K];
+            col[0] = d0;
 #pragma unroll
             for (int m = 1; m < K; ++m) {
                 WT s = 0;
 #pragma unroll
                 for (int c = 0; c < K; ++c) s += u[c] * sh.Bw[c][m];
-                Up[(size_t)l * K + m] = s;
+                col[m] = s;
             }
+            // q1 in place of column 0 when the direction vanishes (alpha = 1
+            // with s in the span); s itself when P P^T s = 0
+            WT q1 = 0;
+#pragma unroll
+            for (int c = 0; c < K; ++c) q1 += u[c] * sh.Bw[c][0];
+            Ds[l] = sh.alive0 ? q1 : Ds[l] / sh.dnorm;
+#pragma unroll
+            for (int m = 0; m < K; ++m) Up[(size_t)l * K + m] = (double)col[m];
         }
         WT pv[1] = {p0};
         WT *scr = sizeof(WT) == 8 ? (WT *)sh.red_d : (WT *)sh.red_f;
         block_sum_multi<WT, 1>(pv, scr, &sh.nd2);
-        const WT nd = sqrt(sh.nd2);
-        const bool keep_q1 = sh.alive0 != 0;
+        const double nd = sqrt((double)sh.nd2);
 #pragma unroll 1
-        for (int l = tid; l < n; l += SB) {
-            if (nd > 0) {
-                Up[(size_t)l * K] /= nd;
-            } else if (keep_q1) {  // alpha = 1 with s in the span: keep q1
-                WT s = 0;
-#pragma unroll
-                for (int c = 0; c < K; ++c)
-                    if (c < kk)
-                        s += (sizeof(WT) == 8 ? (WT)a.U64[(size_t)c * n + l] : (WT)a.U32[(size_t)l * a.KP + c]) *
-                             sh.Bw[c][0];
-                Up[(size_t)l * K] = s;
-            } else {               // P P^T s = 0: the new column is s
-                Up[(size_t)l * K] = Ds[l] / sh.dnorm;
-            }
-        }
+        for (int l = tid; l < n; l += SB)
+            Up[(size_t)l * K] = nd > 0.0 ? Up[(size_t)l * K] / nd : (double)Ds[l];
         __syncthreads();
     }
 
-    // 5. FP64 Cholesky QR of Up: Gram entries spread over the warps
+    // 5. FP64 Gram matrix of U' (upper triangle), entries spread over the warps
 #pragma unroll 1
     for (int e = w; e < kk * kk; e += NW) {
         const int p = e / kk, q = e % kk;
         if (q < p) continue;
         double s = 0.0;
-        for (int l = lane; l < n; l += 32) s = fma((double)Up[(size_t)l * K + p], (double)Up[(size_t)l * K + q], s);
+        for (int l = lane; l < n; l += 32) s = fma(Up[(size_t)l * K + p], Up[(size_t)l * K + q], s);
         s = warp_sum(s);
         if (lane == 0) sh.G[p][q] = s;
     }
     __syncthreads();
     if (w == 0) {
-        // right-looking Cholesky G = R^T R on the upper triangle, lane m owns
-        // column m; 1/R_jj from one reciprocal square root per step
-        double rinv_own = 0.0;
-#pragma unroll 1
-        for (int j = 0; j < kk; ++j) {
-            const double gjj = sh.G[j][j];
-            const double rinv = rsqrt(gjj);
-            if (lane == j) { sh.G[j][j] = gjj * rinv; rinv_own = rinv; }
-            if (lane > j && lane < kk) sh.G[j][lane] *= rinv;
-            __syncwarp();
-            if (lane > j && lane < kk)
-                for (int p = j + 1; p <= lane; ++p) sh.G[p][lane] = fma(-sh.G[j][p], sh.G[j][lane], sh.G[p][lane]);
-            __syncwarp();
+        // E = G - I; the series needs max|E| small
+        double emax = 0.0;
+        for (int e = lane; e < kk * kk; e += 32) {
+            const int p = e / kk, q = e % kk;
+            if (q >= p) emax = fmax(emax, fabs(sh.G[p][q] - (p == q ? 1.0 : 0.0)));
         }
-        if (lane < kk) sh.Rd[lane] = rinv_own;
-        __syncwarp();
-        // R^-1 (upper): lane m solves R x = e_m by back substitution
-        if (lane < kk) {
-            double x[K];
 #pragma unroll
-            for (int q = 0; q < K; ++q) x[q] = 0.0;
-#pragma unroll 1
-            for (int i = lane; i >= 0; --i) {
-                double s = (i == lane) ? 1.0 : 0.0;
-                for (int p = i + 1; p <= lane; ++p) s = fma(-sh.G[i][p], x[p], s);
-                x[i] = s * sh.Rd[i];
+        for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        if (emax <= 1e-6) {
+            // R1 = triu(E) with the diagonal halved; R2 from -R1^T R1 the same
+            // way; R = R1 + R2; (I + R)^-1 = I - R + R^2 (error O(|E|^3))
+            for (int e = lane; e < kk * kk; e += 32) {
+                const int p = e / kk, q = e % kk;
+                sh.T1[p][q] = q > p ? sh.G[p][q] : (q == p ? 0.5 * (sh.G[p][p] - 1.0) : 0.0);
             }
-            for (int i = 0; i <= lane; ++i) sh.Ri[i][lane] = x[i];
+            __syncwarp();
+            for (int e = lane; e < kk * kk; e += 32) {
+                const int p = e / kk, q = e % kk;
+                double s = 0.0;
+                for (int m = 0; m <= (p < q ? p : q); ++m) s = fma(sh.T1[m][p], sh.T1[m][q], s);
+                sh.T2[p][q] = s;  // (R1^T R1)_pq
+            }
+            __syncwarp();
+            for (int e = lane; e < kk * kk; e += 32) {
+                const int p = e / kk, q = e % kk;
+                const double r2v = q > p ? -sh.T2[p][q] : (q == p ? -0.5 * sh.T2[p][p] : 0.0);
+                sh.G[p][q] = sh.T1[p][q] + r2v;  // R (upper; lower entries zero)
+            }
+            __syncwarp();
+            for (int e = lane; e < kk * kk; e += 32) {
+                const int p = e / kk, q = e % kk;
+                double s = 0.0;
+                for (int m = p; m <= q; ++m) s = fma(sh.G[p][m], sh.G[m][q], s);  // (R^2)_pq
+                sh.Ri[p][q] = (p == q ? 1.0 : 0.0) - (q >= p ? sh.G[p][q] : 0.0) + (q >= p ? s : 0.0);
+            }
+        } else {
+            // direct right-looking Cholesky on the upper triangle (lane m owns
+            // column m), then (R)^-1 by back substitution
+            double rinv_own = 0.0;
+#pragma unroll 1
+            for (int j = 0; j < kk; ++j) {
+                const double gjj = sh.G[j][j];
+                const double rinv = rsqrt(gjj);
+                if (lane == j) { sh.G[j][j] = gjj * rinv; rinv_own = rinv; }
+                if (lane > j && lane < kk) sh.G[j][lane] *= rinv;
+                __syncwarp();
+                if (lane > j && lane < kk)
+                    for (int p = j + 1; p <= lane; ++p) sh.G[p][lane] = fma(-sh.G[j][p], sh.G[j][lane], sh.G[p][lane]);
+                __syncwarp();
+            }
+            if (lane < kk) sh.Rd[lane] = rinv_own;
+            __syncwarp();
+            if (lane < kk) {
+                for (int i = 0; i < kk; ++i) sh.Ri[i][lane] = 0.0;
+#pragma unroll 1
+                for (int i = lane; i >= 0; --i) {
+                    double s = (i == lane) ? 1.0 : 0.0;
+                    for (int p = i + 1; p <= lane; ++p) s = fma(-sh.G[i][p], sh.Ri[p][lane], s);
+                    sh.Ri[i][lane] = s * sh.Rd[i];
+                }
+            }
         }
     }
     __syncthreads();
 
-    // 6. U'' = Up R^-1, written in every form the kernels read
+    // 6. U'' = U' (I + R)^-1, written in every form the kernels read
 #pragma unroll 1
     for (int l = tid; l < n; l += SB) {
         double row[K];
 #pragma unroll
-        for (int m = 0; m < K; ++m) row[m] = m < kk ? (double)Up[(size_t)l * K + m] : 0.0;
+        for (int m = 0; m < K; ++m) row[m] = m < kk ? Up[(size_t)l * K + m] : 0.0;
 #pragma unroll
         for (int m = 0; m < K; ++m) {
             if (m >= kk) break;
@@ -420,10 +495,10 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         }
     }
     __syncthreads();
+
     // seeds: the recent argmin pairs under the new basis
-    const int nwatch = st->watch_n;
     if (w < nwatch) {
-        const int2 pr = st->watch[w];
+        const int2 pr = sh.watch[w];
         float seed = INFINITY;
         if (sizeof(TX) == 8) {
             double v[K + 1];
@@ -445,13 +520,28 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             float v[K + 1];
 #pragma unroll
             for (int q = 0; q <= K; ++q) v[q] = 0.f;
-            for (int l = lane; l < n; l += 32) {
-                const float D = (float)ld_x<TX>(a.X, (size_t)pr.x * n + l) - (float)ld_x<TX>(a.X, (size_t)pr.y * n + l);
-                v[K] = fmaf(D, D, v[K]);
-                const float *ur = a.U32 + (size_t)l * a.KP;
+            if (prefetch) {
 #pragma unroll
-                for (int c = 0; c < K; ++c)
-                    if (c < kk) v[c] = fmaf(ur[c], D, v[c]);
+                for (int q = 0; q < kSeedRegs; ++q) {
+                    const int l = lane + 32 * q;
+                    if (l < n) {
+                        const float D = wxi[q] - wxj[q];
+                        v[K] = fmaf(D, D, v[K]);
+                        const float *ur = a.U32 + (size_t)l * a.KP;
+#pragma unroll
+                        for (int c = 0; c < K; ++c)
+                            if (c < kk) v[c] = fmaf(ur[c], D, v[c]);
+                    }
+                }
+            } else {
+                for (int l = lane; l < n; l += 32) {
+                    const float D = (float)ld_x<TX>(a.X, (size_t)pr.x * n + l) - (float)ld_x<TX>(a.X, (size_t)pr.y * n + l);
+                    v[K] = fmaf(D, D, v[K]);
+                    const float *ur = a.U32 + (size_t)l * a.KP;
+#pragma unroll
+                    for (int c = 0; c < K; ++c)
+                        if (c < kk) v[c] = fmaf(ur[c], D, v[c]);
+                }
             }
             warp_sum_multi<float, K + 1>(v);
             float zz = 0.f;
@@ -472,8 +562,8 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
 template <typename TX, int K>
 cudaError_t launch_su(const SelectUpdateArgs &a, cudaStream_t s)
 {
-    const size_t need = (size_t)a.n * (K + 1) * sizeof(double);
-    const size_t shm = need <= kDynSmem ? need : 0;
+    const size_t need = (size_t)a.n * K * sizeof(double) + (size_t)a.n * sizeof(TX);
+    const size_t shm = (K <= 8 && (size_t)a.n * K * sizeof(double) <= kDynSmem) ? need : 0;
     select_update_kernel<TX, K><<<a.grid, SB, shm, s>>>(a);
     return cudaGetLastError();
 }

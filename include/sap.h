@@ -236,6 +236,44 @@ sap_status sap_min_secant_noalloc(const float *X, int64_t N, int32_t n, const do
                                   double eps, void *cuda_stream, int64_t *i, int64_t *j,
                                   double *ratio);
 
+/*
+ * Soft-min objective: a smooth surrogate of the min ratio that Algorithm 1
+ * maximises, for gradient-based training of the basis.  The paper has no
+ * counterpart; its max-min problem (Sec. IV, the objective of Algorithm 1)
+ * is the tau -> 0 limit:
+ *     L(U) = -tau log sum_{i<j kept} exp(-r_ij / tau),
+ * over the pairs the handle keeps (distinct points, and d_ij >= eps after
+ * sap_set_min_secant_length).  min r - tau log P <= L <= min r, P = number of
+ * kept pairs.  The gradient is
+ *     dL/dU = sum_{i<j} p_ij (x_i - x_j)(y_i - y_j)^T / (d_ij^2 r_ij),
+ *     p_ij = exp((L - r_ij)/tau),  y = U^T x,
+ * an n x k matrix laid out like U (column-major FP64); pairs with
+ * r_ij < 1.1e-19 count in L but not in the gradient.  L depends only on the
+ * span of U, so U^T dL/dU is symmetric.
+ *
+ * Requirements: FP32 or BF16 data, a basis set with 1 <= k <= 8, n <= 512,
+ * tau > 0; otherwise SAP_E_UNSUPPORTED / SAP_E_ARG / SAP_E_STATE.  Both
+ * passes run every pair on the GPU from the stored FP32 lengths and an
+ * extended-precision (FP32 hi + lo) Y = X U; the error is stated with the
+ * tests and grows like 1/tau.  Results are reproducible bit for bit.
+ *
+ * sap_softmin_forward: L at the current basis (host output).  Synchronises.
+ * sap_softmin_backward: G_out = dL/dU at the current basis, given L, the
+ *   value sap_softmin_forward returned for this basis and tau (the weights
+ *   p_ij are formed with it).  G_out is n x k column-major FP64, host or
+ *   device (out_is_device).  Synchronises.
+ * sap_softmin_ascent: `steps` Riemannian gradient-ascent steps on the
+ *   Grassmannian, all on the device (one CUDA graph per step):
+ *   G_R = G - U (U^T G), U <- Q factor of U + eta G_R / ||G_R||_F (FP64
+ *   Cholesky QR, positive diagonal of R).  A step with G_R = 0 leaves U
+ *   unchanged.  hist (nullable, host, steps + 1 doubles) receives L before
+ *   each step and at the final basis.  The handle's basis is the final one
+ *   (read it with sap_get_basis; sap_min_secant then judges it).
+ */
+sap_status sap_softmin_forward(sap_handle h, double tau, double *L_out);
+sap_status sap_softmin_backward(sap_handle h, double tau, double L, double *G_out, int out_is_device);
+sap_status sap_softmin_ascent(sap_handle h, double tau, double eta, int32_t steps, double *hist);
+
 /* Read the handle's statistics. */
 sap_status sap_get_stats(sap_handle h, sap_stats *out);
 
@@ -245,8 +283,10 @@ sap_status sap_get_stats(sap_handle h, sap_stats *out);
  * handle's stream; sap_get_kernel_time returns the accumulated device time
  * (ms) and launch count of one kernel class.  Classes: 0 Y = XU product,
  * 1 restructured all-pairs pass, 2 plain all-pairs pass, 3 explicit-difference
- * recheck, 5 FP64 recheck fused with the update (4 is unused).  Enabling
- * resets the accumulators.
+ * recheck, 5 FP64 recheck fused with the update (4 is unused), 6 soft-min
+ * forward pass, 7 soft-min backward pass, 8 soft-min near pairs, 9 soft-min
+ * other kernels (Y, gradient sums, ascent step).  Enabling resets the
+ * accumulators.
  */
 sap_status sap_set_profiling(sap_handle h, int enable);
 sap_status sap_get_kernel_time(sap_handle h, int32_t kernel_class,

@@ -22,7 +22,9 @@ PLAIN, RESTRUCTURED = 0, 1
 UPDATE_LITERAL, UPDATE_ANGLE = 0, 1
 SPLIT_FP16, SPLIT_BF16 = 0, 1
 KERNEL_CLASSES = {"gemm_y": 0, "restructured_pass": 1, "plain_pass": 2,
-                  "explicit_recheck": 3, "select_update": 5, "update": 5}
+                  "explicit_recheck": 3, "select_update": 5, "update": 5,
+                  "softmin_forward": 6, "softmin_backward": 7, "softmin_near": 8,
+                  "softmin_other": 9}
 
 STATUS = {0: "SAP_OK", 1: "SAP_E_ARG", 2: "SAP_E_STATE", 3: "SAP_E_NOT_ORTHONORMAL",
           4: "SAP_E_NO_SECANT", 5: "SAP_E_OOM", 6: "SAP_E_CUDA", 7: "SAP_E_TIMEOUT",
@@ -84,6 +86,9 @@ def load_library():
         "sap_get_stats": ([vp, ctypes.POINTER(Stats)], i32),
         "sap_set_profiling": ([vp, i32], i32),
         "sap_get_kernel_time": ([vp, i32, f64p, i64p], i32),
+        "sap_softmin_forward": ([vp, f64, f64p], i32),
+        "sap_softmin_backward": ([vp, f64, f64, vp, i32], i32),
+        "sap_softmin_ascent": ([vp, f64, f64, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -289,6 +294,28 @@ def sap_get_kernel_time(h, kernel_class):
     return ms.value, cnt.value
 
 
+def sap_softmin_forward(h, tau):
+    L = ctypes.c_double()
+    _check(h, load_library().sap_softmin_forward(h, float(tau), ctypes.byref(L)))
+    return L.value
+
+
+def sap_softmin_backward(h, tau, L, k, n, out=None):
+    """dL/dU as (k, n) FP64 (NumPy, or the given torch CUDA tensor)."""
+    if out is None:
+        out = np.empty((k, n), dtype=np.float64)
+    p, dev = _ptr(out)
+    _check(h, load_library().sap_softmin_backward(h, float(tau), float(L), p, dev))
+    return out
+
+
+def sap_softmin_ascent(h, tau, eta, steps):
+    hist = np.empty(int(steps) + 1, dtype=np.float64)
+    _check(h, load_library().sap_softmin_ascent(h, float(tau), float(eta), int(steps),
+                                                hist.ctypes.data_as(ctypes.c_void_p)))
+    return hist
+
+
 # ------------------------------------------------------------ handle class --
 
 class Sap:
@@ -372,3 +399,12 @@ class Sap:
 
     def kernel_time(self, kernel_class):
         return sap_get_kernel_time(self.h, kernel_class)
+
+    def softmin_forward(self, tau):
+        return sap_softmin_forward(self.h, tau)
+
+    def softmin_backward(self, tau, L, out=None):
+        return sap_softmin_backward(self.h, tau, L, self.k, self.n, out)
+
+    def softmin_ascent(self, tau, eta, steps):
+        return sap_softmin_ascent(self.h, tau, eta, steps)

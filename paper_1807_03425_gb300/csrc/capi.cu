@@ -10,6 +10,7 @@
 // graphs of `chunk` iterations.
 #include "sap_internal.cuh"
 #include "restructured.cuh"
+#include "softmin.cuh"
 #include "../../include/sap.h"
 
 #include <cuda_bf16.h>
@@ -25,7 +26,8 @@ using namespace sap;
 
 namespace {
 
-constexpr int kClasses = 6;
+constexpr int kClasses = 10;
+// 6..9: soft-min forward pass, backward pass, near pairs, other (softmin.cu)
 enum KClass { K_GEMM = 0, K_RESTR = 1, K_PLAIN = 2, K_EXPL = 3, K_FP64 = 4, K_UPDATE = 5 };
 
 struct GraphEntry {
@@ -79,6 +81,7 @@ struct sap_ctx {
     int64_t n_excluded = 0;
 
     RestrState rs;           // restructured-form buffers (restructured.cuh)
+    SoftState ss;            // soft-min buffers (softmin.cuh)
 
     long long launches = 0;
     std::vector<GraphEntry> graphs;
@@ -359,6 +362,13 @@ void handle_push_timing(sap_handle h, int cls, cudaEvent_t a, cudaEvent_t b)
     if (a) h->pending.push_back({cls, a, b});
 }
 sap_status handle_fail(sap_handle h, sap_status s, const char *msg) { return fail(h, s, msg); }
+SoftState &soft_state(sap_handle h) { return h->ss; }
+double *handle_u64(sap_handle h) { return h->U64; }
+float *handle_u32_mut(sap_handle h) { return h->U32; }
+sap_status handle_reset_state(sap_handle h) { return reset_state(h); }
+int handle_profiling(sap_handle h) { return h->profiling ? 1 : 0; }
+long long handle_launches(sap_handle h) { return h->launches; }
+void handle_add_launches(sap_handle h, long long delta) { h->launches += delta; }
 } // namespace sap
 
 extern "C" {
@@ -392,6 +402,7 @@ sap_status sap_destroy(sap_handle h)
     for (auto &p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : h->event_pool) cudaEventDestroy(e);
     restructured_free(h);
+    softmin_free(h);
     dfree(h->X32); dfree(h->X64); dfree(h->U64); dfree(h->U32);
     dfree(h->tiles); dfree(h->cand1); dfree(h->cand2); dfree(h->partials);
     dfree(h->work); dfree(h->st); dfree(h->hist); dfree(h->am);
@@ -795,6 +806,25 @@ sap_status sap_get_kernel_time(sap_handle h, int32_t kernel_class, double *total
     if (total_ms) *total_ms = h->ktime[kernel_class];
     if (launches) *launches = h->kcount[kernel_class];
     return SAP_OK;
+}
+
+sap_status sap_softmin_forward(sap_handle h, double tau, double *L_out)
+{
+    CHECK_HANDLE(h);
+    if (!L_out) return fail(h, SAP_E_ARG, "null output");
+    return softmin_forward(h, tau, L_out);
+}
+
+sap_status sap_softmin_backward(sap_handle h, double tau, double L, double *G_out, int out_is_device)
+{
+    CHECK_HANDLE(h);
+    return softmin_backward(h, tau, L, G_out, out_is_device);
+}
+
+sap_status sap_softmin_ascent(sap_handle h, double tau, double eta, int32_t steps, double *hist)
+{
+    CHECK_HANDLE(h);
+    return softmin_ascent(h, tau, eta, steps, hist);
 }
 
 sap_status sap_estimate_dim(sap_handle h, const double *U0, int32_t k_max, int32_t iters,

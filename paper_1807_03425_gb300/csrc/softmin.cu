@@ -47,8 +47,8 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kSoftStagesMax = 3;
 constexpr int kFwdWarps = 16;            // consumer warps of the forward pass
 constexpr int kBwdWarps = 8;             // consumer warps of the backward pass
-constexpr int kNearWarps = 4;            // warps per block of the near-pair kernels
-constexpr int kNearChunk = 32;           // near pairs per warp
+constexpr int kNearWarps = 8;            // warps per block of the near-pair kernels
+constexpr int kNearChunk = 16;           // near pairs per warp
 constexpr int kSoftMaxN = 512;           // ambient dimension limit of this objective
 constexpr float kFltMin = 1.17549435e-38f;
 
@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(256) ydf_kernel(const float *X, int N, int n, 
 #pragma unroll
         for (int c = 0; c < K; ++c) hi[c] = lo[c] = 0.f;
         if (row < N)
+#pragma unroll 4
             for (int l = sl; l < n; l += 8) {
                 const float x = X[(size_t)row * n + l];
 #pragma unroll
@@ -541,11 +542,16 @@ struct SoftNearArgs {
 };
 
 // The near pairs from explicit differences, one warp per pair, kNearChunk
-// consecutive pairs per warp.  r from the explicit FP32 length and the hi+lo
-// differences of Y.  Forward: (M, S) per block.  Backward: per-warp FP32
-// accumulation of c_ij (x_i - x_j)(y_i - y_j)^T in shared memory, then the
-// block's sum as hi + lo pairs.
-template <int K, bool BWD>
+// consecutive pairs per warp taken kNearIlp at a time with their loads
+// interleaved (the kernel is latency-bound: a pair is a few hundred flops).
+// Lane l holds coordinates l, l + 32, ... (NM of them, n <= 32 NM) of the
+// differences in registers.  r from the explicit FP32 length and the hi+lo
+// differences of Y.  Forward: (M, S) per block.  Backward: per-lane FP32
+// accumulation of c_ij (x_i - x_j)(y_i - y_j)^T for its coordinates, summed
+// over the block's warps as hi + lo pairs.
+constexpr int kNearIlp = 4;
+
+template <int K, int NM, bool BWD>
 __global__ void __launch_bounds__(kNearWarps * 32) soft_near_kernel(SoftNearArgs a)
 {
     extern __shared__ float gw[];  // backward: kNearWarps x n x K
@@ -555,91 +561,108 @@ __global__ void __launch_bounds__(kNearWarps * 32) soft_near_kernel(SoftNearArgs
     const int n = a.n;
     const float K2 = a.K2;
     const float LK2 = BWD ? (float)(a.dev->L * (double)K2) : 0.f;
-    float *g = gw + (size_t)warp * n * K;
-    if (BWD)
-        for (int idx = lane; idx < n * K; idx += 32) g[idx] = 0.f;
-    __syncwarp();
+    float gacc[BWD ? NM : 1][K];
+#pragma unroll
+    for (int m = 0; m < (BWD ? NM : 1); ++m)
+#pragma unroll
+        for (int c = 0; c < K; ++c) gacc[m][c] = 0.f;
     float M = INFINITY;
     double S64 = 0.0;
     const long long p0 = ((long long)blockIdx.x * kNearWarps + warp) * kNearChunk;
     const long long p1 = min((long long)a.n_near, p0 + kNearChunk);
-    for (long long pi = p0; pi < p1; ++pi) {
-        const int2 pr = a.near[pi];
-        const int i = pr.x, j = pr.y;
-        float D[kSoftMaxN / 32];
-        float dd = 0.f;
+    for (long long pb = p0; pb < p1; pb += kNearIlp) {
+        int ii[kNearIlp], jj[kNearIlp];
+        bool valid[kNearIlp];
 #pragma unroll
-        for (int m = 0; m < kSoftMaxN / 32; ++m) {
-            const int l = lane + 32 * m;
-            D[m] = l < n ? a.X[(size_t)i * n + l] - a.X[(size_t)j * n + l] : 0.f;
-            dd = fmaf(D[m], D[m], dd);
+        for (int e = 0; e < kNearIlp; ++e) {
+            valid[e] = pb + e < p1;
+            const int2 pr = valid[e] ? a.near[pb + e] : a.near[p0];
+            ii[e] = pr.x;
+            jj[e] = pr.y;
         }
-        dd = warp_sumf(dd);
-        float dyl = 0.f;
-        if (lane < K) {
-            const size_t o = (size_t)lane * a.Npad;
-            dyl = (a.Yh[o + i] - a.Yh[o + j]) + (a.Yl[o + i] - a.Yl[o + j]);
-        }
-        float dy[K];
+        float D[kNearIlp][NM], dd[kNearIlp], dyl[kNearIlp];
 #pragma unroll
-        for (int c = 0; c < K; ++c) dy[c] = __shfl_sync(FULL, dyl, c);
-        float r, inv_d2;  // ratio and 1/d^2
-        if (dd >= 1e-30f) {
-            float zz = 0.f;
+        for (int e = 0; e < kNearIlp; ++e) {
+            dd[e] = 0.f;
 #pragma unroll
-            for (int c = 0; c < K; ++c) zz = fmaf(dy[c], dy[c], zz);
-            r = sqrtf(zz / dd);
-            inv_d2 = 1.0f / dd;
-        } else {
-            // too short for FP32 squares: projection and length in FP64
-            double d2 = 0.0, z[K];
-#pragma unroll
-            for (int c = 0; c < K; ++c) z[c] = 0.0;
-            for (int l = lane; l < n; l += 32) {
-                const double Dl = (double)a.X[(size_t)i * n + l] - (double)a.X[(size_t)j * n + l];
-                d2 = fma(Dl, Dl, d2);
-#pragma unroll
-                for (int c = 0; c < K; ++c) z[c] = fma(a.U64[(size_t)c * n + l], Dl, z[c]);
-            }
-            d2 = warp_sum(d2);
-            double zz = 0.0;
-#pragma unroll
-            for (int c = 0; c < K; ++c) {
-                z[c] = warp_sum(z[c]);
-                zz = fma(z[c], z[c], zz);
-            }
-            // scale D and dy by 1/d so the FP32 products below stay in range
-            const double sc = d2 > 0.0 ? 1.0 / sqrt(d2) : 0.0;
-#pragma unroll
-            for (int m = 0; m < kSoftMaxN / 32; ++m) {
+            for (int m = 0; m < NM; ++m) {
                 const int l = lane + 32 * m;
-                D[m] = l < n ? (float)(((double)a.X[(size_t)i * n + l] - (double)a.X[(size_t)j * n + l]) * sc) : 0.f;
+                D[e][m] = l < n ? a.X[(size_t)ii[e] * n + l] - a.X[(size_t)jj[e] * n + l] : 0.f;
+                dd[e] = fmaf(D[e][m], D[e][m], dd[e]);
             }
-#pragma unroll
-            for (int c = 0; c < K; ++c) dy[c] = (float)(z[c] * sc);
-            r = d2 > 0.0 ? (float)sqrt(zz / d2) : NAN;
-            inv_d2 = 1.0f;  // D and dy already carry 1/d each
+            dyl[e] = 0.f;
+            if (lane < K) {
+                const size_t o = (size_t)lane * a.Npad;
+                dyl[e] = (a.Yh[o + ii[e]] - a.Yh[o + jj[e]]) + (a.Yl[o + ii[e]] - a.Yl[o + jj[e]]);
+            }
         }
-        if (!BWD) {
-            if (r == r) {
-                const float am = (M - r) * K2;
-                if (am > 0.f) {
-                    S64 = S64 * (double)ex2_approx(-am) + 1.0;
-                    M = r;
-                } else {
-                    S64 += (double)ex2_approx(fmaxf(am, -200.f));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int e = 0; e < kNearIlp; ++e) dd[e] += __shfl_xor_sync(FULL, dd[e], o);
+#pragma unroll
+        for (int e = 0; e < kNearIlp; ++e) {
+            if (!valid[e]) continue;
+            float dy[K];
+#pragma unroll
+            for (int c = 0; c < K; ++c) dy[c] = __shfl_sync(FULL, dyl[e], c);
+            float r, inv_d2;  // ratio; 1/d^2
+            if (dd[e] >= 1e-30f) {
+                float zz = 0.f;
+#pragma unroll
+                for (int c = 0; c < K; ++c) zz = fmaf(dy[c], dy[c], zz);
+                r = sqrtf(zz / dd[e]);
+                inv_d2 = 1.0f / dd[e];
+            } else {
+                // too short for FP32 squares: projection and length in FP64,
+                // D and dy rescaled by 1/d so the FP32 products stay in range
+                const int i = ii[e], j = jj[e];
+                double d2 = 0.0, z[K];
+#pragma unroll
+                for (int c = 0; c < K; ++c) z[c] = 0.0;
+                for (int l = lane; l < n; l += 32) {
+                    const double Dl = (double)a.X[(size_t)i * n + l] - (double)a.X[(size_t)j * n + l];
+                    d2 = fma(Dl, Dl, d2);
+#pragma unroll
+                    for (int c = 0; c < K; ++c) z[c] = fma(a.U64[(size_t)c * n + l], Dl, z[c]);
                 }
+                d2 = warp_sum(d2);
+                double zz = 0.0;
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    z[c] = warp_sum(z[c]);
+                    zz = fma(z[c], z[c], zz);
+                }
+                const double sc = d2 > 0.0 ? 1.0 / sqrt(d2) : 0.0;
+#pragma unroll
+                for (int c = 0; c < K; ++c) dy[c] = (float)(z[c] * sc);
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    const int l = lane + 32 * m;
+                    D[e][m] = l < n ? (float)(((double)a.X[(size_t)i * n + l] - (double)a.X[(size_t)j * n + l]) * sc)
+                                    : 0.f;
+                }
+                r = d2 > 0.0 ? (float)sqrt(zz / d2) : NAN;
+                inv_d2 = 1.0f;
             }
-        } else {
-            const float pw = ex2_approx(fmaxf(fmaf(r, -K2, LK2), -200.f));
-            const float coef = (r * r >= kFltMin) ? pw * inv_d2 / r : 0.f;
+            if (!BWD) {
+                if (r == r) {
+                    const float am = (M - r) * K2;
+                    if (am > 0.f) {
+                        S64 = S64 * (double)ex2_approx(-am) + 1.0;
+                        M = r;
+                    } else {
+                        S64 += (double)ex2_approx(fmaxf(am, -200.f));
+                    }
+                }
+            } else {
+                const float pw = ex2_approx(fmaxf(fmaf(r, -K2, LK2), -200.f));
+                const float coef = (r * r >= kFltMin) ? pw * inv_d2 / r : 0.f;
 #pragma unroll
-            for (int m = 0; m < kSoftMaxN / 32; ++m) {
-                const int l = lane + 32 * m;
-                if (l < n) {
-                    const float cD = coef * D[m];
+                for (int m = 0; m < (BWD ? NM : 1); ++m) {
+                    const float cD = coef * D[e][m];
 #pragma unroll
-                    for (int c = 0; c < K; ++c) g[l * K + c] = fmaf(cD, dy[c], g[l * K + c]);
+                    for (int c = 0; c < K; ++c) gacc[m][c] = fmaf(cD, dy[c], gacc[m][c]);
                 }
             }
         }
@@ -659,6 +682,14 @@ __global__ void __launch_bounds__(kNearWarps * 32) soft_near_kernel(SoftNearArgs
             a.part[blockIdx.x] = pt;
         }
     } else {
+        float *g = gw + (size_t)warp * n * K;
+#pragma unroll
+        for (int m = 0; m < (BWD ? NM : 1); ++m) {
+            const int l = lane + 32 * m;
+            if (l < n)
+#pragma unroll
+                for (int c = 0; c < K; ++c) g[l * K + c] = gacc[m][c];
+        }
         __syncthreads();
         float2 *out = a.GP + (size_t)blockIdx.x * K * n;
         for (int o = threadIdx.x; o < n * K; o += blockDim.x) {
@@ -673,44 +704,92 @@ __global__ void __launch_bounds__(kNearWarps * 32) soft_near_kernel(SoftNearArgs
 
 // ------------------------------------------------------- gradient blocks ---
 
-// One block per point block B: z_B from the tile partials (rows of tiles
-// (B, J), negated columns of tiles (I, B)), FP32 sums of 8 tiles carried in
-// hi + lo, then the block's share of sum_i (x_i - xbar) z_i^T with error-free
-// products, written as hi + lo pairs GP[B][c * n + l].
+// Gradient of the far pairs for point block B = blockIdx.x (one wave of
+// nb blocks), in two phases.
+// (1) z_i, i in block B: the rows of tiles (B, J), J >= B, plus the (negated)
+//     columns of tiles (I, B), I <= B.  The nb + 1 terms of each entry are
+//     dealt to 8 thread groups, accumulated in hi + lo and merged in a fixed
+//     order, so the sum is reproducible and (near) exact.
+// (2) g_cl = sum_i (x_il - xbar_l) z_ic with error-free products: thread
+//     (group q, coordinate l) takes the rows q, q + 8, ... (loads issued
+//     together) for all K components; the groups merge in a fixed order;
+//     GP[B][c * n + l] = (hi, lo).
+constexpr int kZGroups = 8;
+
 template <int K>
-__global__ void __launch_bounds__(256) soft_grad_kernel(const float *P, int nb, const float *X, const float *center,
-                                                        int N, int n, float2 *GP)
+__global__ void __launch_bounds__(kZGroups * T, 1) soft_grad_kernel(const float *P, int nb, const float *X,
+                                                                    const float *center, int N, int n, float2 *GP)
 {
-    __shared__ float zh[K * T], zl[K * T];
+    extern __shared__ float2 part_[];  // kZGroups x K x T (40 KB at K = 5)
+    auto part = reinterpret_cast<float2 (*)[K][T]>(part_);
+    __shared__ float zh[K][T], zl[K][T];
     const int B = blockIdx.x;
-    for (int e = threadIdx.x; e < K * T; e += blockDim.x) {
-        float hi = 0.f, lo = 0.f, chunk = 0.f;
-        int cnt = 0;
-        for (int J = B; J < nb; ++J) {
-            chunk += P[(size_t)tile_index(B, J, nb) * 2 * K * T + e];
-            if (++cnt == 8) { df_add(hi, lo, chunk); chunk = 0.f; cnt = 0; }
+    const int a = threadIdx.x % T, q = threadIdx.x / T;
+    {
+        float hi[K], lo[K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) hi[c] = lo[c] = 0.f;
+        const int nterms = nb + 1;  // J = B..nb-1 (rows), then I = 0..B (columns)
+#pragma unroll 2
+        for (int t = q; t < nterms; t += kZGroups) {
+            const int J = B + t;
+            const float *src = J < nb ? P + (size_t)tile_index(B, J, nb) * 2 * K * T + a
+                                      : P + (size_t)tile_index(t - (nb - B), B, nb) * 2 * K * T + (size_t)K * T + a;
+            float v[K];
+#pragma unroll
+            for (int c = 0; c < K; ++c) v[c] = src[c * T];
+#pragma unroll
+            for (int c = 0; c < K; ++c) df_add(hi[c], lo[c], v[c]);
         }
-        for (int I = 0; I <= B; ++I) {
-            chunk += P[(size_t)tile_index(I, B, nb) * 2 * K * T + K * T + e];
-            if (++cnt == 8) { df_add(hi, lo, chunk); chunk = 0.f; cnt = 0; }
+#pragma unroll
+        for (int c = 0; c < K; ++c) part[q][c][a] = make_float2(hi[c], lo[c]);
+        __syncthreads();
+        if (q < K) {
+            const int c = q;  // group q finishes component c = q
+            float h = part[0][c][a].x, l = part[0][c][a].y;
+            for (int g2 = 1; g2 < kZGroups; ++g2) df_merge(h, l, part[g2][c][a].x, part[g2][c][a].y);
+            df_norm(h, l);
+            zh[c][a] = h;
+            zl[c][a] = l;
         }
-        df_add(hi, lo, chunk);
-        df_norm(hi, lo);
-        zh[e] = hi;
-        zl[e] = lo;
+        __syncthreads();
     }
-    __syncthreads();
+    constexpr int RPG = T / kZGroups;  // rows per group
     const int rows = min(T, N - B * T);
-    for (int o = threadIdx.x; o < n * K; o += blockDim.x) {
-        const int c = o / n, l = o % n;
-        const float cl = center[l];
-        float hi = 0.f, lo = 0.f;
-        for (int a = 0; a < rows; ++a) {
-            const float x = __fsub_rn(X[(size_t)(B * T + a) * n + l], cl);
-            df_fma(hi, lo, x, zh[c * T + a], zl[c * T + a]);
+    for (int l0 = 0; l0 < n; l0 += T) {
+        const int l = l0 + a;
+        float hi[K], lo[K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) hi[c] = lo[c] = 0.f;
+        if (l < n) {
+            const float cl = center[l];
+            float xv[RPG];
+#pragma unroll
+            for (int t = 0; t < RPG; ++t) {
+                const int row = q + kZGroups * t;
+                xv[t] = row < rows ? X[(size_t)(B * T + row) * n + l] : 0.f;
+            }
+#pragma unroll
+            for (int t = 0; t < RPG; ++t) {
+                const int row = q + kZGroups * t;
+                if (row < rows) {
+                    const float x = __fsub_rn(xv[t], cl);
+#pragma unroll
+                    for (int c = 0; c < K; ++c) df_fma(hi[c], lo[c], x, zh[c][row], zl[c][row]);
+                }
+            }
         }
-        df_norm(hi, lo);
-        GP[(size_t)B * K * n + o] = make_float2(hi, lo);
+#pragma unroll
+        for (int c = 0; c < K; ++c) part[q][c][a] = make_float2(hi[c], lo[c]);
+        __syncthreads();
+        if (q < K && l < n) {
+            const int c = q;
+            float h = part[0][c][a].x, lw = part[0][c][a].y;
+            for (int g2 = 1; g2 < kZGroups; ++g2) df_merge(h, lw, part[g2][c][a].x, part[g2][c][a].y);
+            df_norm(h, lw);
+            GP[(size_t)B * K * n + (size_t)c * n + l] = make_float2(h, lw);
+        }
+        __syncthreads();
     }
 }
 
@@ -720,6 +799,7 @@ __global__ void __launch_bounds__(256) soft_gsum_kernel(const float2 *GP, int np
     const int o = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (o >= nK) return;
     float hi = 0.f, lo = 0.f;
+#pragma unroll 4
     for (int p = lane; p < nparts; p += 32) {
         const float2 v = GP[(size_t)p * nK + o];
         df_merge(hi, lo, v.x, v.y);
@@ -915,7 +995,7 @@ struct SoftKernels {
             e = cudaFuncSetAttribute(soft_pass_kernel<K, kBwdWarps, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kSmemLimit);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(soft_near_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(soft_near_kernel<K, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kNearWarps * kSoftMaxN * K * 4);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(soft_step_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -923,6 +1003,9 @@ struct SoftKernels {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(ydf_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      2 * K * kSoftMaxN * 4);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(soft_grad_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kZGroups * K * T * sizeof(float2)));
         return e;
     }
     static cudaError_t ydf(const float *X, int N, int n, const double *U64, int Npad, float *Yh, float *Yl, int grid,
@@ -939,18 +1022,26 @@ struct SoftKernels {
             soft_pass_kernel<K, kFwdWarps, false><<<grid, (kFwdWarps + 1) * 32, fwd_smem(K, a.stages), s>>>(a);
         return cudaGetLastError();
     }
-    static cudaError_t near(const SoftNearArgs &a, bool bwd, int grid, cudaStream_t s)
+    template <int NM>
+    static void near_nm(const SoftNearArgs &a, bool bwd, int grid, cudaStream_t s)
     {
         if (bwd)
-            soft_near_kernel<K, true><<<grid, kNearWarps * 32, kNearWarps * a.n * K * 4, s>>>(a);
+            soft_near_kernel<K, NM, true><<<grid, kNearWarps * 32, kNearWarps * a.n * K * 4, s>>>(a);
         else
-            soft_near_kernel<K, false><<<grid, kNearWarps * 32, 0, s>>>(a);
+            soft_near_kernel<K, NM, false><<<grid, kNearWarps * 32, 0, s>>>(a);
+    }
+    static cudaError_t near(const SoftNearArgs &a, bool bwd, int grid, cudaStream_t s)
+    {
+        if (a.n <= 128)
+            near_nm<4>(a, bwd, grid, s);
+        else
+            near_nm<16>(a, bwd, grid, s);
         return cudaGetLastError();
     }
     static cudaError_t grad(const float *P, int nb, const float *X, const float *center, int N, int n, float2 *GP,
                             cudaStream_t s)
     {
-        soft_grad_kernel<K><<<nb, 256, 0, s>>>(P, nb, X, center, N, n, GP);
+        soft_grad_kernel<K><<<nb, kZGroups * T, kZGroups * K * T * sizeof(float2), s>>>(P, nb, X, center, N, n, GP);
         return cudaGetLastError();
     }
     static cudaError_t step(const SoftStepArgs &a, cudaStream_t s)

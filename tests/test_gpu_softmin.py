@@ -18,8 +18,9 @@ a wrong weight or a transposed operand fails while rounding does not:
       |dp| <= p ((|dr| + |dL|)/tau + u (L + r)/tau + 2^-21),
   the coefficient and product add rho_t = gamma_{n+3} + 2^-21 + 4u, the
   per-warp FP32 sums gamma_32, and the Laplacian form (row and column sums
-  of c_ij (y_i - y_j), size p/d, in FP32 trees of depth <= 33, times
-  x - mean) adds sqrt(k) gamma_34 p (nu_i + nu_j)/d_ij.
+  of c_ij (y_i - y_j), size p/d, in FP32 trees of depth <= 24 within a
+  tile and extended precision across tiles, times x - mean) adds, with
+  margin, sqrt(k) gamma_34 p (nu_i + nu_j)/d_ij.
 Each bound is taken x1.2.  The finite-difference check uses h = 1e-3 with a
 tolerance of 2e-2 relative (truncation ~ h^2/tau^2 at tau = 0.01).
 """

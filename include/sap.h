@@ -189,16 +189,29 @@ sap_status sap_get_history(sap_handle h, double *hist, int64_t *argmins,
                            int32_t capacity);
 
 /*
- * Dimension estimation (Sec. VI-A): run SAP for every k = 1..k_max (k_max <=
- * min(n, 32)) from the first k columns of U0 (n x k_max column-major FP64,
- * orthonormal), iters iterations each with step alpha; ratios_out[k-1]
- * receives the min ratio of the final basis for k, and k_out the smallest k
- * whose ratio exceeds threshold (strictly), or -1.  All k run together: one
- * launch per stage covers every basis.  Leaves the handle's basis unchanged.
+ * Dimension estimation (Sec. VI-A): run SAP for every k = 1..k_max from the
+ * first k columns of U0 (n x k_max column-major FP64, orthonormal), iters
+ * iterations each with step alpha; ratios_out[k-1] (nullable) receives the
+ * min ratio of the final basis for k, and k_out (nullable) the smallest k
+ * whose ratio exceeds threshold (strictly), or -1.  FP32 or BF16 data;
+ * k_max <= 20 (the padded widths of all bases fill one 256-wide
+ * tensor-core product).  All bases advance together: each iteration is one
+ * product for all bases, then every basis's pass, recheck and update on
+ * concurrent branches of one CUDA graph.  Leaves the handle's own basis
+ * unchanged (its watch list restarts).  Synchronises.
  */
 sap_status sap_estimate_dim(sap_handle h, const double *U0, int32_t k_max,
                             int32_t iters, double alpha, double threshold,
                             int32_t *k_out, double *ratios_out);
+
+/* History of basis k (1 <= k <= k_max) in the last sap_estimate_dim: the min
+ * ratio of U_0..U_iters and the argmin pairs, as for sap_get_history. */
+sap_status sap_get_sweep_history(sap_handle h, int32_t k, double *hist,
+                                 int64_t *argmins, int32_t capacity);
+
+/* Final basis of k (1 <= k <= k_max) in the last sap_estimate_dim: n x k
+ * column-major FP64 into U_out (host, or device when out_is_device). */
+sap_status sap_get_sweep_basis(sap_handle h, int32_t k, double *U_out, int out_is_device);
 
 /*
  * The projected data under the current basis (Sec. V shows such projections):

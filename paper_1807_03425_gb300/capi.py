@@ -81,6 +81,8 @@ def load_library():
         "sap_run": ([vp, f64, i32, vp, vp], i32),
         "sap_get_history": ([vp, vp, vp, i32], i32),
         "sap_estimate_dim": ([vp, vp, i32, i32, f64, f64, i32p, vp], i32),
+        "sap_get_sweep_history": ([vp, i32, vp, vp, i32], i32),
+        "sap_get_sweep_basis": ([vp, i32, vp, i32], i32),
         "sap_project": ([vp, vp, i32], i32),
         "sap_min_secant_noalloc": ([vp, i64, i32, vp, i32, f64, vp, i64p, i64p, f64p], i32),
         "sap_get_stats": ([vp, ctypes.POINTER(Stats)], i32),
@@ -251,6 +253,22 @@ def sap_estimate_dim(h, U0, iters, alpha, threshold):
     return kout.value, ratios
 
 
+def sap_get_sweep_history(h, k, count):
+    hist = np.empty(count, dtype=np.float64)
+    am = np.empty((count, 2), dtype=np.int64)
+    _check(h, load_library().sap_get_sweep_history(h, int(k), hist.ctypes.data_as(ctypes.c_void_p),
+                                                   am.ctypes.data_as(ctypes.c_void_p), int(count)))
+    return hist, am
+
+
+def sap_get_sweep_basis(h, k, n, out=None):
+    if out is None:
+        out = np.empty((k, n), dtype=np.float64)
+    p, dev = _ptr(out)
+    _check(h, load_library().sap_get_sweep_basis(h, int(k), p, dev))
+    return out
+
+
 def sap_project(h, out):
     """out: (N, k) float32 NumPy array or torch CUDA tensor."""
     p, dev = _ptr(out)
@@ -385,6 +403,12 @@ class Sap:
 
     def estimate_dim(self, U0, iters, alpha, threshold):
         return sap_estimate_dim(self.h, U0, iters, alpha, threshold)
+
+    def sweep_history(self, k, count):
+        return sap_get_sweep_history(self.h, k, count)
+
+    def sweep_basis(self, k):
+        return sap_get_sweep_basis(self.h, k, self.n)
 
     def project(self, out=None):
         if out is None:

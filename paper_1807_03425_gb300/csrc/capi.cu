@@ -11,6 +11,7 @@
 #include "sap_internal.cuh"
 #include "restructured.cuh"
 #include "softmin.cuh"
+#include "sweep.cuh"
 #include "../../include/sap.h"
 
 #include <cuda_bf16.h>
@@ -58,6 +59,7 @@ struct sap_ctx {
     int k = 0, KP = 0;
     double *U64 = nullptr;
     float *U32 = nullptr;
+    float *U32lo = nullptr;   // fl(U64 - U32), for the extended-precision recheck
 
     int2 *tiles = nullptr;   // plain-form point blocks
     int ntiles = 0;
@@ -82,6 +84,7 @@ struct sap_ctx {
 
     RestrState rs;           // restructured-form buffers (restructured.cuh)
     SoftState ss;            // soft-min buffers (softmin.cuh)
+    SweepState *sw = nullptr; // dimension sweep (sweep.cuh)
 
     long long launches = 0;
     std::vector<GraphEntry> graphs;
@@ -246,7 +249,7 @@ sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only)
         SelectUpdateArgs u;
         u.X = f64 ? (const void *)h->X64 : (const void *)h->X32;
         u.x_is_f64 = f64; u.N = (int)h->N; u.n = h->n;
-        u.U64 = h->U64; u.U32 = h->U32; u.KP = h->KP;
+        u.U64 = h->U64; u.U32 = h->U32; u.U32lo = h->U32lo; u.KP = h->KP;
         u.Uhi = h->rs.Uhi; u.Ulo = h->rs.Ulo; u.NP = h->rs.NP;
         u.split_bf16 = h->split == SAP_SPLIT_BF16; u.split_scale = h->split == SAP_SPLIT_BF16 ? 256.f : 2048.f;
         u.k = h->k; u.alpha = alpha; u.mode = (int)h->mode; u.eval_only = eval_only;
@@ -335,6 +338,7 @@ int handle_sms(sap_handle h) { return h->sms; }
 ProbState *handle_state(sap_handle h) { return h->st; }
 const float *handle_x32(sap_handle h) { return h->X32; }
 const float *handle_u32(sap_handle h) { return h->U32; }
+const float *handle_u32lo(sap_handle h) { return h->U32lo; }
 int2 *handle_cand1(sap_handle h) { return h->cand1; }
 int2 *handle_cand2(sap_handle h) { return h->cand2; }
 long long handle_cap(sap_handle h) { return h->cap; }
@@ -368,6 +372,21 @@ float *handle_u32_mut(sap_handle h) { return h->U32; }
 sap_status handle_reset_state(sap_handle h) { return reset_state(h); }
 int handle_profiling(sap_handle h) { return h->profiling ? 1 : 0; }
 long long handle_launches(sap_handle h) { return h->launches; }
+SweepState *&sweep_state(sap_handle h) { return h->sw; }
+int handle_mode(sap_handle h) { return (int)h->mode; }
+Cert handle_seed_cert(int n, int k) { return cert_plain_f32(n, k); }
+sap_status handle_check_status(sap_handle h, ProbState *st)
+{
+    int status = 0;
+    CK(cudaMemcpy(&status, &st->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) {
+        CK(cudaMemset(&st->status, 0, sizeof(int)));
+        if (status & ST_NO_SECANT) return fail(h, SAP_E_NO_SECANT, "every pair is excluded");
+        if (status & ST_TIMEOUT) return fail(h, SAP_E_TIMEOUT, "a device-side wait gave up");
+        if (status & ST_OVERFLOW) return fail(h, SAP_E_UNSUPPORTED, "candidate list overflow (too many near-ties)");
+    }
+    return SAP_OK;
+}
 void handle_add_launches(sap_handle h, long long delta) { h->launches += delta; }
 } // namespace sap
 
@@ -403,7 +422,8 @@ sap_status sap_destroy(sap_handle h)
     for (auto e : h->event_pool) cudaEventDestroy(e);
     restructured_free(h);
     softmin_free(h);
-    dfree(h->X32); dfree(h->X64); dfree(h->U64); dfree(h->U32);
+    sweep_free(h->sw);
+    dfree(h->X32); dfree(h->X64); dfree(h->U64); dfree(h->U32); dfree(h->U32lo);
     dfree(h->tiles); dfree(h->cand1); dfree(h->cand2); dfree(h->partials);
     dfree(h->work); dfree(h->st); dfree(h->hist); dfree(h->am);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -581,11 +601,12 @@ sap_status sap_set_basis(sap_handle h, const double *U, int32_t k, int u_is_devi
     CK(cudaStreamSynchronize(h->stream));
     if (k != h->k) {
         drop_graphs(h);
-        dfree(h->U64); dfree(h->U32); dfree(h->work);
+        dfree(h->U64); dfree(h->U32); dfree(h->U32lo); dfree(h->work);
         h->k = k;
         h->KP = padded_stride(k);  // pad columns stay zero
         CK(dalloc(&h->U64, (size_t)n * k));
         CK(dalloc(&h->U32, (size_t)n * h->KP));
+        CK(dalloc(&h->U32lo, (size_t)n * h->KP));
         h->work_elems = (size_t)(kMaxK + 1) * n;
         CK(dalloc(&h->work, h->work_elems));
         if (h->dt != SAP_F64) {
@@ -594,10 +615,16 @@ sap_status sap_set_basis(sap_handle h, const double *U, int32_t k, int u_is_devi
         }
     }
     CK(cudaMemcpy(h->U64, Uh.data(), Uh.size() * sizeof(double), cudaMemcpyHostToDevice));
-    std::vector<float> u32((size_t)n * h->KP, 0.f);
+    std::vector<float> u32((size_t)n * h->KP, 0.f), u32lo((size_t)n * h->KP, 0.f);
     for (int l = 0; l < n; ++l)
-        for (int c = 0; c < k; ++c) u32[(size_t)l * h->KP + c] = (float)Uh[(size_t)c * n + l];
+        for (int c = 0; c < k; ++c) {
+            const double v = Uh[(size_t)c * n + l];
+            const float f = (float)v;
+            u32[(size_t)l * h->KP + c] = f;
+            u32lo[(size_t)l * h->KP + c] = (float)(v - (double)f);
+        }
     CK(cudaMemcpy(h->U32, u32.data(), u32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->U32lo, u32lo.data(), u32lo.size() * sizeof(float), cudaMemcpyHostToDevice));
     if (h->dt != SAP_F64) {
         sap_status s = restructured_upload_basis(h, Uh.data());
         if (s != SAP_OK) return s;
@@ -831,8 +858,22 @@ sap_status sap_estimate_dim(sap_handle h, const double *U0, int32_t k_max, int32
                             double alpha, double threshold, int32_t *k_out, double *ratios_out)
 {
     CHECK_HANDLE(h);
-    (void)U0; (void)k_max; (void)iters; (void)alpha; (void)threshold; (void)k_out; (void)ratios_out;
-    return fail(h, SAP_E_UNSUPPORTED, "dimension sweep not built yet");
+    if (!k_out && !ratios_out) return fail(h, SAP_E_ARG, "no output");
+    const sap_status s = sweep_run(h, U0, k_max, iters, alpha, threshold, k_out, ratios_out);
+    if (s != SAP_OK) return s;
+    return reset_state(h);  // the handle's own watch list and bounds start afresh
+}
+
+sap_status sap_get_sweep_history(sap_handle h, int32_t k, double *hist, int64_t *argmins, int32_t capacity)
+{
+    CHECK_HANDLE(h);
+    return sweep_history(h, k, hist, argmins, capacity);
+}
+
+sap_status sap_get_sweep_basis(sap_handle h, int32_t k, double *U_out, int out_is_device)
+{
+    CHECK_HANDLE(h);
+    return sweep_basis(h, k, U_out, out_is_device);
 }
 
 } // extern "C"

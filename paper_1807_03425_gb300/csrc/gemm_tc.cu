@@ -21,6 +21,8 @@
 #include "tc_ptx.cuh"
 #include "gemm_tc.cuh"
 
+#include <algorithm>
+
 namespace sap {
 namespace {
 
@@ -66,6 +68,9 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
     tc::tc_fence_after();
     const uint32_t tbase = *tslot;
     const int m0 = blockIdx.x * GM;
+    // this CTA's K slice
+    const int kb0 = (int)(((long long)blockIdx.y * a.nkb) / a.ksplit);
+    const int nkb = (int)(((long long)(blockIdx.y + 1) * a.nkb) / a.ksplit) - kb0;
 
     auto stage_a_hi = [&](int s) { return smem + (size_t)s * stage_bytes; };
     auto stage_a_lo = [&](int s) { return smem + (size_t)s * stage_bytes + a_bytes; };
@@ -75,17 +80,18 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
     if (warp == 0 && lane == 0) {
         // TMA producer
         int issued = 0;
-        for (int kb = 0; kb < a.nkb; ++kb) {
+        for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % S;
             if (kb >= S && !tc::mbar_wait_bounded(&empty[s], ((kb / S) & 1) ^ 1, kWaitBudget)) {
                 atomicExch(&abort_sh, 1);
                 break;
             }
+            const int kx = (kb0 + kb) * GK;
             tc::mbar_expect_tx(&full[s], stage_bytes);
-            tc::tma_load_2d(stage_a_hi(s), &a.ta_hi, kb * GK, m0, &full[s]);
-            tc::tma_load_2d(stage_a_lo(s), &a.ta_lo, kb * GK, m0, &full[s]);
-            tc::tma_load_2d(stage_b_hi(s), &a.tb_hi, kb * GK, 0, &full[s]);
-            tc::tma_load_2d(stage_b_lo(s), &a.tb_lo, kb * GK, 0, &full[s]);
+            tc::tma_load_2d(stage_a_hi(s), &a.ta_hi, kx, m0, &full[s]);
+            tc::tma_load_2d(stage_a_lo(s), &a.ta_lo, kx, m0, &full[s]);
+            tc::tma_load_2d(stage_b_hi(s), &a.tb_hi, kx, 0, &full[s]);
+            tc::tma_load_2d(stage_b_lo(s), &a.tb_lo, kx, 0, &full[s]);
             ++issued;
         }
         // make sure no copy of ours is still in flight before the CTA exits
@@ -94,7 +100,7 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         const uint32_t idesc = tc::idesc_f16(GM, KPG, a.ab_bf16);
-        for (int kb = 0; kb < a.nkb; ++kb) {
+        for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % S;
             if (!tc::mbar_wait_bounded(&full[s], (kb / S) & 1, kWaitBudget)) {
                 atomicExch(&abort_sh, 1);
@@ -130,10 +136,17 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
             tc::tmem_ld8(lane_base + KPG + c0, d2);
             if (row < a.Npad) {
                 // component-major (Y^T): consecutive lanes write consecutive rows
+                if (a.ksplit == 1) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (c0 + q < a.KY)
-                        a.Y[(size_t)(c0 + q) * a.Npad + row] = fmaf(d2[q], a.lo_scale, d1[q]) * a.out_scale;
+                    for (int q = 0; q < 8; ++q)
+                        if (c0 + q < a.KY)
+                            a.Y[(size_t)(c0 + q) * a.Npad + row] = fmaf(d2[q], a.lo_scale, d1[q]) * a.out_scale;
+                } else {
+                    float *dst = a.Ypart + (size_t)blockIdx.y * a.KY * a.Npad;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (c0 + q < a.KY) dst[(size_t)(c0 + q) * a.Npad + row] = fmaf(d2[q], a.lo_scale, d1[q]);
+                }
             }
         }
     } else if (threadIdx.x == 0) {
@@ -142,6 +155,16 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, ncols);
+}
+
+// Y = (sum of the K slices, in slice order) * out_scale.
+__global__ void ksum_kernel(const float *Ypart, int ksplit, size_t count, float out_scale, float *Y)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        float s = Ypart[e];
+        for (int q = 1; q < ksplit; ++q) s += Ypart[(size_t)q * count + e];
+        Y[e] = s * out_scale;
+    }
 }
 
 } // namespace
@@ -167,7 +190,16 @@ cudaError_t gemm_configure()
 cudaError_t launch_gemm_y(const GemmArgs &a, cudaStream_t s)
 {
     const size_t shm = gemm_smem_bytes(a.KPG, a.stages);
-    gemm_y_kernel<<<a.Npad / GM, 128, shm, s>>>(a);
+    const int ksplit = a.ksplit < 1 ? 1 : a.ksplit;
+    if (ksplit > a.nkb) return cudaErrorInvalidValue;
+    GemmArgs b = a;
+    b.ksplit = ksplit;
+    gemm_y_kernel<<<dim3(a.Npad / GM, ksplit), 128, shm, s>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || ksplit == 1) return e;
+    const size_t count = (size_t)a.KY * a.Npad;
+    ksum_kernel<<<(unsigned)std::min<size_t>((count + 255) / 256, 2048), 256, 0, s>>>(a.Ypart, ksplit, count,
+                                                                                    a.out_scale, a.Y);
     return cudaGetLastError();
 }
 

@@ -19,11 +19,15 @@ struct GemmArgs {
     float lo_scale;             // 2^-s: weight of the low-part accumulator
     float out_scale;            // 1/scale of X
     ProbState *st;              // receives ST_TIMEOUT if a wait gives up
+    int ksplit;                 // K slices (grid.y); > 1: raw slices go to Ypart
+    float *Ypart;               // ksplit x KY x Npad FP32 (ksplit > 1)
 };
 
 size_t gemm_smem_bytes(int KPG, int stages);
 int gemm_pick_stages(int KPG, int nkb);
 cudaError_t gemm_configure();
+// Y = X U; with ksplit > 1 each K slice accumulates separately (shorter FP32
+// chains) and a second kernel sums the slices into Y.
 cudaError_t launch_gemm_y(const GemmArgs &a, cudaStream_t s);
 
 } // namespace sap

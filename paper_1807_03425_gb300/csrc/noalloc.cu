@@ -181,6 +181,7 @@ extern "C" sap_status sap_min_secant_noalloc(const float *X, int64_t N, int32_t 
     q.n = n;
     q.U64 = const_cast<double *>(U);
     q.U32 = g->U32;
+    q.U32lo = nullptr;
     q.KP = KP;
     q.Uhi = nullptr;
     q.Ulo = nullptr;

@@ -459,6 +459,7 @@ struct ExplArgs {
     const float *X;
     int N, n;
     const float *U32;  // n x KP
+    const float *U32lo;  // n x KP, fl(U64 - U32) (extended-precision variant)
     int k, KP;
     const int2 *cand1;
     unsigned int cap1;
@@ -567,30 +568,129 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
     }
 }
 
-template <int K>
-cudaError_t launch_expl_k(const ExplArgs &x, int grid, cudaStream_t s)
+// ---- extended-precision explicit recheck (large n)
+__device__ __forceinline__ void xs_two_sum(float a, float b, float &s, float &e)
 {
-    explicit_recheck_kernel<K><<<grid, 256, 0, s>>>(x);
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) += x * (yh + yl), the product x * yh error-free
+__device__ __forceinline__ void xs_fma(float &hi, float &lo, float x, float yh, float yl)
+{
+    const float p = __fmul_rn(x, yh);
+    const float pe = fmaf(x, yh, -p);
+    float s, e;
+    xs_two_sum(hi, p, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, fmaf(x, yl, pe)));
+}
+
+// The same tier for large n, where the FP32 dot products' certified error
+// (gamma_{n+3}) would pass too many pairs on: D = fl(x_i - x_j) in FP32, then
+// |D|^2 and U^T D accumulated as hi + lo FP32 pairs with error-free products
+// against the hi + lo FP32 basis.  Since U is orthonormal, the rounding of D
+// moves U^T D by at most 2^-24 d and d by 2^-24 d, so |r~ - r| <= 2^-24 +
+// 2 * 2^-24 r plus the final FP32 roundings (cert_explicit_df).  One warp per
+// pair, K + 1 extended accumulators per lane.
+template <int K>
+__global__ void __launch_bounds__(256) explicit_df_kernel(ExplArgs a)
+{
+    __shared__ float red[32];
+    __shared__ int scan[33];
+    __shared__ int base_sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned int c1 = (unsigned int)a.st->cnt1;
+    if (c1 > a.cap1) c1 = a.cap1;
+    const long long total = (long long)c1 + a.n_near;
+    const float seed = load_pos_float(&a.st->seed_ub);
+    for (long long base = (long long)blockIdx.x * 8; base < total; base += (long long)gridDim.x * 8) {
+        const long long idx = base + warp;
+        const bool valid = idx < total;
+        const int2 pr = valid ? (idx < c1 ? a.cand1[idx] : a.near[idx - c1]) : make_int2(0, 0);
+        float zh[K + 1], zl[K + 1];
+#pragma unroll
+        for (int q = 0; q <= K; ++q) zh[q] = zl[q] = 0.f;
+        if (valid) {
+#pragma unroll 2
+            for (int l = lane; l < a.n; l += 32) {
+                const float D = a.X[(size_t)pr.x * a.n + l] - a.X[(size_t)pr.y * a.n + l];
+                xs_fma(zh[K], zl[K], D, D, 0.f);
+                const float *uh = a.U32 + (size_t)l * a.KP, *ul = a.U32lo + (size_t)l * a.KP;
+#pragma unroll
+                for (int c = 0; c < K; ++c) xs_fma(zh[c], zl[c], D, uh[c], ul[c]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q <= K; ++q) {
+                const float h2 = __shfl_xor_sync(0xffffffffu, zh[q], o);
+                const float l2 = __shfl_xor_sync(0xffffffffu, zl[q], o);
+                float s, e;
+                xs_two_sum(zh[q], h2, s, e);
+                zh[q] = s;
+                zl[q] = __fadd_rn(zl[q], __fadd_rn(l2, e));
+            }
+        const float dd = zh[K] + zl[K];
+        float zz = 0.f;
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            const float z = zh[c] + zl[c];
+            zz = fmaf(z, z, zz);
+        }
+        const int code = !valid ? 0 : (dd < 1e-30f ? 2 : 1);  // 2: too short for FP32
+        const float rr = code == 1 ? sqrtf(zz / dd) : INFINITY;
+        const float bmin = block_min(rr, red);
+        float U = fminf(seed, load_pos_float(&a.st->run_ub2));
+        if (bmin < INFINITY) {
+            const float ub = cert_upper(bmin, a.cert);
+            if (threadIdx.x == 0) atomic_min_pos_float(&a.st->run_ub2, ub);
+            U = fminf(U, ub);
+        }
+        const float th = cert_emit_threshold(U, a.cert);
+        const int cnt = (lane == 0 && (code == 2 || (code == 1 && rr <= th))) ? 1 : 0;
+        int tot;
+        const int off = block_exclusive_scan(cnt, scan, &tot);
+        if (tot == 0) continue;
+        if (threadIdx.x == 0) base_sh = (int)atomicAdd((unsigned int *)&a.st->cnt2, (unsigned int)tot);
+        __syncthreads();
+        if (cnt) {
+            const long long pos = (long long)(unsigned int)base_sh + off;
+            if (pos < a.cap2) a.cand2[pos] = pr;
+            else atomicOr(&a.st->status, ST_OVERFLOW);
+        }
+        __syncthreads();
+    }
+}
+
+template <int K>
+cudaError_t launch_expl_k(const ExplArgs &x, bool df, int grid, cudaStream_t s)
+{
+    if (df)
+        explicit_df_kernel<K><<<grid, 256, 0, s>>>(x);
+    else
+        explicit_recheck_kernel<K><<<grid, 256, 0, s>>>(x);
     return cudaGetLastError();
 }
 
-cudaError_t launch_explicit(const ExplArgs &x, int grid, cudaStream_t s)
+cudaError_t launch_explicit(const ExplArgs &x, bool df, int grid, cudaStream_t s)
 {
     switch (x.k) {
-    case 1: return launch_expl_k<1>(x, grid, s);
-    case 2: return launch_expl_k<2>(x, grid, s);
-    case 3: return launch_expl_k<3>(x, grid, s);
-    case 4: return launch_expl_k<4>(x, grid, s);
-    case 5: return launch_expl_k<5>(x, grid, s);
-    case 6: return launch_expl_k<6>(x, grid, s);
-    case 7: return launch_expl_k<7>(x, grid, s);
-    case 8: return launch_expl_k<8>(x, grid, s);
+    case 1: return launch_expl_k<1>(x, df, grid, s);
+    case 2: return launch_expl_k<2>(x, df, grid, s);
+    case 3: return launch_expl_k<3>(x, df, grid, s);
+    case 4: return launch_expl_k<4>(x, df, grid, s);
+    case 5: return launch_expl_k<5>(x, df, grid, s);
+    case 6: return launch_expl_k<6>(x, df, grid, s);
+    case 7: return launch_expl_k<7>(x, df, grid, s);
+    case 8: return launch_expl_k<8>(x, df, grid, s);
     default: break;
     }
-    if (x.k <= 12) return launch_expl_k<12>(x, grid, s);
-    if (x.k <= 16) return launch_expl_k<16>(x, grid, s);
-    if (x.k <= 24) return launch_expl_k<24>(x, grid, s);
-    return launch_expl_k<32>(x, grid, s);
+    if (x.k <= 12) return launch_expl_k<12>(x, df, grid, s);
+    if (x.k <= 16) return launch_expl_k<16>(x, df, grid, s);
+    if (x.k <= 24) return launch_expl_k<24>(x, df, grid, s);
+    return launch_expl_k<32>(x, df, grid, s);
 }
 
 // -------------------------------------------------------------- host side --
@@ -654,17 +754,22 @@ void dfree(T_ *&p)
 
 // Bound on |y~_c - y_c| per unit ||fl(x - mean)|| (see gemm_tc.cu):
 // centring and epilogue roundings, the split residuals and dropped low
-// product, and the FP32 accumulation chain of the high product
-// (ceil(NP/16) MMAs, plus slack for the in-instruction adder tree), each
-// accumulation step bounded by 2^-23 (truncation) of twice the running
-// magnitude.  Times 1.25 for margin.
-double y_error_unit(int NP, bool bf16)
+// product, the FP32 accumulation chain of the high product within a K slice
+// (ceil(NP/(16 ksplit)) MMAs, plus slack for the in-instruction adder
+// tree), each accumulation step bounded by 2^-23 (truncation) of twice the
+// running magnitude, and the FP32 sum of the slices.  Times 1.25 for margin.
+double y_error_unit(int NP, bool bf16, int ksplit)
 {
     const double u = std::ldexp(1.0, -24);
     const double split = bf16 ? 3.0 * std::ldexp(1.0, -16) : 3.0 * std::ldexp(1.0, -22);
-    const double acc = (std::ceil(NP / 16.0) + 4.0) * 2.0 * std::ldexp(1.0, -23);
-    return (3.0 * u + split + acc) * 1.25;
+    const double acc = (std::ceil(NP / (16.0 * ksplit)) + 4.0) * 2.0 * std::ldexp(1.0, -23);
+    const double slices = (ksplit - 1) * 2.0 * u;  // FP32 sum of the K slices
+    return (3.0 * u + split + acc + slices) * 1.25;
 }
+
+// K slices of the product: each slice at least 8 blocks of 64, at most 8
+// slices (shorter FP32 accumulation chains for large n).
+int pick_ksplit(int nkb) { return std::max(1, std::min(8, nkb / 8)); }
 
 Cert cert_pass(int n, int k, double b_cap)
 {
@@ -675,6 +780,24 @@ Cert cert_pass(int n, int k, double b_cap)
     c.rho = (float)((g(n + 2) + g(k) + 6 * u) * 1.05);
     return c;
 }
+
+// Extended-precision tier: 2^-24 absolute from the rounding of D (U
+// orthonormal), n^1.5 2^-46 from the hi + lo accumulation; relative: the
+// rounding of d, the FP32 squares and sum of the k components, the division
+// and the square root.
+Cert cert_explicit_df(int n, int k)
+{
+    const double u = std::ldexp(1.0, -24);
+    auto g = [&](double m) { return m * u / (1.0 - m * u); };
+    Cert c;
+    c.A = (float)((u + std::pow((double)n, 1.5) * std::ldexp(1.0, -46)) * 1.1);
+    c.rho = (float)((g(k + 2) + 6 * u) * 1.1);
+    return c;
+}
+
+// Explicit tier in extended precision for large n (the FP32 tier's
+// gamma_{n+3} bound grows with n).
+bool explicit_uses_df(int n) { return n > 256; }
 
 Cert cert_explicit(int n, int k)
 {
@@ -829,7 +952,8 @@ sap_status restructured_prepare(sap_handle h)
     RCK(cudaGetLastError());
     rownorm_kernel<<<(r.Npad + 7) / 8, 256, 0, s>>>(X, N, n, r.center, r.nu, r.Npad);
     RCK(cudaGetLastError());
-    r.y_eps = y_error_unit(r.NP, bf16);
+    r.ksplit = pick_ksplit(r.NP / 64);
+    r.y_eps = y_error_unit(r.NP, bf16, r.ksplit);
     if (!make_map(&r.gemm.ta_hi, r.Xhi, bf16, r.NP, r.Npad, 128) ||
         !make_map(&r.gemm.ta_lo, r.Xlo, bf16, r.NP, r.Npad, 128))
         return handle_fail(h, SAP_E_CUDA, "cuTensorMapEncodeTiled failed for X");
@@ -854,12 +978,15 @@ sap_status restructured_basis_alloc(sap_handle h)
     dfree(r.Uhi);
     dfree(r.Ulo);
     dfree(r.Y);
+    dfree(r.Ypart);
     r.KPG = (k + 15) / 16 * 16;
     r.KY = padded_stride(k);   // <= KPG; columns >= k are zero
     RCK(cudaMalloc(&r.Uhi, (size_t)r.KPG * r.NP * 2));
     RCK(cudaMalloc(&r.Ulo, (size_t)r.KPG * r.NP * 2));
     RCK(cudaMalloc(&r.Y, (size_t)r.Npad * r.KY * sizeof(float)));
     RCK(cudaMemset(r.Y, 0, (size_t)r.Npad * r.KY * sizeof(float)));
+    dfree(r.Ypart);
+    if (r.ksplit > 1) RCK(cudaMalloc(&r.Ypart, (size_t)r.ksplit * r.Npad * r.KY * sizeof(float)));
     if (!make_map(&r.gemm.tb_hi, r.Uhi, bf16, r.NP, r.KPG, r.KPG) ||
         !make_map(&r.gemm.tb_lo, r.Ulo, bf16, r.NP, r.KPG, r.KPG))
         return handle_fail(h, SAP_E_CUDA, "cuTensorMapEncodeTiled failed for U");
@@ -870,10 +997,144 @@ sap_status restructured_basis_alloc(sap_handle h)
 sap_status restructured_upload_basis(sap_handle h, const double *U)
 {
     RestrState &r = restr_state(h);
-    const int k = handle_k(h), n = handle_n_dim(h);
+    const int k = handle_k(h);
+    std::vector<uint16_t> hi((size_t)r.KPG * r.NP, 0), lo((size_t)r.KPG * r.NP, 0);
+    restructured_split_host(h, U, k, hi.data(), lo.data());
+    RCK(cudaMemcpy(r.Uhi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice));
+    RCK(cudaMemcpy(r.Ulo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice));
+    if (r.k_cls != k) return classify(h, k);
+    return SAP_OK;
+}
+
+sap_status restructured_set_bound(sap_handle h, double b_cap)
+{
+    RestrState &r = restr_state(h);
+    r.b_cap = b_cap;
+    const int k = handle_k(h);
+    if (k > 0) return classify(h, k);
+    return SAP_OK;
+}
+
+GemmArgs product_args(sap_handle h, const RestrState &r)
+{
+    GemmArgs g = r.gemm;
+    g.Npad = r.Npad;
+    g.nkb = r.NP / 64;
+    g.ab_bf16 = handle_split_bf16(h);
+    g.lo_scale = g.ab_bf16 ? 1.0f / 256.f : 1.0f / 2048.f;
+    g.out_scale = 1.0f / r.xscale;
+    g.ksplit = r.ksplit;
+    return g;
+}
+
+sap_status restructured_enqueue_product(sap_handle h, const CUtensorMap *mhi, const CUtensorMap *mlo, int KPG,
+                                        float *Y, int KY, float *Ypart, ProbState *st, cudaStream_t s)
+{
+    RestrState &r = restr_state(h);
+    GemmArgs g = product_args(h, r);
+    g.tb_hi = *mhi;
+    g.tb_lo = *mlo;
+    g.Y = Y;
+    g.KY = KY;
+    g.KPG = KPG;
+    g.stages = gemm_pick_stages(KPG, g.nkb);
+    g.st = st;
+    g.Ypart = Ypart;
+    cudaEvent_t ea, eb;
+    handle_count_launch(h, 0, &ea, &eb);
+    if (ea) cudaEventRecord(ea, s);
+    RCK(launch_gemm_y(g, s));
+    if (eb) cudaEventRecord(eb, s);
+    handle_push_timing(h, 0, ea, eb);
+    return SAP_OK;
+}
+
+sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStream_t s)
+{
+    RestrState &r = restr_state(h);
+    const int n = handle_n_dim(h);
+    cudaEvent_t ea, eb;
+    {
+        PassArgs p;
+        p.w = r.w;
+        p.wtiles = r.wtiles;
+        p.ntiles = r.nwtiles;
+        p.Y = b.Y;
+        p.KY = b.KY;
+        p.Npad = r.Npad;
+        p.stages = pass_pick_stages(b.KY);
+        p.cert = cert_pass(n, b.k, r.b_cap);
+        p.st = b.st;
+        p.cand = b.cand1;
+        p.cap = b.cap;
+        handle_count_launch(h, 1, &ea, &eb);
+        if (ea) cudaEventRecord(ea, s);
+        RCK(launch_pass(p, b.k, std::min(r.nwtiles, handle_sms(h)), s));
+        if (eb) cudaEventRecord(eb, s);
+        handle_push_timing(h, 1, ea, eb);
+    }
+    {
+        ExplArgs x;
+        x.X = handle_x32(h);
+        x.N = (int)handle_n_points(h);
+        x.n = n;
+        x.U32 = b.U32;
+        x.U32lo = b.U32lo;
+        x.k = b.k;
+        x.KP = b.KP;
+        x.cand1 = b.cand1;
+        x.cap1 = (unsigned int)b.cap;
+        x.near = r.near;
+        x.n_near = r.n_near;
+        const bool df = explicit_uses_df(n);
+        x.cert = df ? cert_explicit_df(n, b.k) : cert_explicit(n, b.k);
+        x.st = b.st;
+        x.cand2 = b.cand2;
+        x.cap2 = b.cap;
+        handle_count_launch(h, 3, &ea, &eb);
+        if (ea) cudaEventRecord(ea, s);
+        RCK(launch_explicit(x, df, 2 * handle_sms(h), s));
+        if (eb) cudaEventRecord(eb, s);
+        handle_push_timing(h, 3, ea, eb);
+    }
+    return SAP_OK;
+}
+
+sap_status restructured_enqueue(sap_handle h, double alpha)
+{
+    (void)alpha;
+    RestrState &r = restr_state(h);
+    cudaStream_t s = handle_stream(h);
+    sap_status st = restructured_enqueue_product(h, &r.gemm.tb_hi, &r.gemm.tb_lo, r.KPG, r.Y, r.KY, r.Ypart,
+                                                 handle_state(h), s);
+    if (st != SAP_OK) return st;
+    BasisView b;
+    b.k = handle_k(h);
+    b.KP = handle_kp(h);
+    b.KY = r.KY;
+    b.U32 = handle_u32(h);
+    b.U32lo = handle_u32lo(h);
+    b.Y = r.Y;
+    b.st = handle_state(h);
+    b.cand1 = handle_cand1(h);
+    b.cand2 = handle_cand2(h);
+    b.cap = handle_cap(h);
+    return restructured_enqueue_basis(h, b, s);
+}
+
+bool restructured_u_maps(sap_handle h, void *Uhi, void *Ulo, int KPG, CUtensorMap *mhi, CUtensorMap *mlo)
+{
+    RestrState &r = restr_state(h);
+    const bool bf16 = handle_split_bf16(h) != 0;
+    return make_map(mhi, Uhi, bf16, r.NP, KPG, KPG) && make_map(mlo, Ulo, bf16, r.NP, KPG, KPG);
+}
+
+void restructured_split_host(sap_handle h, const double *U, int k, uint16_t *hi, uint16_t *lo)
+{
+    RestrState &r = restr_state(h);
+    const int n = handle_n_dim(h);
     const bool bf16 = handle_split_bf16(h) != 0;
     const double lo_mul = bf16 ? 256.0 : 2048.0;
-    std::vector<uint16_t> hi((size_t)r.KPG * r.NP, 0), lo((size_t)r.KPG * r.NP, 0);
     for (int c = 0; c < k; ++c)
         for (int l = 0; l < n; ++l) {
             const double v = U[(size_t)c * n + l];
@@ -890,89 +1151,12 @@ sap_status restructured_upload_basis(sap_handle h, const double *U)
                 std::memcpy(&lo[idx], &lv, 2);
             }
         }
-    RCK(cudaMemcpy(r.Uhi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice));
-    RCK(cudaMemcpy(r.Ulo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice));
-    if (r.k_cls != k) return classify(h, k);
-    return SAP_OK;
 }
 
-sap_status restructured_set_bound(sap_handle h, double b_cap)
+sap_status restructured_classify(sap_handle h, int k)
 {
-    RestrState &r = restr_state(h);
-    r.b_cap = b_cap;
-    const int k = handle_k(h);
-    if (k > 0) return classify(h, k);
-    return SAP_OK;
-}
-
-sap_status restructured_enqueue(sap_handle h, double alpha)
-{
-    (void)alpha;
-    RestrState &r = restr_state(h);
-    cudaStream_t s = handle_stream(h);
-    const int k = handle_k(h), n = handle_n_dim(h);
-    ProbState *st = handle_state(h);
-    cudaEvent_t ea, eb;
-    {
-        GemmArgs g = r.gemm;
-        g.Y = r.Y;
-        g.KY = r.KY;
-        g.Npad = r.Npad;
-        g.nkb = r.NP / 64;
-        g.KPG = r.KPG;
-        g.ab_bf16 = handle_split_bf16(h);
-        g.stages = gemm_pick_stages(r.KPG, g.nkb);
-        g.lo_scale = g.ab_bf16 ? 1.0f / 256.f : 1.0f / 2048.f;
-        g.out_scale = 1.0f / r.xscale;
-        g.st = st;
-        handle_count_launch(h, 0, &ea, &eb);
-        if (ea) cudaEventRecord(ea, s);
-        RCK(launch_gemm_y(g, s));
-        if (eb) cudaEventRecord(eb, s);
-        handle_push_timing(h, 0, ea, eb);
-    }
-    {
-        PassArgs p;
-        p.w = r.w;
-        p.wtiles = r.wtiles;
-        p.ntiles = r.nwtiles;
-        p.Y = r.Y;
-        p.KY = r.KY;
-        p.Npad = r.Npad;
-        p.stages = pass_pick_stages(r.KY);
-        p.cert = cert_pass(n, k, r.b_cap);
-        p.st = st;
-        p.cand = handle_cand1(h);
-        p.cap = handle_cap(h);
-        handle_count_launch(h, 1, &ea, &eb);
-        if (ea) cudaEventRecord(ea, s);
-        RCK(launch_pass(p, k, std::min(r.nwtiles, handle_sms(h)), s));
-        if (eb) cudaEventRecord(eb, s);
-        handle_push_timing(h, 1, ea, eb);
-    }
-    {
-        ExplArgs x;
-        x.X = handle_x32(h);
-        x.N = (int)handle_n_points(h);
-        x.n = n;
-        x.U32 = handle_u32(h);
-        x.k = k;
-        x.KP = handle_kp(h);
-        x.cand1 = handle_cand1(h);
-        x.cap1 = (unsigned int)handle_cap(h);
-        x.near = r.near;
-        x.n_near = r.n_near;
-        x.cert = cert_explicit(n, k);
-        x.st = st;
-        x.cand2 = handle_cand2(h);
-        x.cap2 = handle_cap(h);
-        handle_count_launch(h, 3, &ea, &eb);
-        if (ea) cudaEventRecord(ea, s);
-        RCK(launch_explicit(x, 2 * handle_sms(h), s));
-        if (eb) cudaEventRecord(eb, s);
-        handle_push_timing(h, 3, ea, eb);
-    }
-    return SAP_OK;
+    if (restr_state(h).k_cls == k) return SAP_OK;
+    return classify(h, k);
 }
 
 sap_status restructured_project(sap_handle h, float *Y_out, int out_is_device)
@@ -981,17 +1165,13 @@ sap_status restructured_project(sap_handle h, float *Y_out, int out_is_device)
     cudaStream_t s = handle_stream(h);
     const int k = handle_k(h);
     const int N = (int)handle_n_points(h);
-    GemmArgs g = r.gemm;
+    GemmArgs g = product_args(h, r);
     g.Y = r.Y;
     g.KY = r.KY;
-    g.Npad = r.Npad;
-    g.nkb = r.NP / 64;
     g.KPG = r.KPG;
-    g.ab_bf16 = handle_split_bf16(h);
     g.stages = gemm_pick_stages(r.KPG, g.nkb);
-    g.lo_scale = g.ab_bf16 ? 1.0f / 256.f : 1.0f / 2048.f;
-    g.out_scale = 1.0f / r.xscale;
     g.st = handle_state(h);
+    g.Ypart = r.Ypart;
     cudaEvent_t ea, eb;
     handle_count_launch(h, 0, &ea, &eb);
     if (ea) cudaEventRecord(ea, s);
@@ -1023,7 +1203,7 @@ void restructured_free(sap_handle h)
 {
     RestrState &r = restr_state(h);
     dfree(r.Xhi); dfree(r.Xlo); dfree(r.center); dfree(r.nu); dfree(r.w); dfree(r.wtiles);
-    dfree(r.near); dfree(r.counters); dfree(r.Uhi); dfree(r.Ulo); dfree(r.Y);
+    dfree(r.near); dfree(r.counters); dfree(r.Uhi); dfree(r.Ulo); dfree(r.Y); dfree(r.Ypart);
 }
 
 void restructured_stats(sap_handle h, sap_stats *out)

@@ -35,6 +35,8 @@ struct RestrState {
     int KPG = 0;              // k rounded up to the MMA N granule (16)
     float *Y = nullptr;       // Npad x KY
     int KY = 0;               // k rounded up to 4
+    int ksplit = 1;           // K slices of the product (shorter accumulation chains)
+    float *Ypart = nullptr;   // ksplit x KY x Npad slice results (ksplit > 1)
     GemmArgs gemm;            // tensor maps and shapes of the product
     bool maps_x = false, maps_u = false;
 };
@@ -46,6 +48,7 @@ int handle_sms(sap_handle h);
 ProbState *handle_state(sap_handle h);
 const float *handle_x32(sap_handle h);
 const float *handle_u32(sap_handle h);
+const float *handle_u32lo(sap_handle h);
 int2 *handle_cand1(sap_handle h);
 int2 *handle_cand2(sap_handle h);
 long long handle_cap(sap_handle h);
@@ -61,7 +64,24 @@ void handle_count_launch(sap_handle h, int cls, cudaEvent_t *a, cudaEvent_t *b);
 void handle_push_timing(sap_handle h, int cls, cudaEvent_t a, cudaEvent_t b);
 sap_status handle_fail(sap_handle h, sap_status s, const char *msg);
 
+// One basis of the restructured form: the handle's own, or one of the bases
+// of a dimension sweep that share the handle's dataset, lengths and near list.
+struct BasisView {
+    int k, KP, KY;            // width, FP32 basis stride, Y stride (components)
+    const float *U32, *U32lo; // n x KP FP32 basis and its low part
+    float *Y;                 // KY x Npad, component-major
+    ProbState *st;
+    int2 *cand1, *cand2;      // candidate lists of the pass and of the explicit tier
+    long long cap;            // capacity of each list
+};
+
 // Restructured-form entry points (restructured.cu).
+sap_status restructured_enqueue_product(sap_handle h, const CUtensorMap *mhi, const CUtensorMap *mlo, int KPG,
+                                        float *Y, int KY, float *Ypart, ProbState *st, cudaStream_t s);
+sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStream_t s); // pass + explicit tier
+bool restructured_u_maps(sap_handle h, void *Uhi, void *Ulo, int KPG, CUtensorMap *mhi, CUtensorMap *mlo);
+void restructured_split_host(sap_handle h, const double *U, int k, uint16_t *hi, uint16_t *lo); // k rows of NP
+sap_status restructured_classify(sap_handle h, int k);  // near list for width k (valid for every k' <= k)
 sap_status restructured_prepare(sap_handle h);          // X split, norms, lengths, near list
 sap_status restructured_basis_alloc(sap_handle h);      // U operands and Y for k
 sap_status restructured_upload_basis(sap_handle h, const double *U); // n x k col-major

@@ -216,6 +216,7 @@ struct SelectUpdateArgs {
     int N, n;
     double *U64;           // n x k column-major, updated in place
     float *U32;            // n x KP row-major, written
+    float *U32lo;          // n x KP: fl(U64 - U32), written when non-null
     int KP;
     void *Uhi, *Ulo;       // tensor-core operands (KPG x NP, 16-bit), or null
     int NP;

@@ -477,6 +477,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             a.U64[(size_t)m * n + l] = s;
             const float sf = (float)s;
             a.U32[(size_t)l * a.KP + m] = sf;
+            if (a.U32lo) a.U32lo[(size_t)l * a.KP + m] = (float)(s - (double)sf);
             if (a.Uhi) {
                 // hi + lo * 2^-s of the FP32 value (the FP32 rounding adds 2^-24
                 // relative to the split residual)

@@ -818,6 +818,7 @@ struct SoftStepArgs {
     const double *G;     // n x K column-major (dL/dU)
     double *U64;         // n x K column-major, updated in place
     float *U32;          // n x KP row-major
+    float *U32lo;        // n x KP, fl(U64 - U32)
     int KP;
     void *Uhi, *Ulo;     // tensor-core operands of the SAP pass (KPG x NP 16-bit) or null
     int NP;
@@ -933,6 +934,7 @@ __global__ void __launch_bounds__(256) soft_step_kernel(SoftStepArgs a)
             a.U64[(size_t)m * n + l] = s;
             const float sf = (float)s;
             a.U32[(size_t)l * a.KP + m] = sf;
+            a.U32lo[(size_t)l * a.KP + m] = (float)(s - (double)sf);
             if (a.Uhi) {
                 const size_t idx = (size_t)m * a.NP + l;
                 if (a.split_bf16) {
@@ -1231,6 +1233,7 @@ sap_status enqueue_step(sap_handle h, double eta)
     sa.G = ss.G;
     sa.U64 = handle_u64(h);
     sa.U32 = handle_u32_mut(h);
+    sa.U32lo = const_cast<float *>(handle_u32lo(h));
     sa.KP = handle_kp(h);
     sa.Uhi = r.Uhi; sa.Ulo = r.Ulo; sa.NP = r.NP;
     sa.split_bf16 = handle_split_bf16(h);

@@ -1,0 +1,56 @@
+// sweep.cuh -- the dimension-estimation sweep (Sec. VI-A): SAP for every
+// k = 1..k_max over one dataset, all bases advancing together.
+#pragma once
+
+#include <cuda.h>
+#include <vector>
+
+#include "sap_internal.cuh"
+#include "../../include/sap.h"
+
+namespace sap {
+
+struct SweepBasis {
+    int k = 0, KP = 0, KY = 0, off = 0;  // width, FP32 stride, Y stride, first component in the sweep's Y
+    double *U64 = nullptr;               // n x k column-major
+    float *U32 = nullptr, *U32lo = nullptr;
+    double *work = nullptr;
+    ProbState *st = nullptr;
+    int2 *cand1 = nullptr, *cand2 = nullptr;
+    Partial *partials = nullptr;
+    double *hist = nullptr;
+    int2 *am = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+struct SweepState {
+    int kmax = 0;
+    int hist_cap = 0;
+    int last_iters = -1;
+    long long cap = 0;
+    std::vector<SweepBasis> b;
+    void *Uhi = nullptr, *Ulo = nullptr;  // all bases' split operands, KPG x NP 16-bit
+    int KPG = 0;
+    CUtensorMap mhi, mlo;
+    float *Y = nullptr;                   // KY x Npad, all bases' components
+    int KY = 0;
+    float *Ypart = nullptr;
+    int ksplit = 1;
+    ProbState *gst = nullptr;             // status word of the product
+    cudaEvent_t fork = nullptr;
+};
+
+sap_status sweep_run(sap_handle h, const double *U0, int kmax, int iters, double alpha, double threshold,
+                     int *k_out, double *ratios_out);
+sap_status sweep_history(sap_handle h, int k, double *hist, int64_t *argmins, int capacity);
+sap_status sweep_basis(sap_handle h, int k, double *U_out, int out_is_device);
+void sweep_free(SweepState *&s);
+
+// Engine accessors (capi.cu).
+SweepState *&sweep_state(sap_handle h);
+int handle_mode(sap_handle h);
+Cert handle_seed_cert(int n, int k);
+sap_status handle_check_status(sap_handle h, ProbState *st);
+
+} // namespace sap

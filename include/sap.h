@@ -287,6 +287,31 @@ sap_status sap_softmin_forward(sap_handle h, double tau, double *L_out);
 sap_status sap_softmin_backward(sap_handle h, double tau, double L, double *G_out, int out_is_device);
 sap_status sap_softmin_ascent(sap_handle h, double tau, double eta, int32_t steps, double *hist);
 
+/*
+ * Uneven batch: B independent datasets (Sec. VII's noisy-data setting is the
+ * intended use: many small hyperspectral scenes), each X_b an N_b x n
+ * row-major array of the same n and dtype (2 <= N_b <= 92681, B <= 4096),
+ * run together.  The batch handle owns one dataset handle per X_b.
+ * sap_set_min_secant_length, sap_set_split, sap_set_update_mode, sap_set_path
+ * and sap_set_basis apply to every dataset; sap_get_stats sums over them;
+ * calls on one basis (sap_step, sap_run, sap_min_secant, sap_get_basis, the
+ * sweep and the soft-min calls) return SAP_E_STATE on a batch handle.
+ *
+ * sap_run_batch: iters SAP iterations of every dataset followed by one
+ * evaluation, as one captured CUDA graph per chunk of iterations that
+ * forks to every dataset's stream and joins (the datasets never wait on
+ * each other inside a chunk).  hist (nullable) receives B x (iters + 1)
+ * min ratios and argmins (nullable) B x (iters + 1) pairs, dataset-major.
+ * Every dataset needs a basis.  Synchronises.
+ */
+sap_status sap_create_batch(const void *const *Xs, const int64_t *Ns, int32_t B, int32_t n,
+                            sap_dtype dt, int x_is_device, sap_handle *out);
+sap_status sap_batch_count(sap_handle h, int32_t *B);   /* 1 for an ordinary handle */
+sap_status sap_set_basis_b(sap_handle h, int32_t b, const double *U, int32_t k, int u_is_device);
+sap_status sap_get_basis_b(sap_handle h, int32_t b, double *U_out, int out_is_device);
+sap_status sap_min_secant_b(sap_handle h, int32_t b, int64_t *i, int64_t *j, double *ratio);
+sap_status sap_run_batch(sap_handle h, double alpha, int32_t iters, double *hist, int64_t *argmins);
+
 /* Read the handle's statistics. */
 sap_status sap_get_stats(sap_handle h, sap_stats *out);
 

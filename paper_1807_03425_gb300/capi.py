@@ -83,6 +83,12 @@ def load_library():
         "sap_estimate_dim": ([vp, vp, i32, i32, f64, f64, i32p, vp], i32),
         "sap_get_sweep_history": ([vp, i32, vp, vp, i32], i32),
         "sap_get_sweep_basis": ([vp, i32, vp, i32], i32),
+        "sap_create_batch": ([vp, vp, i32, i32, i32, i32, ctypes.POINTER(vp)], i32),
+        "sap_batch_count": ([vp, i32p], i32),
+        "sap_set_basis_b": ([vp, i32, vp, i32, i32], i32),
+        "sap_get_basis_b": ([vp, i32, vp, i32], i32),
+        "sap_min_secant_b": ([vp, i32, i64p, i64p, f64p], i32),
+        "sap_run_batch": ([vp, f64, i32, vp, vp], i32),
         "sap_project": ([vp, vp, i32], i32),
         "sap_min_secant_noalloc": ([vp, i64, i32, vp, i32, f64, vp, i64p, i64p, f64p], i32),
         "sap_get_stats": ([vp, ctypes.POINTER(Stats)], i32),
@@ -334,6 +340,65 @@ def sap_softmin_ascent(h, tau, eta, steps):
     return hist
 
 
+def sap_create_batch(Xs, dtype=None):
+    """Xs: list of (N_b, n) NumPy arrays (float32, float64, or uint16 BF16
+    bits) of one dtype and n.  Returns a batch handle."""
+    lib = load_library()
+    if dtype is None:
+        dt = str(Xs[0].dtype)
+        dtype = F64 if "float64" in dt else (BF16 if "uint16" in dt or "bfloat16" in dt else F32)
+    want = {F32: np.float32, F64: np.float64, BF16: np.uint16}[dtype]
+    arrs = [np.ascontiguousarray(X, dtype=want) for X in Xs]
+    n = arrs[0].shape[1]
+    ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data_as(ctypes.c_void_p) for a in arrs])
+    Ns = (ctypes.c_int64 * len(arrs))(*[a.shape[0] for a in arrs])
+    h = ctypes.c_void_p()
+    code = lib.sap_create_batch(ctypes.cast(ptrs, ctypes.c_void_p), ctypes.cast(Ns, ctypes.c_void_p),
+                                len(arrs), n, dtype, 0, ctypes.byref(h))
+    if code != 0:
+        raise SapError(code, "sap_create_batch(B=%d, n=%d)" % (len(arrs), n))
+    return h
+
+
+def sap_batch_count(h):
+    b = ctypes.c_int32()
+    _check(h, load_library().sap_batch_count(h, ctypes.byref(b)))
+    return b.value
+
+
+def sap_set_basis_b(h, b, U):
+    if not hasattr(U, "data_ptr"):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+    p, dev = _ptr(U)
+    _check(h, load_library().sap_set_basis_b(h, int(b), p, U.shape[0], dev))
+
+
+def sap_get_basis_b(h, b, k, n, out=None):
+    if out is None:
+        out = np.empty((k, n), dtype=np.float64)
+    p, dev = _ptr(out)
+    _check(h, load_library().sap_get_basis_b(h, int(b), p, dev))
+    return out
+
+
+def sap_min_secant_b(h, b):
+    i, j, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    _check(h, load_library().sap_min_secant_b(h, int(b), ctypes.byref(i), ctypes.byref(j), ctypes.byref(r)))
+    return i.value, j.value, r.value
+
+
+def sap_run_batch(h, alpha, iters, B, history=True):
+    lib = load_library()
+    if not history:
+        _check(h, lib.sap_run_batch(h, float(alpha), int(iters), None, None))
+        return None
+    hist = np.empty((B, iters + 1), dtype=np.float64)
+    am = np.empty((B, iters + 1, 2), dtype=np.int64)
+    _check(h, lib.sap_run_batch(h, float(alpha), int(iters), hist.ctypes.data_as(ctypes.c_void_p),
+                                am.ctypes.data_as(ctypes.c_void_p)))
+    return hist, am
+
+
 # ------------------------------------------------------------ handle class --
 
 class Sap:
@@ -432,3 +497,53 @@ class Sap:
 
     def softmin_ascent(self, tau, eta, steps):
         return sap_softmin_ascent(self.h, tau, eta, steps)
+
+
+class SapBatch:
+    """Several datasets of one dimension run together (uneven sizes)."""
+
+    def __init__(self, Xs, dtype=None):
+        self.Ns = [int(X.shape[0]) for X in Xs]
+        self.n = int(Xs[0].shape[1])
+        self.B = len(Xs)
+        self.h = sap_create_batch(Xs, dtype)
+        self.ks = [0] * self.B
+
+    def close(self):
+        if self.h is not None:
+            sap_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_min_secant_length(self, eps):
+        sap_set_min_secant_length(self.h, eps)
+
+    def set_split(self, split):
+        sap_set_split(self.h, {"fp16": SPLIT_FP16, "bf16": SPLIT_BF16}.get(split, split))
+
+    def set_basis(self, b, U):
+        sap_set_basis_b(self.h, b, U)
+        self.ks[b] = int(U.shape[0])
+
+    def get_basis(self, b):
+        return sap_get_basis_b(self.h, b, self.ks[b], self.n)
+
+    def min_secant(self, b):
+        return sap_min_secant_b(self.h, b)
+
+    def run(self, alpha, iters, history=True):
+        return sap_run_batch(self.h, alpha, iters, self.B, history)
+
+    def stats(self):
+        return sap_get_stats(self.h)

@@ -86,6 +86,12 @@ struct sap_ctx {
     SoftState ss;            // soft-min buffers (softmin.cuh)
     SweepState *sw = nullptr; // dimension sweep (sweep.cuh)
 
+    // uneven batch: one ordinary handle per dataset, run together
+    bool is_batch = false;
+    std::vector<sap_handle> kids;
+    std::vector<cudaEvent_t> kid_done;
+    cudaEvent_t fork = nullptr;
+
     long long launches = 0;
     std::vector<GraphEntry> graphs;
 
@@ -417,6 +423,11 @@ sap_status sap_destroy(sap_handle h)
 {
     if (!h) return SAP_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    for (sap_handle k : h->kids) sap_destroy(k);
+    h->kids.clear();
+    for (cudaEvent_t e : h->kid_done) cudaEventDestroy(e);
+    h->kid_done.clear();
+    if (h->fork) cudaEventDestroy(h->fork);
     drop_graphs(h);
     for (auto &p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : h->event_pool) cudaEventDestroy(e);
@@ -508,6 +519,28 @@ sap_status sap_create(const void *X, int64_t N, int32_t n, sap_dtype dt, int x_i
     return SAP_OK;
 }
 
+// Batch handles forward the dataset-wide settings to every dataset; calls
+// that act on one basis need the _b variants.
+#define FORWARD_BATCH(h, call)                                        \
+    do {                                                              \
+        if ((h)->is_batch) {                                          \
+            for (size_t b_ = 0; b_ < (h)->kids.size(); ++b_) {        \
+                sap_handle kid = (h)->kids[b_];                       \
+                const sap_status s_ = (call);                         \
+                if (s_ != SAP_OK) {                                   \
+                    (h)->err = "dataset " + std::to_string(b_) + ": " + kid->err; \
+                    return s_;                                        \
+                }                                                     \
+            }                                                         \
+            return SAP_OK;                                            \
+        }                                                             \
+    } while (0)
+
+#define NOT_BATCH(h)                                                                 \
+    do {                                                                             \
+        if ((h)->is_batch) return fail(h, SAP_E_STATE, "batch handle: use the _b calls"); \
+    } while (0)
+
 sap_status sap_set_stream(sap_handle h, void *cuda_stream)
 {
     CHECK_HANDLE(h);
@@ -527,6 +560,7 @@ sap_status sap_set_stream(sap_handle h, void *cuda_stream)
 sap_status sap_set_path(sap_handle h, sap_path p)
 {
     CHECK_HANDLE(h);
+    FORWARD_BATCH(h, sap_set_path(kid, p));
     if (p != SAP_PLAIN && p != SAP_RESTRUCTURED) return fail(h, SAP_E_ARG, "unknown path");
     if (p == SAP_RESTRUCTURED && h->dt == SAP_F64)
         return fail(h, SAP_E_UNSUPPORTED, "the restructured form needs FP32 or BF16 data");
@@ -540,6 +574,7 @@ sap_status sap_set_path(sap_handle h, sap_path p)
 sap_status sap_set_update_mode(sap_handle h, sap_update_mode m)
 {
     CHECK_HANDLE(h);
+    FORWARD_BATCH(h, sap_set_update_mode(kid, m));
     if (m != SAP_UPDATE_LITERAL && m != SAP_UPDATE_ANGLE) return fail(h, SAP_E_ARG, "unknown mode");
     if (m != h->mode) drop_graphs(h);
     h->mode = m;
@@ -549,6 +584,7 @@ sap_status sap_set_update_mode(sap_handle h, sap_update_mode m)
 sap_status sap_set_split(sap_handle h, sap_split s)
 {
     CHECK_HANDLE(h);
+    FORWARD_BATCH(h, sap_set_split(kid, s));
     if (s != SAP_SPLIT_FP16 && s != SAP_SPLIT_BF16) return fail(h, SAP_E_ARG, "unknown split");
     if (h->dt == SAP_F64) return fail(h, SAP_E_UNSUPPORTED, "no tensor-core product for FP64 data");
     if (s == h->split) return SAP_OK;
@@ -566,6 +602,7 @@ sap_status sap_set_split(sap_handle h, sap_split s)
 sap_status sap_set_min_secant_length(sap_handle h, double eps)
 {
     CHECK_HANDLE(h);
+    FORWARD_BATCH(h, sap_set_min_secant_length(kid, eps));
     if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(h, SAP_E_ARG, "eps must be finite and >= 0");
     CK(cudaStreamSynchronize(h->stream));
     drop_graphs(h);
@@ -580,6 +617,7 @@ sap_status sap_set_min_secant_length(sap_handle h, double eps)
 sap_status sap_set_basis(sap_handle h, const double *U, int32_t k, int u_is_device)
 {
     CHECK_HANDLE(h);
+    FORWARD_BATCH(h, sap_set_basis(kid, U, k, u_is_device));
     if (!U || k < 1 || k > kMaxK || k > h->n) return fail(h, SAP_E_ARG, "need 1 <= k <= min(n, 32)");
     if (h->path == SAP_PLAIN && h->dt != SAP_F64 && k > 8)
         return fail(h, SAP_E_UNSUPPORTED, "the FP32 plain form supports k <= 8");
@@ -635,6 +673,7 @@ sap_status sap_set_basis(sap_handle h, const double *U, int32_t k, int u_is_devi
 sap_status sap_get_basis(sap_handle h, double *U_out, int out_is_device)
 {
     CHECK_HANDLE(h);
+    NOT_BATCH(h);
     if (!U_out) return fail(h, SAP_E_ARG, "null output");
     if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
     CK(cudaMemcpyAsync(U_out, h->U64, (size_t)h->n * h->k * sizeof(double),
@@ -658,6 +697,7 @@ static sap_status read_last(sap_handle h, int64_t *i, int64_t *j, double *ratio)
 sap_status sap_min_secant(sap_handle h, int64_t *i, int64_t *j, double *ratio)
 {
     CHECK_HANDLE(h);
+    NOT_BATCH(h);
     if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
     sap_status s = enqueue_iteration(h, 0.0, 1);
     if (s != SAP_OK) return s;
@@ -667,6 +707,7 @@ sap_status sap_min_secant(sap_handle h, int64_t *i, int64_t *j, double *ratio)
 sap_status sap_step(sap_handle h, double alpha, int64_t *i, int64_t *j, double *ratio)
 {
     CHECK_HANDLE(h);
+    NOT_BATCH(h);
     if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
     if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(h, SAP_E_ARG, "alpha must be in [0, 1]");
     sap_status s = enqueue_iteration(h, alpha, 0);
@@ -711,6 +752,7 @@ static int kernels_per_iteration(sap_handle h)
 sap_status sap_run(sap_handle h, double alpha, int32_t iters, double *hist, int64_t *argmins)
 {
     CHECK_HANDLE(h);
+    NOT_BATCH(h);
     if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
     if (iters < 0) return fail(h, SAP_E_ARG, "iters must be >= 0");
     if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(h, SAP_E_ARG, "alpha must be in [0, 1]");
@@ -774,6 +816,7 @@ sap_status sap_get_history(sap_handle h, double *hist, int64_t *argmins, int32_t
 sap_status sap_project(sap_handle h, float *Y_out, int out_is_device)
 {
     CHECK_HANDLE(h);
+    NOT_BATCH(h);
     if (!Y_out) return fail(h, SAP_E_ARG, "null output");
     if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
     if (h->dt == SAP_F64) return fail(h, SAP_E_UNSUPPORTED, "no tensor-core product for FP64 data");
@@ -786,6 +829,27 @@ sap_status sap_get_stats(sap_handle h, sap_stats *out)
 {
     if (!h || !out) return SAP_E_ARG;
     std::memset(out, 0, sizeof(*out));
+    if (h->is_batch) {
+        // sums over the datasets (k and the tier counts of the last one)
+        out->kernel_launches = h->launches;
+        out->n_dim = h->n;
+        for (sap_handle kid : h->kids) {
+            sap_stats ks;
+            const sap_status st = sap_get_stats(kid, &ks);
+            if (st != SAP_OK) return st;
+            out->n_points += ks.n_points;
+            out->n_pairs += ks.n_pairs;
+            out->n_excluded += ks.n_excluded;
+            out->n_near += ks.n_near;
+            out->kernel_launches += ks.kernel_launches;
+            out->k = ks.k;
+            out->last_tier1 = ks.last_tier1;
+            out->last_tier2 = ks.last_tier2;
+            out->cert_bound = ks.cert_bound;
+            out->y_error_unit = std::max(out->y_error_unit, ks.y_error_unit);
+        }
+        return SAP_OK;
+    }
     out->n_points = h->N;
     out->n_dim = h->n;
     out->k = h->k;
@@ -838,6 +902,7 @@ sap_status sap_get_kernel_time(sap_handle h, int32_t kernel_class, double *total
 sap_status sap_softmin_forward(sap_handle h, double tau, double *L_out)
 {
     CHECK_HANDLE(h);
+    NOT_BATCH(h);
     if (!L_out) return fail(h, SAP_E_ARG, "null output");
     return softmin_forward(h, tau, L_out);
 }
@@ -845,12 +910,14 @@ sap_status sap_softmin_forward(sap_handle h, double tau, double *L_out)
 sap_status sap_softmin_backward(sap_handle h, double tau, double L, double *G_out, int out_is_device)
 {
     CHECK_HANDLE(h);
+    NOT_BATCH(h);
     return softmin_backward(h, tau, L, G_out, out_is_device);
 }
 
 sap_status sap_softmin_ascent(sap_handle h, double tau, double eta, int32_t steps, double *hist)
 {
     CHECK_HANDLE(h);
+    NOT_BATCH(h);
     return softmin_ascent(h, tau, eta, steps, hist);
 }
 
@@ -858,6 +925,7 @@ sap_status sap_estimate_dim(sap_handle h, const double *U0, int32_t k_max, int32
                             double alpha, double threshold, int32_t *k_out, double *ratios_out)
 {
     CHECK_HANDLE(h);
+    NOT_BATCH(h);
     if (!k_out && !ratios_out) return fail(h, SAP_E_ARG, "no output");
     const sap_status s = sweep_run(h, U0, k_max, iters, alpha, threshold, k_out, ratios_out);
     if (s != SAP_OK) return s;
@@ -874,6 +942,181 @@ sap_status sap_get_sweep_basis(sap_handle h, int32_t k, double *U_out, int out_i
 {
     CHECK_HANDLE(h);
     return sweep_basis(h, k, U_out, out_is_device);
+}
+
+sap_status sap_create_batch(const void *const *Xs, const int64_t *Ns, int32_t B, int32_t n, sap_dtype dt,
+                            int x_is_device, sap_handle *out)
+{
+    if (!out) return SAP_E_ARG;
+    *out = nullptr;
+    if (!Xs || !Ns || B < 1 || B > 4096 || n < 1 || n > 16384) return SAP_E_ARG;
+    if (dt != SAP_F32 && dt != SAP_BF16 && dt != SAP_F64) return SAP_E_ARG;
+    for (int b = 0; b < B; ++b)
+        if (!Xs[b] || Ns[b] < 2 || Ns[b] > 92681) return SAP_E_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return SAP_E_NO_DEVICE;
+    }
+    sap_handle h = new sap_ctx();
+    h->is_batch = true;
+    h->n = n;
+    h->dt = dt;
+    auto cleanup_fail = [&](sap_status s) { sap_destroy(h); return s; };
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+        return cleanup_fail(SAP_E_CUDA);
+    h->own_stream = true;
+    if (cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) return cleanup_fail(SAP_E_CUDA);
+    for (int b = 0; b < B; ++b) {
+        sap_handle kid = nullptr;
+        const sap_status st = sap_create(Xs[b], Ns[b], n, dt, x_is_device, &kid);
+        if (st != SAP_OK) return cleanup_fail(st);
+        h->kids.push_back(kid);
+        h->N += Ns[b];
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return cleanup_fail(SAP_E_CUDA);
+        h->kid_done.push_back(e);
+    }
+    *out = h;
+    return SAP_OK;
+}
+
+sap_status sap_batch_count(sap_handle h, int32_t *B)
+{
+    CHECK_HANDLE(h);
+    if (!B) return fail(h, SAP_E_ARG, "null output");
+    *B = h->is_batch ? (int32_t)h->kids.size() : 1;
+    return SAP_OK;
+}
+
+static sap_status kid_of(sap_handle h, int32_t b, sap_handle *kid)
+{
+    if (!h->is_batch) return fail(h, SAP_E_STATE, "not a batch handle");
+    if (b < 0 || b >= (int32_t)h->kids.size()) return fail(h, SAP_E_ARG, "dataset index out of range");
+    *kid = h->kids[b];
+    return SAP_OK;
+}
+
+static sap_status kid_result(sap_handle h, int32_t b, sap_handle kid, sap_status st)
+{
+    if (st != SAP_OK) h->err = "dataset " + std::to_string(b) + ": " + kid->err;
+    return st;
+}
+
+sap_status sap_set_basis_b(sap_handle h, int32_t b, const double *U, int32_t k, int u_is_device)
+{
+    CHECK_HANDLE(h);
+    sap_handle kid;
+    sap_status st = kid_of(h, b, &kid);
+    if (st != SAP_OK) return st;
+    return kid_result(h, b, kid, sap_set_basis(kid, U, k, u_is_device));
+}
+
+sap_status sap_get_basis_b(sap_handle h, int32_t b, double *U_out, int out_is_device)
+{
+    CHECK_HANDLE(h);
+    sap_handle kid;
+    sap_status st = kid_of(h, b, &kid);
+    if (st != SAP_OK) return st;
+    return kid_result(h, b, kid, sap_get_basis(kid, U_out, out_is_device));
+}
+
+sap_status sap_min_secant_b(sap_handle h, int32_t b, int64_t *i, int64_t *j, double *ratio)
+{
+    CHECK_HANDLE(h);
+    sap_handle kid;
+    sap_status st = kid_of(h, b, &kid);
+    if (st != SAP_OK) return st;
+    return kid_result(h, b, kid, sap_min_secant(kid, i, j, ratio));
+}
+
+// One graph: fork to every dataset's stream, `chunk` iterations of each
+// dataset's own chain (they are independent), join.
+static sap_status batch_graph(sap_handle h, double alpha, int eval_only, int chunk, cudaGraphExec_t *out,
+                              long long *launches)
+{
+    cudaGraph_t graph = nullptr;
+    std::vector<long long> before;
+    for (sap_handle kid : h->kids) before.push_back(kid->launches);
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    sap_status s = SAP_OK;
+    cudaError_t e = cudaEventRecord(h->fork, h->stream);
+    for (size_t b = 0; b < h->kids.size() && s == SAP_OK && e == cudaSuccess; ++b) {
+        sap_handle kid = h->kids[b];
+        e = cudaStreamWaitEvent(kid->stream, h->fork, 0);
+        for (int c = 0; c < chunk && s == SAP_OK && e == cudaSuccess; ++c) s = enqueue_iteration(kid, alpha, eval_only);
+        if (s == SAP_OK && e == cudaSuccess) e = cudaEventRecord(h->kid_done[b], kid->stream);
+        if (s == SAP_OK && e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->kid_done[b], 0);
+        if (s != SAP_OK) h->err = "dataset " + std::to_string(b) + ": " + kid->err;
+    }
+    const cudaError_t ee = cudaStreamEndCapture(h->stream, &graph);
+    *launches = 0;
+    for (size_t b = 0; b < h->kids.size(); ++b) {
+        *launches += h->kids[b]->launches - before[b];
+        h->kids[b]->launches = before[b];  // capture only records; replays are counted
+    }
+    if (s != SAP_OK || e != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (s != SAP_OK) return s;
+        CK(e != cudaSuccess ? e : ee);
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    *out = exec;
+    return SAP_OK;
+}
+
+sap_status sap_run_batch(sap_handle h, double alpha, int32_t iters, double *hist, int64_t *argmins)
+{
+    CHECK_HANDLE(h);
+    if (!h->is_batch) return fail(h, SAP_E_STATE, "not a batch handle");
+    if (iters < 0) return fail(h, SAP_E_ARG, "iters must be >= 0");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(h, SAP_E_ARG, "alpha must be in [0, 1]");
+    for (size_t b = 0; b < h->kids.size(); ++b) {
+        sap_handle kid = h->kids[b];
+        if (kid->k == 0) return fail(h, SAP_E_STATE, "dataset " + std::to_string(b) + " has no basis");
+        sap_status st = ensure_hist(kid, iters + 1);
+        if (st != SAP_OK) return kid_result(h, (int32_t)b, kid, st);
+        if (cudaMemsetAsync(&kid->st->iter, 0, sizeof(int), kid->stream) != cudaSuccess ||
+            cudaStreamSynchronize(kid->stream) != cudaSuccess)
+            return fail(h, SAP_E_CUDA, "dataset stream");
+    }
+    auto run = [&](int chunk, int eval_only, int reps) -> sap_status {
+        if (reps <= 0) return SAP_OK;
+        cudaGraphExec_t exec = nullptr;
+        long long per = 0;
+        sap_status st = batch_graph(h, eval_only ? 0.0 : alpha, eval_only, chunk, &exec, &per);
+        if (st != SAP_OK) return st;
+        cudaError_t e = cudaSuccess;
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            e = cudaGraphLaunch(exec, h->stream);
+            h->launches += per;
+        }
+        cudaGraphExecDestroy(exec);
+        CK(e);
+        return SAP_OK;
+    };
+    const int chunk = std::min(iters, 16);
+    sap_status st = SAP_OK;
+    if (chunk > 0) {
+        st = run(chunk, 0, iters / chunk);
+        if (st == SAP_OK && iters % chunk) st = run(iters % chunk, 0, 1);
+    }
+    if (st == SAP_OK) st = run(1, 1, 1);
+    if (st != SAP_OK) return st;
+    CK(cudaStreamSynchronize(h->stream));
+    for (size_t b = 0; b < h->kids.size(); ++b) {
+        sap_handle kid = h->kids[b];
+        kid->last_iters = iters;
+        const size_t off = b * (size_t)(iters + 1);
+        st = sap_get_history(kid, hist ? hist + off : nullptr, argmins ? argmins + 2 * off : nullptr, iters + 1);
+        if (st != SAP_OK) return kid_result(h, (int32_t)b, kid, st);
+    }
+    return SAP_OK;
 }
 
 } // extern "C"

@@ -9,8 +9,20 @@ the FP64 argmin and the FP64 basis update.  Steps run as replays of captured
 CUDA graphs on a stream owned here, timed with CUDA events on that stream.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                        [--workload moment_curve|fp64_small|sweep|batch|softmin]
 Under torchrun every rank runs its own replica (the workload does not need a
 collective); the time is the max over ranks and value counts all ranks.
+
+The default workload is the one above.  The others measure the remaining
+forms of the hot path, one JSON line each, on their own synthetic inputs:
+  fp64_small -- plain form in FP64, moment curve N = 200, n = 10, k = 3,
+                1000 iterations (launch/latency bound);
+  sweep      -- dimension sweep k = 1..20 over N = 4096 blob images of
+                64 x 64 pixels (n = 4096), 500 iterations;
+  batch      -- 32 hyperspectral scenes (n = 224, N log-uniform in
+                [500, 20000], BF16, eps = 0.05), k = 10, all advancing together;
+  softmin    -- soft-min Riemannian ascent, moment curve N = 16384, n = 100,
+                k = 5, tau = 0.01, 200 steps.
 """
 from __future__ import annotations
 
@@ -46,9 +58,11 @@ def kernel_source_sha() -> str:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="moment_curve",
+                    choices=["moment_curve", "fp64_small", "sweep", "batch", "softmin"])
     return ap.parse_args()
 
 
@@ -220,6 +234,7 @@ def run_native(args):
     sap.set_stream(stream)
     sap.set_path("restructured")
     sap.set_basis(U0)
+    tuning = sap.autotune(alpha, 16)
 
     # warm-up (also captures the graphs the timed run replays)
     sap.run(alpha, Wm, history=False)
@@ -252,6 +267,7 @@ def run_native(args):
     splain.set_stream(stream)
     splain.set_path("plain")
     splain.set_basis(U0)
+    tuning_plain = splain.autotune(alpha, 4)
     splain.run(alpha, 5, history=False)
     if Kp % 32:
         splain.run(alpha, Kp % 32, history=False)
@@ -322,7 +338,8 @@ def run_native(args):
         "config": {"workload": cfg["workload"], "N": N, "n": n, "k": k, "alpha": alpha,
                    "path": "restructured", "split": "fp16x2 operands, FP32 accumulate",
                    "l2": "inputs larger than L2: 136 MB of stored lengths streamed every step",
-                   "parallelism": "replicas" if ws > 1 else "single"},
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "tuning": tuning, "tuning_plain": tuning_plain},
         "secant_evals_per_s": value * P,
         "plain": {"value": plain_value, "unit": "iterations/s", "ms_per_step": ms_plain / Kp,
                   "steps": Kp, "secant_evals_per_s": plain_value * P},
@@ -352,12 +369,376 @@ def run_native(args):
     splain.close()
 
 
+# ------------------------------------------------ the other forms of the path
+
+def _common(args, workload, value, unit, ms, K, Wm, dtype, extra_cfg):
+    ws, _, _ = dist()
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": ws, "steps": K, "warmup": Wm,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype, "data": "synthetic", "config": dict({"workload": workload}, **extra_cfg)}
+    return line
+
+
+def _timed(stream, fn):
+    """Device time (ms, CUDA events on the library's stream) and wall time (s)
+    of fn(), which enqueues on `stream` and synchronises."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    out = fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), time.perf_counter() - t0, out
+
+
+def _kernel_ms(sap, name):
+    t, c = sap.kernel_time(name)
+    return (t / c if c else None), c
+
+
+def run_fp64_small(args):
+    """Plain form in FP64 on the small moment-curve workload: launch/latency
+    bound (19,900 pairs per iteration)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1807_03425_gb300 import Sap
+    _, rank, local = dist()
+    torch.cuda.set_device(local)
+    cfg = W.CONFIGS["c1"]
+    N, n, k, alpha, T = cfg["N"], 2 * cfg["m"], cfg["k"], cfg["alpha"], cfg["T"]
+    X = W.moment_curve(N, cfg["m"], cfg["data_seed"], np.float64)
+    U0 = W.random_basis(n, k, cfg["basis_seed"])
+    P = N * (N - 1) // 2
+    K = args.steps if args.steps else 5 * T
+    Wm = max(args.warmup if args.warmup is not None else 3, 3)
+    stream = torch.cuda.Stream()
+    s = Sap(X)
+    s.set_stream(stream)
+    s.set_basis(U0)
+    tuning = s.autotune(alpha, 16)
+    for _ in range(Wm):
+        s.run(alpha, T, history=False)
+    reps = max(1, K // T)
+    st0 = s.stats()["kernel_launches"]
+    clocks = Clocks(local)
+    tw0 = time.time()
+
+    def go():
+        for _ in range(reps):
+            s.set_basis(U0)
+            s.run(alpha, T, history=False)
+    ms, wall, _ = _timed(stream, go)
+    clk = clocks.stop(tw0, time.time())
+    launches = s.stats()["kernel_launches"] - st0
+    hist, _ = s.get_history(T + 1)
+    s.set_basis(U0)
+    s.set_profiling(True)
+    s.run(alpha, 200, history=False)
+    kp, _ = _kernel_ms(s, "plain_pass")
+    ku, _ = _kernel_ms(s, "update")
+    s.set_profiling(False)
+    its = reps * T
+    if rank != 0:
+        return
+    line = _common(args, cfg["workload"], its / (ms * 1e-3), "iterations/s", ms / its, its, Wm, "f64",
+                   {"N": N, "n": n, "k": k, "alpha": alpha, "path": "plain", "iterations_per_run": T,
+                    "tuning": tuning,
+                    "l2": "whole problem L2-resident (80 KB)"})
+    line.update({
+        "secant_evals_per_s": its * P / (ms * 1e-3),
+        "us_per_iteration": 1e3 * ms / its,
+        "roofline": {"bound": "latency", "achieved": 1e3 * ms / its, "unit": "us/iteration", "peak": None,
+                     "frac": None, "traffic": None,
+                     "note": "two launches per iteration (plain FP64 pass, FP64 recheck + update) replayed "
+                             "from CUDA graphs; the pass does 1.8 MFLOP FP64"},
+        "kernel_ms_per_step": {"plain_pass": kp, "update": ku},
+        "final_min_ratio": float(hist[-1]),
+        "e2e": {"value": its / wall, "unit": "iterations/s", "h2d_bytes_per_step": n * k * 8 / T,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": launches,
+    })
+    if clk:
+        line["clocks"] = clk
+    t0 = time.perf_counter()
+    import oracle as O
+    O.run(X, U0, alpha, T)
+    dt = time.perf_counter() - t0
+    line["cpu_baseline"] = {"value": T / dt, "unit": "iterations/s", "cores": O.num_threads(), "kind": "oracle",
+                            "sample": "one full %d-iteration FP64 run of the same workload" % T}
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
+def run_sweep(args):
+    """Dimension sweep k = 1..20 over N = 4096 blob images (n = 4096): every
+    iteration advances all 20 bases (one tensor-core product for all of them,
+    then 20 independent pass/recheck/update chains)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1807_03425_gb300 import Sap
+    _, rank, local = dist()
+    torch.cuda.set_device(local)
+    cfg = W.CONFIGS["c3"]
+    N, n, kmax, alpha, thr = cfg["N"], cfg["n"], cfg["kmax"], cfg["alpha"], cfg["threshold"]
+    X = W.blob_images(N, cfg["data_seed"])
+    U0 = W.random_basis(n, kmax, cfg["basis_seed"])
+    P = N * (N - 1) // 2
+    K = args.steps if args.steps else cfg["T"]
+    Wm = max(args.warmup if args.warmup is not None else 8, 3)
+    stream = torch.cuda.Stream()
+    s = Sap(X)
+    s.set_stream(stream)
+    s.set_basis(U0)              # the widest basis: its tuning serves every k
+    tuning = s.autotune(alpha, 4)
+    s.estimate_dim(U0, Wm, alpha, thr)
+    st0 = s.stats()["kernel_launches"]
+    clocks = Clocks(local)
+    tw0 = time.time()
+    ms, wall, (kout, ratios) = _timed(stream, lambda: s.estimate_dim(U0, K, alpha, thr))
+    clk = clocks.stop(tw0, time.time())
+    launches = s.stats()["kernel_launches"] - st0
+    # kernel classes, launched one by one (the bases' chains still overlap)
+    s.set_profiling(True)
+    s.estimate_dim(U0, 16, alpha, thr)
+    kt = {name: _kernel_ms(s, name) for name in ("gemm_y", "restructured_pass", "explicit_recheck", "update")}
+    s.set_profiling(False)
+    its = K
+    it_s = its / (ms * 1e-3)
+    # per iteration: sum over k of (2k + 2) flops per pair in the passes; the
+    # product is 3 MMAs of 2 N n (padded widths: 256) on the tensor cores
+    pass_flops = P * sum(2 * k + 2 for k in range(1, kmax + 1))
+    gemm_flops = 3 * 2 * N * n * 256
+    sm_max = peaks()[1]
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    bf16_peak = None
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as f:
+            bf16_peak = float(json.load(f)["bf16_tflops_sustained"])
+    if rank != 0:
+        return
+    line = _common(args, cfg["workload"], it_s, "sweep iterations/s", ms / its, its, Wm, "f32",
+                   {"N": N, "n": n, "k": "1..%d" % kmax, "alpha": alpha, "threshold": thr, "tuning": tuning,
+                    "l2": "stored lengths 33.5 MB (L2-resident, shared by the 20 bases); X operands 67 MB"})
+    pass_ms = kt["restructured_pass"][0] or 0.0
+    line.update({
+        "sap_iterations_per_s": it_s * kmax,
+        "secant_evals_per_s": it_s * kmax * P,
+        "k_estimate": kout, "ratios": [float(r) for r in ratios],
+        "roofline": {"kernel": "whole sweep iteration (20 passes)", "bound": "alu",
+                     "achieved": pass_flops / (ms * 1e-3 / its) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": pass_flops / (ms * 1e-3 / its) / 1e12 / fp32_peak, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                     "alg_flops_per_iteration": pass_flops},
+        "gemm_roofline": {"kernel": "gemm_y", "bound": "tensor",
+                          "achieved": gemm_flops / (kt["gemm_y"][0] * 1e-3) / 1e12 if kt["gemm_y"][0] else None,
+                          "peak": bf16_peak, "unit": "TFLOP/s",
+                          "frac": (gemm_flops / (kt["gemm_y"][0] * 1e-3) / 1e12 / bf16_peak)
+                          if (kt["gemm_y"][0] and bf16_peak) else None,
+                          "peak_source": "measured bf16_tflops_sustained (FP16 operands: same nominal rate)"},
+        "kernel_ms_per_launch": {name: v[0] for name, v in kt.items()},
+        "pass_ms_per_basis_avg": pass_ms,
+        "e2e": {"value": its / wall, "unit": "sweep iterations/s", "h2d_bytes_per_step": n * kmax * 8 / its,
+                "d2h_bytes_per_step": kmax * 8 / its},
+        "gpu_launches": launches,
+    })
+    if clk:
+        line["clocks"] = clk
+    import oracle as O
+    Ns = 256
+    Xs = X[:Ns].astype(np.float64)
+    t0 = time.perf_counter()
+    for k in range(1, kmax + 1):
+        O.step(Xs, U0[:k], alpha)
+    dt = time.perf_counter() - t0
+    Ps = Ns * (Ns - 1) // 2
+    line["cpu_baseline"] = {"value": (Ps / P) / dt, "unit": "sweep iterations/s", "cores": O.num_threads(),
+                            "kind": "oracle",
+                            "sample": "one FP64 step of each k = 1..20 over the first %d images (%d pairs), "
+                                      "scaled by %d/%d pairs" % (Ns, Ps, Ps, P)}
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
+def run_batch(args):
+    """32 uneven hyperspectral scenes advancing together (one captured graph
+    per chunk of iterations, one branch per scene)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1807_03425_gb300 import BF16, SapBatch
+    _, rank, local = dist()
+    torch.cuda.set_device(local)
+    cfg = W.CONFIGS["c4"]
+    B, n, k, alpha, eps = cfg["B"], cfg["n"], cfg["k"], cfg["alpha"], cfg["eps"]
+    Xs, Ns = W.hyperspectral_batch(B, cfg["data_seed"])
+    Us = [W.random_basis(n, k, cfg["basis_seed"] + b) for b in range(B)]
+    Ptot = sum(N * (N - 1) // 2 for N in Ns)
+    K = args.steps if args.steps else 160
+    Wm = max(args.warmup if args.warmup is not None else 16, 3)
+    stream = torch.cuda.Stream()
+    sb = SapBatch([W.bf16_bits(X) for X in Xs], dtype=BF16)
+    sb.set_stream(stream)
+    sb.set_min_secant_length(eps)
+    for b in range(B):
+        sb.set_basis(b, Us[b])
+    sb.autotune(alpha, 4)
+    for b in range(B):
+        sb.set_basis(b, Us[b])
+    sb.run(alpha, Wm, history=False)
+    sb.run(alpha, K, history=False)  # same chunking as the timed call: graphs cached
+    for b in range(B):
+        sb.set_basis(b, Us[b])
+    st = sb.stats()
+    st0 = st["kernel_launches"]
+    clocks = Clocks(local)
+    tw0 = time.time()
+    ms, wall, _ = _timed(stream, lambda: sb.run(alpha, K, history=False))
+    clk = clocks.stop(tw0, time.time())
+    st1 = sb.stats()
+    launches = st1["kernel_launches"] - st0
+    its = K
+    it_s = its / (ms * 1e-3)
+    hbm = peaks()[0]
+    alg = 4 * (Ptot - st1["n_excluded"] - st1["n_near"])
+    if rank != 0:
+        return
+    line = _common(args, cfg["workload"], it_s, "batch iterations/s", ms / its, its, Wm, "f32",
+                   {"datasets": B, "N_min": min(Ns), "N_max": max(Ns), "n": n, "k": k, "alpha": alpha,
+                    "eps": eps, "input": "BF16 data, FP32 arithmetic",
+                    "l2": "inputs larger than L2: %.2f GB of stored lengths streamed every iteration" % (4 * Ptot / 1e9)})
+    line.update({
+        "sap_iterations_per_s": it_s * B,
+        "secant_evals_per_s": it_s * Ptot,
+        "pairs_total": Ptot, "pairs_excluded": st1["n_excluded"], "near_pairs": st1["n_near"],
+        "roofline": {"kernel": "whole batch iteration (32 passes + tails)", "bound": "hbm",
+                     "achieved": alg / (ms * 1e-3 / its) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": alg / (ms * 1e-3 / its) / 1e9 / hbm, "traffic": None,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                     "alg_bytes_per_iteration": alg},
+        "e2e": {"value": its / wall, "unit": "batch iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": launches,
+    })
+    if clk:
+        line["clocks"] = clk
+    import oracle as O
+    b0 = int(np.argmin(Ns))
+    Xs0 = Xs[b0].astype(np.float64)
+    t0 = time.perf_counter()
+    O.step(Xs0, Us[b0], alpha, eps=eps)
+    dt = time.perf_counter() - t0
+    P0 = Ns[b0] * (Ns[b0] - 1) // 2
+    line["cpu_baseline"] = {"value": (P0 / Ptot) / dt, "unit": "batch iterations/s", "cores": O.num_threads(),
+                            "kind": "oracle",
+                            "sample": "one FP64 step of the smallest scene (N = %d, %d pairs), scaled by "
+                                      "%d/%d pairs of the batch" % (Ns[b0], P0, P0, Ptot)}
+    print(json.dumps(line), flush=True)
+    sb.close()
+
+
+def run_softmin(args):
+    """Soft-min Riemannian ascent: each step is a forward pass, a backward
+    pass (pair tiles recomputed), the gradient contraction and the FP64
+    retraction, on the moment curve N = 16384, n = 100, k = 5."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1807_03425_gb300 import Sap
+    _, rank, local = dist()
+    torch.cuda.set_device(local)
+    cfg = W.CONFIGS["c5"]
+    N, n, k, tau, eta = cfg["N"], 2 * cfg["m"], cfg["k"], cfg["tau"], cfg["eta"]
+    X = W.moment_curve(N, cfg["m"], cfg["data_seed"], np.float32)
+    U0 = W.random_basis(n, k, cfg["basis_seed"])
+    P = N * (N - 1) // 2
+    K = args.steps if args.steps else cfg["steps"]
+    Wm = max(args.warmup if args.warmup is not None else 3, 3)
+    stream = torch.cuda.Stream()
+    s = Sap(X)
+    s.set_stream(stream)
+    s.set_path("restructured")
+    s.set_basis(U0)
+    s.softmin_ascent(tau, eta, Wm)
+    s.set_basis(U0)
+    st0 = s.stats()["kernel_launches"]
+    clocks = Clocks(local)
+    tw0 = time.time()
+    ms, wall, hist = _timed(stream, lambda: s.softmin_ascent(tau, eta, K))
+    clk = clocks.stop(tw0, time.time())
+    launches = s.stats()["kernel_launches"] - st0
+    Uf = s.get_basis()
+    _, _, rmin = s.min_secant()
+    s.set_basis(U0)
+    s.set_profiling(True)
+    s.softmin_ascent(tau, eta, 10)
+    kt = {name: _kernel_ms(s, name) for name in ("softmin_forward", "softmin_backward", "softmin_near",
+                                                 "softmin_other")}
+    s.set_profiling(False)
+    hbm = peaks()[0]
+    nex = s.stats()["n_excluded"] + s.stats()["n_near"]
+    alg = 4 * (P - nex)
+    its = K
+    if rank != 0:
+        return
+    fwd, bwd = kt["softmin_forward"][0], kt["softmin_backward"][0]
+    dom = "softmin_backward" if (bwd or 0) >= (fwd or 0) else "softmin_forward"
+    dms = kt[dom][0]
+    line = _common(args, cfg["workload"], its / (ms * 1e-3), "ascent steps/s", ms / its, its, Wm, "f32",
+                   {"N": N, "n": n, "k": k, "tau": tau, "eta": eta,
+                    "l2": "inputs larger than L2: 537 MB of stored lengths read twice per step"})
+    line.update({
+        "pair_evals_per_s": 2 * its * P / (ms * 1e-3),
+        "softmin_first": float(hist[0]), "softmin_final": float(hist[-1]),
+        "min_ratio_final": float(rmin),
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": alg / (dms * 1e-3) / 1e9 if dms else None,
+                     "peak": hbm, "unit": "GB/s", "frac": alg / (dms * 1e-3) / 1e9 / hbm if dms else None,
+                     "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                     "alg_bytes_per_launch": alg, "avg_launch_ms": dms},
+        "kernel_ms_per_launch": {name: v[0] for name, v in kt.items()},
+        "e2e": {"value": its / wall, "unit": "ascent steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 8},
+        "gpu_launches": launches,
+    })
+    if clk:
+        line["clocks"] = clk
+    import oracle as O
+    Ns = 1024
+    Xs = X[:Ns].astype(np.float64)
+    t0 = time.perf_counter()
+    O.softmin_ascent_step(Xs, U0, tau, eta)
+    dt = time.perf_counter() - t0
+    Ps = Ns * (Ns - 1) // 2
+    line["cpu_baseline"] = {"value": (Ps / P) / dt, "unit": "ascent steps/s", "cores": O.num_threads(),
+                            "kind": "oracle",
+                            "sample": "one FP64 ascent step over the first %d points (%d pairs), scaled by "
+                                      "%d/%d pairs" % (Ns, Ps, Ps, P)}
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
 def main():
     args = parse()
+    if args.impl == "reference" or args.workload == "moment_curve":
+        if args.steps is None:
+            args.steps = 20000
+        if args.warmup is None:
+            args.warmup = 200
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "moment_curve":
         run_native(args)
+    else:
+        {"fp64_small": run_fp64_small, "sweep": run_sweep, "batch": run_batch,
+         "softmin": run_softmin}[args.workload](args)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.impl != "reference":
         import torch.distributed as tdist
         if tdist.is_initialized():

@@ -312,6 +312,58 @@ sap_status sap_get_basis_b(sap_handle h, int32_t b, double *U_out, int out_is_de
 sap_status sap_min_secant_b(sap_handle h, int32_t b, int64_t *i, int64_t *j, double *ratio);
 sap_status sap_run_batch(sap_handle h, double alpha, int32_t iters, double *hist, int64_t *argmins);
 
+/*
+ * Cap of the per-pair error bound of the restructured pass (restructured
+ * form of Sec. IV's argmin step, FP32/BF16 data).  The tensor-core Y gives
+ * each pair's ratio a certified error b_ij = sqrt(k) eps_Y (|x_i - xbar| +
+ * |x_j - xbar|) / d_ij; pairs with b_ij above the cap are re-evaluated from
+ * explicit differences every iteration (the near list), the others are
+ * filtered in the pass with their own b_ij.  A larger cap gives a shorter
+ * near list and a wider coarse filter; results do not depend on it.
+ * Default 5e-4; 1e-6 <= b_cap <= 0.25, else SAP_E_ARG.  sap_autotune may
+ * change it.  On a batch handle, every dataset.
+ */
+sap_status sap_set_pass_bound(sap_handle h, double b_cap);
+
+/*
+ * Launch parameters of one iteration.  None of them changes a result (every
+ * choice selects certified candidate sets and takes the same FP64
+ * decisions); they only move time.
+ */
+typedef struct {
+    double pass_bound;              /* cap of the restructured pass's per-pair bound (sap_set_pass_bound) */
+    int32_t pass_stages;            /* TMA ring depth of the restructured pass: 2 or 3; 0 = as many as fit */
+    int32_t explicit_blocks_per_sm; /* explicit-difference tier grid, 1..8 blocks per SM */
+    int32_t update_blocks;          /* FP64 recheck + update grid, 0 (one per SM) .. 304 */
+    int32_t plain_blocks_per_sm;    /* plain pass grid, 1..8 blocks per SM (FP64 data: twice) */
+    double us_per_iteration;        /* measured by sap_autotune; 0 when set by hand */
+} sap_tuning;
+
+/*
+ * Autotuner (the paper has no counterpart; its Sec. V gives no launch
+ * shapes).  Times candidate parameter sets on the handle's current basis,
+ * one parameter at a time from the current set, each as `iters` SAP
+ * iterations with step alpha replayed from captured graphs (best of two
+ * runs, CUDA events on the handle's stream), and keeps the fastest.  The
+ * basis is restored afterwards and the iteration counter restarts, as after
+ * sap_set_basis.  The choice is cached for the process under the problem's
+ * shape (N, n, k, dtype, path, split, eps) and applied automatically by
+ * sap_set_basis, sap_set_path, sap_set_split and sap_set_min_secant_length
+ * when their handle reaches a new shape that has a cached choice
+ * (parameters set by hand stay until the shape changes); if the environment
+ * variable SAP_TUNE_CACHE names a file, choices are appended to it and read back by
+ * later processes.  1 <= iters <= 4096.  On a batch handle every dataset is
+ * tuned.  out (nullable) receives the chosen set.  Synchronises.
+ */
+sap_status sap_autotune(sap_handle h, double alpha, int32_t iters, sap_tuning *out);
+
+/* The handle's current launch parameters. */
+sap_status sap_get_tuning(sap_handle h, sap_tuning *out);
+
+/* Set the launch parameters by hand (ranges as in sap_tuning, else
+ * SAP_E_ARG).  On a batch handle, every dataset. */
+sap_status sap_set_tuning(sap_handle h, const sap_tuning *in);
+
 /* Read the handle's statistics. */
 sap_status sap_get_stats(sap_handle h, sap_stats *out);
 

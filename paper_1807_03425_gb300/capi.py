@@ -47,6 +47,16 @@ class Stats(ctypes.Structure):
                 ("y_error_unit", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("pass_bound", ctypes.c_double), ("pass_stages", ctypes.c_int32),
+                ("explicit_blocks_per_sm", ctypes.c_int32), ("update_blocks", ctypes.c_int32),
+                ("plain_blocks_per_sm", ctypes.c_int32), ("us_per_iteration", ctypes.c_double)]
+
+
+def _tuning_dict(t):
+    return {name: getattr(t, name) for name, _ in Tuning._fields_}
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -97,6 +107,10 @@ def load_library():
         "sap_softmin_forward": ([vp, f64, f64p], i32),
         "sap_softmin_backward": ([vp, f64, f64, vp, i32], i32),
         "sap_softmin_ascent": ([vp, f64, f64, i32, vp], i32),
+        "sap_set_pass_bound": ([vp, f64], i32),
+        "sap_autotune": ([vp, f64, i32, ctypes.POINTER(Tuning)], i32),
+        "sap_get_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
+        "sap_set_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -192,6 +206,31 @@ def sap_set_split(h, split):
 
 def sap_set_min_secant_length(h, eps):
     _check(h, load_library().sap_set_min_secant_length(h, float(eps)))
+
+
+def sap_set_pass_bound(h, b_cap):
+    _check(h, load_library().sap_set_pass_bound(h, b_cap))
+
+
+def sap_autotune(h, alpha, iters):
+    t = Tuning()
+    _check(h, load_library().sap_autotune(h, alpha, iters, ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def sap_get_tuning(h):
+    t = Tuning()
+    _check(h, load_library().sap_get_tuning(h, ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def sap_set_tuning(h, **params):
+    t = Tuning()
+    cur = sap_get_tuning(h) if params.keys() != {n for n, _ in Tuning._fields_} else {}
+    cur.update(params)
+    for name, _ in Tuning._fields_:
+        setattr(t, name, cur.get(name, 0))
+    _check(h, load_library().sap_set_tuning(h, ctypes.byref(t)))
 
 
 def sap_set_basis(h, U):
@@ -447,6 +486,18 @@ class Sap:
     def set_min_secant_length(self, eps):
         sap_set_min_secant_length(self.h, eps)
 
+    def set_pass_bound(self, b_cap):
+        sap_set_pass_bound(self.h, b_cap)
+
+    def autotune(self, alpha, iters=16):
+        return sap_autotune(self.h, alpha, iters)
+
+    def tuning(self):
+        return sap_get_tuning(self.h)
+
+    def set_tuning(self, **params):
+        sap_set_tuning(self.h, **params)
+
     def set_basis(self, U):
         sap_set_basis(self.h, U)
         self.k = int(U.shape[0])
@@ -526,8 +577,18 @@ class SapBatch:
         except Exception:
             pass
 
+    def set_stream(self, stream):
+        sap_set_stream(self.h, stream)
+
     def set_min_secant_length(self, eps):
         sap_set_min_secant_length(self.h, eps)
+
+    def autotune(self, alpha, iters=4):
+        """Tune every dataset (each against its own shape)."""
+        _check(self.h, load_library().sap_autotune(self.h, alpha, iters, None))
+
+    def set_pass_bound(self, b_cap):
+        sap_set_pass_bound(self.h, b_cap)
 
     def set_split(self, split):
         sap_set_split(self.h, {"fp16": SPLIT_FP16, "bf16": SPLIT_BF16}.get(split, split))

@@ -12,6 +12,7 @@
 #include "restructured.cuh"
 #include "softmin.cuh"
 #include "sweep.cuh"
+#include "tune.cuh"
 #include "../../include/sap.h"
 
 #include <cuda_bf16.h>
@@ -36,6 +37,7 @@ struct GraphEntry {
     double alpha;
     int eval_only;
     int chunk;
+    long long launches;   // kernels one replay launches (batch graphs)
 };
 
 double gamma_u(double m, double u) { return m * u / (1.0 - m * u); }
@@ -94,7 +96,12 @@ struct sap_ctx {
 
     long long launches = 0;
     std::vector<GraphEntry> graphs;
+    long long graph_gen = 0;   // bumped whenever this handle's graphs are dropped
+    long long kids_gen = -1;   // batch: sum of the datasets' graph_gen its graphs were made at
 
+    TuneParams tune;          // launch parameters (tune.cu)
+    TuneKey tune_key;         // shape the parameters were last applied for
+    bool tuning = false;      // the autotuner is timing this handle
     bool profiling = false;
     double ktime[kClasses] = {};
     long long kcount[kClasses] = {};
@@ -148,6 +155,7 @@ void drop_graphs(sap_handle h)
 {
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
+    h->graph_gen++;
 }
 
 cudaEvent_t get_event(sap_handle h)
@@ -230,7 +238,7 @@ sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only)
             PlainArgsF64 a;
             a.X = h->X64; a.N = (int)h->N; a.n = h->n; a.U64 = h->U64; a.k = h->k;
             a.tiles = h->tiles; a.ntiles = h->ntiles;
-            a.grid = std::min(h->ntiles, 4 * h->sms);
+            a.grid = std::min(h->ntiles, 2 * std::max(1, h->tune.plain_per_sm) * h->sms);
             a.eps2 = h->eps2_f64; a.cert = cert_plain_f64(); a.st = h->st;
             a.cand = h->cand1; a.cand_cap = h->cap;
             Timed t(h, K_PLAIN);
@@ -239,7 +247,7 @@ sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only)
             PlainArgsF32 a;
             a.X = h->X32; a.N = (int)h->N; a.n = h->n; a.U32 = h->U32; a.k = h->k; a.KP = h->KP;
             a.tiles = h->tiles; a.ntiles = h->ntiles;
-            a.grid = std::min(h->ntiles, 2 * h->sms);
+            a.grid = std::min(h->ntiles, std::max(1, h->tune.plain_per_sm) * h->sms);
             a.eps2_lo = h->eps2_lo; a.eps2_hi = h->eps2_hi; a.cert = c32; a.st = h->st;
             a.cand = h->cand1; a.cand_cap = h->cap;
             Timed t(h, K_PLAIN);
@@ -260,7 +268,8 @@ sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only)
         u.split_bf16 = h->split == SAP_SPLIT_BF16; u.split_scale = h->split == SAP_SPLIT_BF16 ? 256.f : 2048.f;
         u.k = h->k; u.alpha = alpha; u.mode = (int)h->mode; u.eval_only = eval_only;
         u.eps2 = h->eps2_f64; u.list = list; u.cap = (unsigned int)h->cap; u.which = which;
-        u.partials = h->partials; u.grid = std::min(h->sms, kRecheckBlocks);
+        u.partials = h->partials;
+        u.grid = std::min(h->tune.su_blocks > 0 ? h->tune.su_blocks : h->sms, kRecheckBlocks);
         u.work = h->work; u.st = h->st; u.hist = h->hist; u.argmin = h->am; u.seed_cert = c32;
         Timed t(h, K_UPDATE);
         CK(launch_select_update(u, s));
@@ -379,6 +388,24 @@ sap_status handle_reset_state(sap_handle h) { return reset_state(h); }
 int handle_profiling(sap_handle h) { return h->profiling ? 1 : 0; }
 long long handle_launches(sap_handle h) { return h->launches; }
 SweepState *&sweep_state(sap_handle h) { return h->sw; }
+long long handle_graph_gen(sap_handle h) { return h->graph_gen; }
+TuneParams &handle_tune(sap_handle h) { return h->tune; }
+TuneKey handle_tune_key(sap_handle h)
+{
+    TuneKey t;
+    t.N = h->N;
+    t.n = h->n;
+    t.k = h->k;
+    t.dt = (int)h->dt;
+    t.path = (int)h->path;
+    t.split = (int)h->split;
+    std::memcpy(&t.eps_bits, &h->eps, sizeof(double));
+    return t;
+}
+bool &handle_tuning_flag(sap_handle h) { return h->tuning; }
+TuneKey &handle_applied_key(sap_handle h) { return h->tune_key; }
+void handle_drop_graphs(sap_handle h) { drop_graphs(h); }
+bool handle_path_restructured(sap_handle h) { return h->path == SAP_RESTRUCTURED && h->dt != SAP_F64; }
 int handle_mode(sap_handle h) { return (int)h->mode; }
 Cert handle_seed_cert(int n, int k) { return cert_plain_f32(n, k); }
 sap_status handle_check_status(sap_handle h, ProbState *st)
@@ -423,6 +450,7 @@ sap_status sap_destroy(sap_handle h)
 {
     if (!h) return SAP_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);  // before the datasets whose buffers the graphs name
     for (sap_handle k : h->kids) sap_destroy(k);
     h->kids.clear();
     for (cudaEvent_t e : h->kid_done) cudaEventDestroy(e);
@@ -568,7 +596,7 @@ sap_status sap_set_path(sap_handle h, sap_path p)
         return fail(h, SAP_E_UNSUPPORTED, "the FP32 plain form supports k <= 8");
     if (p != h->path) drop_graphs(h);
     h->path = p;
-    return SAP_OK;
+    return tune_lookup(h);
 }
 
 sap_status sap_set_update_mode(sap_handle h, sap_update_mode m)
@@ -596,7 +624,9 @@ sap_status sap_set_split(sap_handle h, sap_split s)
     // re-split the current basis for the new operand type
     std::vector<double> Uh((size_t)h->n * h->k);
     CK(cudaMemcpy(Uh.data(), h->U64, Uh.size() * sizeof(double), cudaMemcpyDeviceToHost));
-    return restructured_upload_basis(h, Uh.data());
+    st = restructured_upload_basis(h, Uh.data());
+    if (st != SAP_OK) return st;
+    return tune_lookup(h);
 }
 
 sap_status sap_set_min_secant_length(sap_handle h, double eps)
@@ -611,7 +641,80 @@ sap_status sap_set_min_secant_length(sap_handle h, double eps)
         sap_status s = restructured_prepare(h);
         if (s != SAP_OK) return s;
     }
+    sap_status s = tune_lookup(h);
+    if (s != SAP_OK) return s;
     return reset_state(h);
+}
+
+sap_status sap_set_pass_bound(sap_handle h, double b_cap)
+{
+    CHECK_HANDLE(h);
+    FORWARD_BATCH(h, sap_set_pass_bound(kid, b_cap));
+    if (!(b_cap >= 1e-6 && b_cap <= 0.25)) return fail(h, SAP_E_ARG, "b_cap must be in [1e-6, 0.25]");
+    if (h->dt == SAP_F64) return fail(h, SAP_E_UNSUPPORTED, "no restructured form for FP64 data");
+    CK(cudaStreamSynchronize(h->stream));
+    TuneParams p = h->tune;
+    p.b_cap = b_cap;
+    p.us_per_iter = 0;
+    return tune_apply(h, p);
+}
+
+static void to_public(const TuneParams &p, sap_tuning *out)
+{
+    out->pass_bound = p.b_cap;
+    out->pass_stages = p.pass_stages;
+    out->explicit_blocks_per_sm = p.expl_per_sm;
+    out->update_blocks = p.su_blocks;
+    out->plain_blocks_per_sm = p.plain_per_sm;
+    out->us_per_iteration = p.us_per_iter;
+}
+
+sap_status sap_get_tuning(sap_handle h, sap_tuning *out)
+{
+    CHECK_HANDLE(h);
+    NOT_BATCH(h);
+    if (!out) return fail(h, SAP_E_ARG, "null output");
+    to_public(h->tune, out);
+    return SAP_OK;
+}
+
+sap_status sap_set_tuning(sap_handle h, const sap_tuning *in)
+{
+    CHECK_HANDLE(h);
+    if (!in) return fail(h, SAP_E_ARG, "null input");
+    FORWARD_BATCH(h, sap_set_tuning(kid, in));
+    if (!(in->pass_bound >= 1e-6 && in->pass_bound <= 0.25) || in->pass_stages < 0 || in->pass_stages > 3 ||
+        in->explicit_blocks_per_sm < 1 || in->explicit_blocks_per_sm > 8 || in->update_blocks < 0 ||
+        in->update_blocks > kRecheckBlocks || in->plain_blocks_per_sm < 1 || in->plain_blocks_per_sm > 8)
+        return fail(h, SAP_E_ARG, "tuning parameter out of range");
+    CK(cudaStreamSynchronize(h->stream));
+    TuneParams p;
+    p.b_cap = in->pass_bound;
+    p.pass_stages = in->pass_stages;
+    p.expl_per_sm = in->explicit_blocks_per_sm;
+    p.su_blocks = in->update_blocks;
+    p.plain_per_sm = in->plain_blocks_per_sm;
+    p.us_per_iter = 0;
+    return tune_apply(h, p);
+}
+
+sap_status sap_autotune(sap_handle h, double alpha, int32_t iters, sap_tuning *out)
+{
+    CHECK_HANDLE(h);
+    if (h->is_batch) {
+        for (size_t b = 0; b < h->kids.size(); ++b) {
+            sap_status st = sap_autotune(h->kids[b], alpha, iters, nullptr);
+            if (st != SAP_OK) return fail(h, st, "dataset " + std::to_string(b) + ": " + h->kids[b]->err);
+        }
+        return SAP_OK;
+    }
+    if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(h, SAP_E_ARG, "alpha must be in [0, 1]");
+    if (iters < 1 || iters > 4096) return fail(h, SAP_E_ARG, "iters must be in [1, 4096]");
+    sap_status st = tune_handle(h, alpha, iters);
+    if (st != SAP_OK) return st;
+    if (out) to_public(h->tune, out);
+    return SAP_OK;
 }
 
 sap_status sap_set_basis(sap_handle h, const double *U, int32_t k, int u_is_device)
@@ -667,6 +770,8 @@ sap_status sap_set_basis(sap_handle h, const double *U, int32_t k, int u_is_devi
         sap_status s = restructured_upload_basis(h, Uh.data());
         if (s != SAP_OK) return s;
     }
+    sap_status s = tune_lookup(h);
+    if (s != SAP_OK) return s;
     return reset_state(h);
 }
 
@@ -739,7 +844,7 @@ static sap_status graph_for(sap_handle h, double alpha, int eval_only, int chunk
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     CK(e);
-    h->graphs.push_back({exec, alpha, eval_only, chunk});
+    h->graphs.push_back({exec, alpha, eval_only, chunk, 0});
     *out = exec;
     return SAP_OK;
 }
@@ -1085,18 +1190,33 @@ sap_status sap_run_batch(sap_handle h, double alpha, int32_t iters, double *hist
             cudaStreamSynchronize(kid->stream) != cudaSuccess)
             return fail(h, SAP_E_CUDA, "dataset stream");
     }
+    // the batch's graphs replay the datasets' buffers: rebuild them once any
+    // dataset dropped its own graphs (new basis, lengths, history buffers ...)
+    long long gen = 0;
+    for (sap_handle kid : h->kids) gen += kid->graph_gen;
+    if (gen != h->kids_gen) {
+        drop_graphs(h);
+        h->kids_gen = gen;
+    }
     auto run = [&](int chunk, int eval_only, int reps) -> sap_status {
         if (reps <= 0) return SAP_OK;
-        cudaGraphExec_t exec = nullptr;
-        long long per = 0;
-        sap_status st = batch_graph(h, eval_only ? 0.0 : alpha, eval_only, chunk, &exec, &per);
-        if (st != SAP_OK) return st;
+        const double a = eval_only ? 0.0 : alpha;
+        const GraphEntry *ge = nullptr;
+        for (const auto &g : h->graphs)
+            if (g.alpha == a && g.eval_only == eval_only && g.chunk == chunk) ge = &g;
+        if (!ge) {
+            cudaGraphExec_t exec = nullptr;
+            long long per = 0;
+            sap_status st = batch_graph(h, a, eval_only, chunk, &exec, &per);
+            if (st != SAP_OK) return st;
+            h->graphs.push_back({exec, a, eval_only, chunk, per});
+            ge = &h->graphs.back();
+        }
         cudaError_t e = cudaSuccess;
         for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-            e = cudaGraphLaunch(exec, h->stream);
-            h->launches += per;
+            e = cudaGraphLaunch(ge->exec, h->stream);
+            h->launches += ge->launches;
         }
-        cudaGraphExecDestroy(exec);
         CK(e);
         return SAP_OK;
     };

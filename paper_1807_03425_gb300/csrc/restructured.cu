@@ -237,16 +237,28 @@ struct PassArgs {
     const float *Y;   // Y^T, KY x Npad
     int KY;
     int Npad;
+    const float *nu;  // ||fl(x_i - mean)||, rounded up (Npad)
+    float beta;       // sqrt(k) eps_Y, rounded up: per-pair bound beta (nu_i + nu_j) / d_ij
     int stages;
-    Cert cert;
+    Cert cert;        // A = the cap of every stored pair's bound (b_cap), rho
     ProbState *st;
     int2 *cand;
     long long cap;
 };
 
+// One ring stage: the w tile, then for each side one 512-byte segment per
+// component of Y^T, then the 128 point norms nu of each side.
 __host__ __device__ inline uint32_t pass_stage_bytes(int KY)
 {
-    return (uint32_t)T * T * 4 + 2u * T * KY * 4;
+    return (uint32_t)T * T * 4 + 2u * T * KY * 4 + 2u * T * 4;
+}
+
+// Certified error of one stored pair's ratio from the tensor-core Y:
+// |r~ - r| <= beta (nu_i + nu_j) / d_ij + rho r, with 1/d_ij = sqrt(w_ij).
+// The same product the length preparation compares with b_cap, rounded up.
+__device__ __forceinline__ float pair_bound(float beta, float nui, float nuj, float w)
+{
+    return beta * (nui + nuj) * sqrtf(w) * 1.000002f;
 }
 
 // Persistent, warp-specialised pass: one block per SM walks the tiles
@@ -261,6 +273,13 @@ __host__ __device__ inline uint32_t pass_stage_bytes(int KY)
 // bounds the minimum from its own pairs (a valid upper bound like any other),
 // tightens the global running bound with a fire-and-forget atomic, and
 // emits its candidates with one atomic per warp when it has any.
+//
+// Bounds.  Every stored pair's error is at most b_p = beta (nu_i + nu_j) /
+// d_ij <= A (= b_cap; pairs above it are on the near list).  The fast path
+// tests each pair against the uniform A; a warp whose tile could tighten the
+// upper bound takes the bound of its minimum from that pair's own b_p, and a
+// pair that passes the uniform test is emitted only if it passes its own:
+// r~_p <= U (1 + rho) + b_p.  Both refinements touch only the rare slow path.
 constexpr int kConsumerWarps = 16;
 constexpr int kPassThreads = (kConsumerWarps + 1) * 32;
 
@@ -271,6 +290,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     constexpr int RSTEP = kConsumerWarps / SR;   // row step of one warp
     constexpr int RPW = T / RSTEP;               // rows per warp
     constexpr int NPR = CPT / 2;                 // column pairs per thread
+    static_assert(RPW * CPT == 32, "one bit per pair of a thread in the emission mask");
     // indexed directly (no integer round trip) so reads stay shared-memory loads
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) uint64_t full[kPassStagesMax], empty[kPassStagesMax];
@@ -279,7 +299,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int KY = a.KY, S = a.stages;
-    const uint32_t wbytes = T * T * 4, ybytes = T * KY * 4, sbytes = wbytes + 2 * ybytes;
+    const uint32_t wbytes = T * T * 4, ybytes = T * KY * 4, sbytes = wbytes + 2 * ybytes + 2 * T * 4;
     const int nmine = blockIdx.x < (unsigned)a.ntiles ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     const long long budget = 4000000000ll;
 
@@ -314,6 +334,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                     tc::bulk_g2s(base + wbytes + ybytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.y * T,
                                  T * 4, &full[s]);
                 }
+                tc::bulk_g2s(base + wbytes + 2 * ybytes, a.nu + (size_t)IJ.x * T, T * 4, &full[s]);
+                tc::bulk_g2s(base + wbytes + 2 * ybytes + T * 4, a.nu + (size_t)IJ.y * T, T * 4, &full[s]);
                 ++issued;
             }
             // no copy of ours may still be in flight when the block exits
@@ -405,26 +427,61 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 mymin = fminf(mymin, v[r][0]);
             }
         }
-        // the warp's reads of stage s are done
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&empty[s]);
-
         const float wmin = warp_min(mymin);
         float U = fminf(fminf(seed, gnow), uwarp);
-        if (wmin < INFINITY) {
-            const float ub = cert_upper(sqrtf(wmin), a.cert);
+        const bool refine = wmin < INFINITY && sqrtf(wmin) < U;  // warp-uniform
+        float thc = cert_emit_threshold(U, a.cert);
+        float thc2 = thc * thc * 1.000001f;
+        if (!refine && !__any_sync(0xffffffffu, mymin <= thc2)) {
+            // fast path: nothing in this tile can bound or be the minimum
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&empty[s]);
+            continue;
+        }
+        const float *nuI = yJ + T * KY;
+        const float *nuJ = nuI + T;
+        if (refine) {
+            // the bound of the tile's minimum from that pair's own error
+            const int src = __ffs(__ballot_sync(0xffffffffu, mymin == wmin)) - 1;
+            float ub = 0.f;
+            if (lane == src) {
+                int prow = row0, pcol = col0;
+#pragma unroll
+                for (int r = 0; r < RPW; ++r)
+#pragma unroll
+                    for (int q = 0; q < CPT; ++q)
+                        if (v[r][q] == wmin) { prow = row0 + r * RSTEP; pcol = col0 + q; }
+                const float b = pair_bound(a.beta, nuI[prow], nuJ[pcol], ws[prow * T + pcol]);
+                ub = (sqrtf(wmin) + b) / (1.0f - a.cert.rho) * 1.000001f;
+            }
+            ub = __shfl_sync(0xffffffffu, ub, src);
             if (lane == 0 && ub < gnow) atomic_min_pos_float(&a.st->run_ub1, ub);
             U = fminf(U, ub);
             uwarp = fminf(uwarp, ub);
+            thc = cert_emit_threshold(U, a.cert);
+            thc2 = thc * thc * 1.000001f;
         }
-        const float th = cert_emit_threshold(U, a.cert);
-        const float th2 = th * th * 1.000001f;
+        // emission: the uniform test, then each survivor against its own bound
+        const float ut = U * (1.0f + a.cert.rho);
+        uint32_t emit = 0u;
         int cnt = 0;
-        if (mymin <= th2)
+        if (mymin <= thc2)
 #pragma unroll
             for (int r = 0; r < RPW; ++r)
 #pragma unroll
-                for (int q = 0; q < CPT; ++q) cnt += v[r][q] <= th2 ? 1 : 0;
+                for (int q = 0; q < CPT; ++q)
+                    if (v[r][q] <= thc2) {
+                        const int prow = row0 + r * RSTEP, pcol = col0 + q;
+                        const float th = (ut + pair_bound(a.beta, nuI[prow], nuJ[pcol], ws[prow * T + pcol])) *
+                                         1.000001f;
+                        if (v[r][q] <= th * th * 1.000001f) {
+                            emit |= 1u << (r * CPT + q);
+                            ++cnt;
+                        }
+                    }
+        // the warp's reads of stage s are done
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&empty[s]);
         if (__any_sync(0xffffffffu, cnt > 0)) {
             int incl = cnt;
 #pragma unroll
@@ -443,7 +500,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 for (int r = 0; r < RPW; ++r)
 #pragma unroll
                     for (int q = 0; q < CPT; ++q)
-                        if (v[r][q] <= th2) {
+                        if (emit >> (r * CPT + q) & 1u) {
                             if (pos < a.cap) a.cand[pos] = make_int2(i0 + row0 + r * RSTEP, j0 + col0 + q);
                             else atomicOr(&a.st->status, ST_OVERFLOW);
                             ++pos;
@@ -776,7 +833,7 @@ Cert cert_pass(int n, int k, double b_cap)
     const double u = std::ldexp(1.0, -24);
     auto g = [&](double m) { return m * u / (1.0 - m * u); };
     Cert c;
-    c.A = (float)b_cap;
+    c.A = (float)(b_cap * 1.0001);  // >= every stored pair's own bound after FP32 rounding
     c.rho = (float)((g(n + 2) + g(k) + 6 * u) * 1.05);
     return c;
 }
@@ -812,6 +869,7 @@ Cert cert_explicit(int n, int k)
 sap_status classify(sap_handle h, int k)
 {
     RestrState &r = restr_state(h);
+    r.b_cap = handle_tune(h).b_cap;
     cudaStream_t s = handle_stream(h);
     RCK(cudaMemsetAsync(r.counters, 0, 8 * sizeof(unsigned int), s));
     WPrepArgs a;
@@ -1008,8 +1066,7 @@ sap_status restructured_upload_basis(sap_handle h, const double *U)
 
 sap_status restructured_set_bound(sap_handle h, double b_cap)
 {
-    RestrState &r = restr_state(h);
-    r.b_cap = b_cap;
+    handle_tune(h).b_cap = b_cap;
     const int k = handle_k(h);
     if (k > 0) return classify(h, k);
     return SAP_OK;
@@ -1062,7 +1119,10 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         p.Y = b.Y;
         p.KY = b.KY;
         p.Npad = r.Npad;
+        p.nu = r.nu;
+        p.beta = (float)(std::sqrt((double)b.k) * r.y_eps * 1.02);
         p.stages = pass_pick_stages(b.KY);
+        if (handle_tune(h).pass_stages >= 2) p.stages = std::min(p.stages, handle_tune(h).pass_stages);
         p.cert = cert_pass(n, b.k, r.b_cap);
         p.st = b.st;
         p.cand = b.cand1;
@@ -1093,7 +1153,7 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         x.cap2 = b.cap;
         handle_count_launch(h, 3, &ea, &eb);
         if (ea) cudaEventRecord(ea, s);
-        RCK(launch_explicit(x, df, 2 * handle_sms(h), s));
+        RCK(launch_explicit(x, df, std::max(1, handle_tune(h).expl_per_sm) * handle_sms(h), s));
         if (eb) cudaEventRecord(eb, s);
         handle_push_timing(h, 3, ea, eb);
     }
@@ -1155,7 +1215,8 @@ void restructured_split_host(sap_handle h, const double *U, int k, uint16_t *hi,
 
 sap_status restructured_classify(sap_handle h, int k)
 {
-    if (restr_state(h).k_cls == k) return SAP_OK;
+    const RestrState &r = restr_state(h);
+    if (r.k_cls == k && r.b_cap == handle_tune(h).b_cap) return SAP_OK;
     return classify(h, k);
 }
 

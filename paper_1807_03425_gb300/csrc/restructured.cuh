@@ -63,6 +63,7 @@ float handle_eps2_hi(sap_handle h);
 void handle_count_launch(sap_handle h, int cls, cudaEvent_t *a, cudaEvent_t *b);
 void handle_push_timing(sap_handle h, int cls, cudaEvent_t a, cudaEvent_t b);
 sap_status handle_fail(sap_handle h, sap_status s, const char *msg);
+TuneParams &handle_tune(sap_handle h);
 
 // One basis of the restructured form: the handle's own, or one of the bases
 // of a dimension sweep that share the handle's dataset, lengths and near list.

@@ -42,6 +42,18 @@ enum StatusBits : int {
     ST_OVERFLOW = 4,
 };
 
+// Launch parameters of one handle, chosen by the autotuner (tune.cu) or set
+// explicitly.  Results never depend on them: every choice evaluates the same
+// certified candidate sets and takes the same FP64 decisions.
+struct TuneParams {
+    double b_cap = 5e-4;     // cap of the restructured pass's per-pair error bound
+    int pass_stages = 0;     // ring depth of the restructured pass (0: as many as fit)
+    int expl_per_sm = 2;     // explicit-difference tier: blocks per SM
+    int su_blocks = 0;       // FP64 recheck + update: blocks (0: one per SM)
+    int plain_per_sm = 2;    // plain pass: blocks per SM (FP64 data: twice as many)
+    double us_per_iter = 0;  // measured by the tuner (0: not tuned)
+};
+
 // Per-problem device state (one basis over one dataset).
 struct ProbState {
     unsigned int seed_ub;   // float bits: upper bound on R* from the watch list

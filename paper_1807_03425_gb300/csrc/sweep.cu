@@ -172,7 +172,7 @@ SelectUpdateArgs update_args(sap_handle h, SweepState &sw, SweepBasis &b, double
     u.cap = (unsigned int)sw.cap;
     u.which = 2;
     u.partials = b.partials;
-    u.grid = std::min(handle_sms(h), kRecheckBlocks);
+    u.grid = std::min(handle_tune(h).su_blocks > 0 ? handle_tune(h).su_blocks : handle_sms(h), kRecheckBlocks);
     u.work = b.work;
     u.st = b.st;
     u.hist = b.hist;
@@ -227,32 +227,52 @@ sap_status run_graph(sap_handle h, SweepState &sw, double alpha, int eval_only, 
         }
         return SAP_OK;
     }
+    // a captured chunk names the handle's buffers and the near-list length:
+    // reuse it while neither changed (the handle bumps its generation
+    // whenever it drops its own graphs)
+    const long long gen = handle_graph_gen(h);
+    const int n_near = restr_state(h).n_near;
+    for (size_t q = 0; q < sw.graphs.size();) {
+        if (sw.graphs[q].gen != gen || sw.graphs[q].n_near != n_near) {
+            cudaGraphExecDestroy(sw.graphs[q].exec);
+            sw.graphs.erase(sw.graphs.begin() + q);
+        } else {
+            ++q;
+        }
+    }
     int done = 0;
     while (done < iters) {
         const int chunk = std::min(kSweepChunk, iters - done);
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        const long long before = handle_launches(h);
-        WCK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
-        sap_status st = SAP_OK;
-        for (int q = 0; q < chunk && st == SAP_OK; ++q) st = enqueue_iteration(h, sw, alpha, eval_only);
-        cudaError_t e = cudaStreamEndCapture(s0, &graph);
-        const long long per_chunk = handle_launches(h) - before;
-        handle_add_launches(h, -per_chunk);
-        if (st != SAP_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return st;
+        const SweepState::Graph *g = nullptr;
+        for (const auto &c : sw.graphs)
+            if (c.alpha == alpha && c.eval_only == eval_only && c.chunk == chunk) g = &c;
+        if (!g) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            const long long before = handle_launches(h);
+            WCK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+            sap_status st = SAP_OK;
+            for (int q = 0; q < chunk && st == SAP_OK; ++q) st = enqueue_iteration(h, sw, alpha, eval_only);
+            cudaError_t e = cudaStreamEndCapture(s0, &graph);
+            const long long per_chunk = handle_launches(h) - before;
+            handle_add_launches(h, -per_chunk);
+            if (st != SAP_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            WCK(e);
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            WCK(e);
+            sw.graphs.push_back({exec, alpha, eval_only, chunk, n_near, gen, per_chunk});
+            g = &sw.graphs.back();
         }
-        WCK(e);
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        WCK(e);
         const int reps = (iters - done) / chunk;
+        cudaError_t e = cudaSuccess;
         for (int q = 0; q < reps && e == cudaSuccess; ++q) {
-            e = cudaGraphLaunch(exec, s0);
-            handle_add_launches(h, per_chunk);
+            e = cudaGraphLaunch(g->exec, s0);
+            handle_add_launches(h, g->launches);
         }
-        cudaGraphExecDestroy(exec);
         WCK(e);
         done += reps * chunk;
     }
@@ -343,6 +363,8 @@ sap_status sweep_basis(sap_handle h, int k, double *U_out, int out_is_device)
 void sweep_free(SweepState *&s)
 {
     if (!s) return;
+    for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
+    s->graphs.clear();
     for (SweepBasis &b : s->b) {
         wfree(b.U64); wfree(b.U32); wfree(b.U32lo); wfree(b.work); wfree(b.st);
         wfree(b.cand1); wfree(b.cand2); wfree(b.partials); wfree(b.hist); wfree(b.am);

@@ -39,6 +39,14 @@ struct SweepState {
     int ksplit = 1;
     ProbState *gst = nullptr;             // status word of the product
     cudaEvent_t fork = nullptr;
+    // captured chunks, reused while the handle's buffers and settings stay
+    struct Graph {
+        cudaGraphExec_t exec;
+        double alpha;
+        int eval_only, chunk, n_near;
+        long long gen, launches;
+    };
+    std::vector<Graph> graphs;
 };
 
 sap_status sweep_run(sap_handle h, const double *U0, int kmax, int iters, double alpha, double threshold,
@@ -49,6 +57,7 @@ void sweep_free(SweepState *&s);
 
 // Engine accessors (capi.cu).
 SweepState *&sweep_state(sap_handle h);
+long long handle_graph_gen(sap_handle h);
 int handle_mode(sap_handle h);
 Cert handle_seed_cert(int n, int k);
 sap_status handle_check_status(sap_handle h, ProbState *st);

@@ -1,0 +1,232 @@
+// tune.cu -- autotuner of the launch parameters of one SAP iteration.
+//
+// The parameters (TuneParams) are the cap of the restructured pass's
+// per-pair error bound (which pairs go on the near list and which are
+// filtered by their own bound), the depth of the pass's TMA ring, and the
+// grid sizes of the explicit-difference tier, of the FP64 recheck + update
+// and of the plain pass.  None of them changes a result: each choice
+// evaluates certified candidate sets and takes the same FP64 decisions, so
+// tuning only moves time.
+//
+// Procedure: from the handle's current parameters, coordinate descent over
+// one parameter at a time; each candidate is timed on the handle's own
+// basis as `iters` graph-replayed SAP iterations (after a warm-up replay
+// that captures the graphs), best of two, with CUDA events on the handle's
+// stream.  The basis is restored afterwards.  Choices are cached per
+// TuneKey for the process, and appended to the file named by the
+// environment variable SAP_TUNE_CACHE when it is set (read back on first
+// use, later lines winning), so a later handle of the same shape starts
+// from the tuned parameters without timing anything.
+#include "tune.cuh"
+#include "restructured.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+namespace sap {
+
+bool TuneKey::operator<(const TuneKey &o) const
+{
+    return std::tie(N, n, k, dt, path, split, eps_bits) < std::tie(o.N, o.n, o.k, o.dt, o.path, o.split, o.eps_bits);
+}
+
+namespace {
+
+std::mutex g_mu;
+std::map<TuneKey, TuneParams> g_cache;
+bool g_loaded = false;
+
+const char *cache_file()
+{
+    const char *p = std::getenv("SAP_TUNE_CACHE");
+    return (p && *p) ? p : nullptr;
+}
+
+// One line per entry: "sap-tune 1 N n k dt path split eps_bits b_cap stages
+// expl_per_sm su_blocks plain_per_sm us_per_iter".
+void load_locked()
+{
+    if (g_loaded) return;
+    g_loaded = true;
+    const char *path = cache_file();
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+        TuneKey k;
+        TuneParams p;
+        int ver = 0;
+        if (std::sscanf(line, "sap-tune %d %lld %d %d %d %d %d %llx %lf %d %d %d %d %lf", &ver, &k.N, &k.n, &k.k,
+                        &k.dt, &k.path, &k.split, &k.eps_bits, &p.b_cap, &p.pass_stages, &p.expl_per_sm,
+                        &p.su_blocks, &p.plain_per_sm, &p.us_per_iter) == 14 &&
+            ver == 1 && p.b_cap >= 1e-6 && p.b_cap <= 0.25 && p.expl_per_sm >= 1 && p.plain_per_sm >= 1 &&
+            p.su_blocks >= 0 && p.pass_stages >= 0)
+            g_cache[k] = p;
+    }
+    std::fclose(f);
+}
+
+void save_locked(const TuneKey &k, const TuneParams &p)
+{
+    g_cache[k] = p;
+    const char *path = cache_file();
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "sap-tune 1 %lld %d %d %d %d %d %llx %.9g %d %d %d %d %.6g\n", k.N, k.n, k.k, k.dt, k.path,
+                 k.split, k.eps_bits, p.b_cap, p.pass_stages, p.expl_per_sm, p.su_blocks, p.plain_per_sm,
+                 p.us_per_iter);
+    std::fclose(f);
+}
+
+bool same_launch(const TuneParams &a, const TuneParams &b)
+{
+    return a.b_cap == b.b_cap && a.pass_stages == b.pass_stages && a.expl_per_sm == b.expl_per_sm &&
+           a.su_blocks == b.su_blocks && a.plain_per_sm == b.plain_per_sm;
+}
+
+} // namespace
+
+sap_status tune_apply(sap_handle h, const TuneParams &p)
+{
+    handle_applied_key(h) = handle_tune_key(h);
+    TuneParams &cur = handle_tune(h);
+    if (same_launch(cur, p)) {
+        cur.us_per_iter = p.us_per_iter;
+        return SAP_OK;
+    }
+    const bool rebound = cur.b_cap != p.b_cap;
+    cur = p;
+    handle_drop_graphs(h);
+    if (rebound && handle_x32(h) && handle_k(h) > 0) return restructured_set_bound(h, p.b_cap);
+    return SAP_OK;
+}
+
+sap_status tune_lookup(sap_handle h)
+{
+    if (handle_tuning_flag(h) || handle_k(h) == 0) return SAP_OK;
+    const TuneKey key = handle_tune_key(h);
+    if (handle_applied_key(h) == key) return SAP_OK;
+    handle_applied_key(h) = key;
+    TuneParams p;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        load_locked();
+        auto it = g_cache.find(key);
+        if (it == g_cache.end()) return SAP_OK;
+        p = it->second;
+    }
+    return tune_apply(h, p);
+}
+
+sap_status tune_handle(sap_handle h, double alpha, int iters)
+{
+    const int n = handle_n_dim(h), k = handle_k(h);
+    cudaStream_t s = handle_stream(h);
+    std::vector<double> U((size_t)n * k);
+    if (cudaStreamSynchronize(s) != cudaSuccess ||
+        cudaMemcpy(U.data(), handle_u64(h), U.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return handle_fail(h, SAP_E_CUDA, "autotune: reading the basis failed");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return handle_fail(h, SAP_E_CUDA, "autotune: event creation failed");
+    }
+    handle_tuning_flag(h) = true;
+    const bool prof = handle_profiling(h) != 0;
+    if (prof) sap_set_profiling(h, 0);
+
+    sap_status st = SAP_OK;
+    // time one parameter set: warm replay (captures), then the best of two
+    auto timed = [&](const TuneParams &c, double *us) -> sap_status {
+        sap_status r = tune_apply(h, c);
+        if (r != SAP_OK) return r;
+        double best = INFINITY;
+        for (int rep = 0; rep < 3; ++rep) {
+            r = sap_set_basis(h, U.data(), k, 0);
+            if (r != SAP_OK) return r;
+            if (rep > 0 && cudaEventRecord(e0, s) != cudaSuccess) return handle_fail(h, SAP_E_CUDA, "event");
+            r = sap_run(h, alpha, iters, nullptr, nullptr);
+            if (r != SAP_OK) return r;
+            if (rep > 0) {
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                    return handle_fail(h, SAP_E_CUDA, "event");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best = std::fmin(best, 1e3 * ms / (iters + 1));
+            }
+        }
+        r = sap_get_history(h, nullptr, nullptr, 0);  // synchronises, reports device status
+        *us = best;
+        return r;
+    };
+
+    TuneParams best = handle_tune(h);
+    double best_us = INFINITY;
+    st = timed(best, &best_us);
+    auto consider = [&](TuneParams c) {
+        if (st != SAP_OK || same_launch(c, best)) return;
+        double us = INFINITY;
+        st = timed(c, &us);
+        if (st == SAP_OK && us < best_us) {
+            best = c;
+            best_us = us;
+        }
+    };
+    const bool restr = handle_path_restructured(h);
+    if (restr) {
+        for (double b : {5e-4, 1e-3, 2e-3, 4e-3, 8e-3, 1.6e-2}) {
+            TuneParams c = best;
+            c.b_cap = b;
+            consider(c);
+        }
+        for (int stg : {0, 2}) {
+            TuneParams c = best;
+            c.pass_stages = stg;
+            consider(c);
+        }
+        for (int e : {1, 2, 4}) {
+            TuneParams c = best;
+            c.expl_per_sm = e;
+            consider(c);
+        }
+    } else {
+        for (int p : {1, 2, 4}) {
+            TuneParams c = best;
+            c.plain_per_sm = p;
+            consider(c);
+        }
+    }
+    for (int sb : {38, 76, 152, 304}) {
+        TuneParams c = best;
+        c.su_blocks = sb;
+        consider(c);
+    }
+    if (st == SAP_OK) {
+        best.us_per_iter = best_us;
+        st = tune_apply(h, best);
+    }
+    // leave the basis as it was (the iteration counter restarts)
+    const sap_status rs = sap_set_basis(h, U.data(), k, 0);
+    if (st == SAP_OK) st = rs;
+    handle_tuning_flag(h) = false;
+    if (prof) sap_set_profiling(h, 1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == SAP_OK) {
+        std::lock_guard<std::mutex> g(g_mu);
+        load_locked();
+        save_locked(handle_tune_key(h), best);
+    }
+    return st;
+}
+
+} // namespace sap

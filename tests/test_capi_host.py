@@ -90,3 +90,12 @@ def test_python_wrapper_raises_without_device(lib):
     with pytest.raises(P.SapError) as e:
         P.Sap(np.zeros((4, 2), dtype=np.float32))
     assert e.value.name == "SAP_E_NO_DEVICE"
+
+
+def test_tuning_calls_validate_without_device(lib):
+    """The tuning entry points reject a NULL handle before any device work."""
+    t = capi.Tuning()
+    assert lib.sap_autotune(None, 0.01, 4, ctypes.byref(t)) == 1
+    assert lib.sap_get_tuning(None, ctypes.byref(t)) == 1
+    assert lib.sap_set_tuning(None, ctypes.byref(t)) == 1
+    assert lib.sap_set_pass_bound(None, 1e-3) == 1

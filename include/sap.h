@@ -336,6 +336,9 @@ typedef struct {
     int32_t explicit_blocks_per_sm; /* explicit-difference tier grid, 1..8 blocks per SM */
     int32_t update_blocks;          /* FP64 recheck + update grid, 0 (one per SM) .. 304 */
     int32_t plain_blocks_per_sm;    /* plain pass grid, 1..8 blocks per SM (FP64 data: twice) */
+    int32_t programmatic_launch;    /* 1: the kernels of an iteration are chained by programmatic
+                                       dependent launch (each starts early and waits where it
+                                       needs its predecessor's output); 0: ordinary launches */
     double us_per_iteration;        /* measured by sap_autotune; 0 when set by hand */
 } sap_tuning;
 

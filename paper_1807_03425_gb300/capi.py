@@ -50,7 +50,8 @@ class Stats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("pass_bound", ctypes.c_double), ("pass_stages", ctypes.c_int32),
                 ("explicit_blocks_per_sm", ctypes.c_int32), ("update_blocks", ctypes.c_int32),
-                ("plain_blocks_per_sm", ctypes.c_int32), ("us_per_iteration", ctypes.c_double)]
+                ("plain_blocks_per_sm", ctypes.c_int32), ("programmatic_launch", ctypes.c_int32),
+                ("us_per_iteration", ctypes.c_double)]
 
 
 def _tuning_dict(t):

@@ -271,6 +271,7 @@ sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only)
         u.partials = h->partials;
         u.grid = std::min(h->tune.su_blocks > 0 ? h->tune.su_blocks : h->sms, kRecheckBlocks);
         u.work = h->work; u.st = h->st; u.hist = h->hist; u.argmin = h->am; u.seed_cert = c32;
+        u.pdl = h->tune.pdl;
         Timed t(h, K_UPDATE);
         CK(launch_select_update(u, s));
     }
@@ -666,6 +667,7 @@ static void to_public(const TuneParams &p, sap_tuning *out)
     out->explicit_blocks_per_sm = p.expl_per_sm;
     out->update_blocks = p.su_blocks;
     out->plain_blocks_per_sm = p.plain_per_sm;
+    out->programmatic_launch = p.pdl;
     out->us_per_iteration = p.us_per_iter;
 }
 
@@ -685,7 +687,8 @@ sap_status sap_set_tuning(sap_handle h, const sap_tuning *in)
     FORWARD_BATCH(h, sap_set_tuning(kid, in));
     if (!(in->pass_bound >= 1e-6 && in->pass_bound <= 0.25) || in->pass_stages < 0 || in->pass_stages > 3 ||
         in->explicit_blocks_per_sm < 1 || in->explicit_blocks_per_sm > 8 || in->update_blocks < 0 ||
-        in->update_blocks > kRecheckBlocks || in->plain_blocks_per_sm < 1 || in->plain_blocks_per_sm > 8)
+        in->update_blocks > kRecheckBlocks || in->plain_blocks_per_sm < 1 || in->plain_blocks_per_sm > 8 ||
+        (in->programmatic_launch != 0 && in->programmatic_launch != 1))
         return fail(h, SAP_E_ARG, "tuning parameter out of range");
     CK(cudaStreamSynchronize(h->stream));
     TuneParams p;
@@ -694,6 +697,7 @@ sap_status sap_set_tuning(sap_handle h, const sap_tuning *in)
     p.expl_per_sm = in->explicit_blocks_per_sm;
     p.su_blocks = in->update_blocks;
     p.plain_per_sm = in->plain_blocks_per_sm;
+    p.pdl = in->programmatic_launch;
     p.us_per_iter = 0;
     return tune_apply(h, p);
 }

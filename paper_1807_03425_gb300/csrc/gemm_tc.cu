@@ -67,6 +67,11 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tbase = *tslot;
+    // Programmatic launch: the next kernel (the pass) may start now and
+    // prefetch its constant tiles; this product's operands and output belong
+    // to the previous kernel's iteration, so wait for it before touching them.
+    grid_dep_launch();
+    grid_dep_wait();
     const int m0 = blockIdx.x * GM;
     // this CTA's K slice
     const int kb0 = (int)(((long long)blockIdx.y * a.nkb) / a.ksplit);
@@ -194,8 +199,7 @@ cudaError_t launch_gemm_y(const GemmArgs &a, cudaStream_t s)
     if (ksplit > a.nkb) return cudaErrorInvalidValue;
     GemmArgs b = a;
     b.ksplit = ksplit;
-    gemm_y_kernel<<<dim3(a.Npad / GM, ksplit), 128, shm, s>>>(b);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(a.pdl != 0, gemm_y_kernel, dim3(a.Npad / GM, ksplit), dim3(128), shm, s, b);
     if (e != cudaSuccess || ksplit == 1) return e;
     const size_t count = (size_t)a.KY * a.Npad;
     ksum_kernel<<<(unsigned)std::min<size_t>((count + 255) / 256, 2048), 256, 0, s>>>(a.Ypart, ksplit, count,

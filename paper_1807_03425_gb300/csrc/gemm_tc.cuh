@@ -21,6 +21,7 @@ struct GemmArgs {
     ProbState *st;              // receives ST_TIMEOUT if a wait gives up
     int ksplit;                 // K slices (grid.y); > 1: raw slices go to Ypart
     float *Ypart;               // ksplit x KY x Npad FP32 (ksplit > 1)
+    int pdl;                    // programmatic launch (see sap_internal.cuh)
 };
 
 size_t gemm_smem_bytes(int KPG, int stages);

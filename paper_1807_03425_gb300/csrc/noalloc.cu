@@ -203,6 +203,7 @@ extern "C" sap_status sap_min_secant_noalloc(const float *X, int64_t N, int32_t 
     q.hist = g->hist;
     q.argmin = g->argmin;
     q.seed_cert = a.cert;
+    q.pdl = 0;
     if (launch_select_update(q, s) != cudaSuccess) return SAP_E_CUDA;
 
     ProbState st;

@@ -244,6 +244,7 @@ struct PassArgs {
     ProbState *st;
     int2 *cand;
     long long cap;
+    int pdl;
 };
 
 // One ring stage: the w tile, then for each side one 512-byte segment per
@@ -261,8 +262,11 @@ __device__ __forceinline__ float pair_bound(float beta, float nui, float nuj, fl
     return beta * (nui + nuj) * sqrtf(w) * 1.000002f;
 }
 
-// Persistent, warp-specialised pass: one block per SM walks the tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...  A producer warp keeps a ring of
+// Persistent, warp-specialised pass: one block per SM.  Each block's first
+// `stages` tiles are blockIdx.x + it * gridDim.x (their constant parts are
+// fetched before the previous kernel has finished); the remaining tiles
+// are handed out from a counter, so a block that starts late (its SM still
+// busy with the previous kernels) takes fewer.  A producer warp keeps a ring of
 // `stages` shared-memory buffers filled by 1-D TMA bulk copies (the 64 KB w
 // tile and, for each side, one 512-byte segment per component of Y^T); 16
 // consumer warps evaluate the tiles.  Full/empty mbarriers hand the buffers
@@ -300,7 +304,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     const int warp = tid >> 5, lane = tid & 31;
     const int KY = a.KY, S = a.stages;
     const uint32_t wbytes = T * T * 4, ybytes = T * KY * 4, sbytes = wbytes + 2 * ybytes + 2 * T * 4;
-    const int nmine = blockIdx.x < (unsigned)a.ntiles ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    // tiles below gridDim.x * S are static (it < S); the rest are dynamic
+    const int nall = blockIdx.x < (unsigned)a.ntiles ? (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    const int nstatic = nall < S ? nall : S;
     const long long budget = 4000000000ll;
 
     if (tid == 0) {
@@ -315,15 +321,64 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     if (warp == kConsumerWarps) {
         // ---------------- producer warp ----------------
         if (lane == 0) {
-            int issued = 0;
-            for (int it = 0; it < nmine; ++it) {
+            // The stored lengths and point norms are constant: the first
+            // stages' copies start before the product of this iteration has
+            // finished (programmatic launch); Y follows after the wait.
+            const int pre = nstatic;
+            for (int it = 0; it < pre; ++it) {
+                const int t = blockIdx.x + it * gridDim.x;
+                const int2 IJ = a.wtiles[t];
+                sIJ[it] = IJ;  // published by the mbarrier completion
+                unsigned char *base = sm + (size_t)it * sbytes;
+                tc::mbar_expect_tx(&full[it], sbytes);
+                tc::bulk_g2s(base, a.w + (size_t)t * T * T, wbytes, &full[it]);
+                tc::bulk_g2s(base + wbytes + 2 * ybytes, a.nu + (size_t)IJ.x * T, T * 4, &full[it]);
+                tc::bulk_g2s(base + wbytes + 2 * ybytes + T * 4, a.nu + (size_t)IJ.y * T, T * 4, &full[it]);
+            }
+            grid_dep_wait();
+            grid_dep_launch();
+            for (int it = 0; it < pre; ++it) {
+                const int2 IJ = sIJ[it];
+                unsigned char *base = sm + (size_t)it * sbytes;
+                for (int c = 0; c < KY; ++c) {
+                    tc::bulk_g2s(base + wbytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.x * T, T * 4,
+                                 &full[it]);
+                    tc::bulk_g2s(base + wbytes + ybytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.y * T,
+                                 T * 4, &full[it]);
+                }
+            }
+            int issued = pre;
+            bool marked = false;
+            // Tiles after the first `stages`: with programmatic launch they
+            // are claimed from a counter (some blocks start late); otherwise
+            // block b takes b + it * gridDim.x.  Either way the next tile and
+            // its coordinates are fetched one step ahead of their use.
+            const int t0 = gridDim.x * S;
+            auto next_tile = [&](int it) -> int {
+                if (a.pdl) return t0 < a.ntiles ? t0 + (int)atomicAdd(&a.st->tile_next, 1u) : a.ntiles;
+                return (int)blockIdx.x + it * (int)gridDim.x;
+            };
+            int tnext = next_tile(pre);
+            int2 IJnext = tnext < a.ntiles ? a.wtiles[tnext] : make_int2(-1, -1);
+            for (int it = pre;; ++it) {
                 const int s = it % S;
+                const int t = tnext;
+                const int2 IJ = IJnext;
+                if (t < a.ntiles) {
+                    tnext = next_tile(it + 1);
+                    IJnext = tnext < a.ntiles ? a.wtiles[tnext] : make_int2(-1, -1);
+                }
                 if (it >= S && !tc::mbar_wait_bounded(&empty[s], ((it / S) - 1) & 1, budget)) {
                     atomicOr(&a.st->status, ST_TIMEOUT);
                     break;
                 }
-                const int t = blockIdx.x + it * gridDim.x;
-                const int2 IJ = a.wtiles[t];
+                if (t >= a.ntiles) {
+                    // no tile left: an arrival without bytes tells the consumers
+                    sIJ[s] = make_int2(-1, -1);
+                    tc::mbar_arrive(&full[s]);
+                    marked = true;
+                    break;
+                }
                 sIJ[s] = IJ;  // published by the mbarrier completion below
                 unsigned char *base = sm + (size_t)s * sbytes;
                 tc::mbar_expect_tx(&full[s], sbytes);
@@ -339,25 +394,33 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 ++issued;
             }
             // no copy of ours may still be in flight when the block exits
+            // (the stage the end marker reused was consumed, so its copies
+            // have landed; its barrier is past that phase)
             for (int it = issued > S ? issued - S : 0; it < issued; ++it)
-                tc::mbar_wait_bounded(&full[it % S], (it / S) & 1, budget);
+                if (!(marked && it % S == issued % S)) tc::mbar_wait_bounded(&full[it % S], (it / S) & 1, budget);
+        } else {
+            grid_dep_wait();
+            grid_dep_launch();
         }
         return;
     }
 
     // ---------------- consumer warps ----------------
+    grid_dep_wait();  // Y, the bounds and the lists of this iteration
+    grid_dep_launch();
     const int seg = warp % SR, row0 = warp / SR;
     const int col0 = seg * 32 * CPT + lane * CPT;
     const float seed = load_pos_float(&a.st->seed_ub);
     float uwarp = INFINITY;  // best upper bound this warp has produced
-    for (int it = 0; it < nmine; ++it) {
+    for (int it = 0;; ++it) {
         const int s = it % S;
         if (!tc::mbar_wait_bounded(&full[s], (it / S) & 1, budget)) {
             if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
             break;
         }
-        const float gnow = load_pos_float(&a.st->run_ub1);  // consumed after the tile
         const int2 IJ = sIJ[s];
+        if (IJ.x < 0) break;  // the producer has no more tiles
+        const float gnow = load_pos_float(&a.st->run_ub1);  // consumed after the tile
         const float *ws = reinterpret_cast<const float *>(sm + (size_t)s * sbytes);
         const float *yI = ws + T * T;   // yI[c * T + a]: component c of point I*T + a
         const float *yJ = yI + T * KY;
@@ -526,6 +589,7 @@ struct ExplArgs {
     ProbState *st;
     int2 *cand2;
     long long cap2;
+    int pdl;
 };
 
 constexpr int EPW = 4;  // entries per warp per round
@@ -544,10 +608,23 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
     __shared__ int scan[33];
     __shared__ int base_sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned int c1 = (unsigned int)a.st->cnt1;
-    if (c1 > a.cap1) c1 = a.cap1;
-    const long long total = (long long)c1 + a.n_near;
+    // The near list is fixed and the basis and bounds are the previous
+    // iteration's (complete once this kernel runs): it is evaluated while the
+    // pass may still be running.  The pass's candidates follow its end.
+    // With programmatic launch the lists are two segments (the near list
+    // first, while the pass may still run; then, after the wait, the pass's
+    // candidates); otherwise one segment covering both.
     const float seed = load_pos_float(&a.st->seed_ub);
+    for (int seg = 0; seg < (a.pdl ? 2 : 1); ++seg) {
+    long long nn = a.n_near, total = a.n_near;
+    if (seg == 1 || !a.pdl) {
+        grid_dep_wait();
+        grid_dep_launch();
+        unsigned int c1 = *(volatile const unsigned int *)&a.st->cnt1;
+        if (c1 > a.cap1) c1 = a.cap1;
+        nn = a.pdl ? 0 : a.n_near;
+        total = nn + c1;
+    }
     for (long long base = (long long)blockIdx.x * 8 * EPW; base < total;
          base += (long long)gridDim.x * 8 * EPW) {
         int2 pr[EPW];
@@ -556,7 +633,7 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
         for (int e = 0; e < EPW; ++e) {
             const long long idx = base + warp * EPW + e;
             valid[e] = idx < total;
-            pr[e] = valid[e] ? (idx < c1 ? a.cand1[idx] : a.near[idx - c1]) : make_int2(0, 0);
+            pr[e] = valid[e] ? (idx < nn ? __ldcg(a.near + idx) : __ldcg(a.cand1 + (idx - nn))) : make_int2(0, 0);
         }
         float acc[EPW * (K + 1)];
 #pragma unroll
@@ -566,7 +643,7 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
             float u[KU];
 #pragma unroll
             for (int c = 0; c < KU; c += 4) {
-                const float4 t = *reinterpret_cast<const float4 *>(a.U32 + (size_t)l * a.KP + c);
+                const float4 t = __ldcg(reinterpret_cast<const float4 *>(a.U32 + (size_t)l * a.KP + c));
                 u[c] = t.x; u[c + 1] = t.y; u[c + 2] = t.z; u[c + 3] = t.w;
             }
 #pragma unroll
@@ -623,6 +700,7 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
         }
         __syncthreads();
     }
+    }
 }
 
 // ---- extended-precision explicit recheck (large n)
@@ -657,14 +735,22 @@ __global__ void __launch_bounds__(256) explicit_df_kernel(ExplArgs a)
     __shared__ int scan[33];
     __shared__ int base_sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned int c1 = (unsigned int)a.st->cnt1;
-    if (c1 > a.cap1) c1 = a.cap1;
-    const long long total = (long long)c1 + a.n_near;
+    // near list first (while the pass may still run), then the pass's candidates
     const float seed = load_pos_float(&a.st->seed_ub);
+    for (int seg = 0; seg < (a.pdl ? 2 : 1); ++seg) {
+    long long nn = a.n_near, total = a.n_near;
+    if (seg == 1 || !a.pdl) {
+        grid_dep_wait();
+        grid_dep_launch();
+        unsigned int c1 = *(volatile const unsigned int *)&a.st->cnt1;
+        if (c1 > a.cap1) c1 = a.cap1;
+        nn = a.pdl ? 0 : a.n_near;
+        total = nn + c1;
+    }
     for (long long base = (long long)blockIdx.x * 8; base < total; base += (long long)gridDim.x * 8) {
         const long long idx = base + warp;
         const bool valid = idx < total;
-        const int2 pr = valid ? (idx < c1 ? a.cand1[idx] : a.near[idx - c1]) : make_int2(0, 0);
+        const int2 pr = valid ? (idx < nn ? __ldcg(a.near + idx) : __ldcg(a.cand1 + (idx - nn))) : make_int2(0, 0);
         float zh[K + 1], zl[K + 1];
 #pragma unroll
         for (int q = 0; q <= K; ++q) zh[q] = zl[q] = 0.f;
@@ -675,7 +761,7 @@ __global__ void __launch_bounds__(256) explicit_df_kernel(ExplArgs a)
                 xs_fma(zh[K], zl[K], D, D, 0.f);
                 const float *uh = a.U32 + (size_t)l * a.KP, *ul = a.U32lo + (size_t)l * a.KP;
 #pragma unroll
-                for (int c = 0; c < K; ++c) xs_fma(zh[c], zl[c], D, uh[c], ul[c]);
+                for (int c = 0; c < K; ++c) xs_fma(zh[c], zl[c], D, __ldcg(uh + c), __ldcg(ul + c));
             }
         }
 #pragma unroll
@@ -719,16 +805,14 @@ __global__ void __launch_bounds__(256) explicit_df_kernel(ExplArgs a)
         }
         __syncthreads();
     }
+    }
 }
 
 template <int K>
 cudaError_t launch_expl_k(const ExplArgs &x, bool df, int grid, cudaStream_t s)
 {
-    if (df)
-        explicit_df_kernel<K><<<grid, 256, 0, s>>>(x);
-    else
-        explicit_recheck_kernel<K><<<grid, 256, 0, s>>>(x);
-    return cudaGetLastError();
+    if (df) return launch_pdl(x.pdl != 0, explicit_df_kernel<K>, dim3(grid), dim3(256), 0, s, x);
+    return launch_pdl(x.pdl != 0, explicit_recheck_kernel<K>, dim3(grid), dim3(256), 0, s, x);
 }
 
 cudaError_t launch_explicit(const ExplArgs &x, bool df, int grid, cudaStream_t s)
@@ -913,8 +997,8 @@ int pass_pick_stages(int KY)
 template <int K, int CPT>
 cudaError_t launch_pass_k(const PassArgs &a, int grid, cudaStream_t s)
 {
-    restr_pass_kernel<K, CPT><<<grid, kPassThreads, pass_smem_bytes(a.KY, a.stages), s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(a.pdl != 0, restr_pass_kernel<K, CPT>, dim3(grid), dim3(kPassThreads),
+                      pass_smem_bytes(a.KY, a.stages), s, a);
 }
 
 template <int K, int CPT>
@@ -1081,6 +1165,7 @@ GemmArgs product_args(sap_handle h, const RestrState &r)
     g.lo_scale = g.ab_bf16 ? 1.0f / 256.f : 1.0f / 2048.f;
     g.out_scale = 1.0f / r.xscale;
     g.ksplit = r.ksplit;
+    g.pdl = handle_tune(h).pdl;
     return g;
 }
 
@@ -1127,6 +1212,7 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         p.st = b.st;
         p.cand = b.cand1;
         p.cap = b.cap;
+        p.pdl = handle_tune(h).pdl;
         handle_count_launch(h, 1, &ea, &eb);
         if (ea) cudaEventRecord(ea, s);
         RCK(launch_pass(p, b.k, std::min(r.nwtiles, handle_sms(h)), s));
@@ -1151,6 +1237,7 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         x.st = b.st;
         x.cand2 = b.cand2;
         x.cap2 = b.cap;
+        x.pdl = handle_tune(h).pdl;
         handle_count_launch(h, 3, &ea, &eb);
         if (ea) cudaEventRecord(ea, s);
         RCK(launch_explicit(x, df, std::max(1, handle_tune(h).expl_per_sm) * handle_sms(h), s));

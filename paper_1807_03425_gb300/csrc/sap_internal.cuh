@@ -22,6 +22,43 @@
 
 namespace sap {
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl may start
+// while the kernel before it in the stream is still running; it must call
+// grid_dep_wait() before it touches anything that kernel (or an earlier
+// one) writes, and everything it reads before that point must be constant
+// over the run (the points, the stored lengths, the near list).  A kernel
+// calls grid_dep_launch() once its dependents may start: every kernel of an
+// iteration calls it only after its own grid_dep_wait(), except where noted,
+// so that a kernel running past its wait implies that the whole previous
+// iteration has completed.
+__device__ __forceinline__ void grid_dep_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch with programmatic stream serialization when `pdl` is set (else an
+// ordinary launch: the griddepcontrol instructions are then no-ops).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
+
 constexpr int kMaxK = 32;          // largest target dimension
 constexpr int kWatch = 8;          // recent argmin pairs re-evaluated as seeds
 constexpr int kTile = 128;         // edge of a w tile (restructured form)
@@ -51,6 +88,7 @@ struct TuneParams {
     int expl_per_sm = 2;     // explicit-difference tier: blocks per SM
     int su_blocks = 0;       // FP64 recheck + update: blocks (0: one per SM)
     int plain_per_sm = 2;    // plain pass: blocks per SM (FP64 data: twice as many)
+    int pdl = 0;             // programmatic dependent launch between the kernels of an iteration
     double us_per_iter = 0;  // measured by the tuner (0: not tuned)
 };
 
@@ -71,6 +109,9 @@ struct ProbState {
     int2 watch[kWatch];
     double last_r;          // result of the latest evaluation
     int last_i, last_j;
+    // dynamic tiles handed out by the restructured pass; on a cache line of
+    // its own, away from the bounds every warp of the pass polls
+    alignas(128) unsigned int tile_next;
 };
 
 // Best pair of one recheck block (FP64).
@@ -249,6 +290,7 @@ struct SelectUpdateArgs {
     double *hist;          // hist_cap entries
     int2 *argmin;          // hist_cap entries
     Cert seed_cert;        // error model of the seed evaluation
+    int pdl;               // launch with programmatic stream serialization
 };
 cudaError_t launch_select_update(const SelectUpdateArgs &a, cudaStream_t s);
 

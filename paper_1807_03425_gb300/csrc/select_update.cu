@@ -44,7 +44,7 @@ namespace {
 
 constexpr int SB = 256;          // threads per block
 constexpr int NW = SB / 32;
-constexpr size_t kDynSmem = 24 * 1024;  // U' kept in shared memory up to this size
+constexpr size_t kDynSmem = 40 * 1024;  // dynamic part of phase 2 (static part < 8 KB: total within 48 KB)
 constexpr int kSeedRegs = 4;     // watch-pair coordinates prefetched per lane (n <= 128)
 
 template <typename TX>
@@ -84,6 +84,84 @@ __device__ __forceinline__ void block_sum_multi(V (&v)[M], V *scratch /* NW*M */
     __syncthreads();
 }
 
+// Reduce-scatter of S per-lane values (S a power of two, 8..32) over a warp:
+// halving exchanges (each level adds half of the remaining values), then
+// butterfly adds; S - 1 + log2(32/S) additions instead of 5 per value.  On
+// return v[0] of lane L holds the warp total of entry rs_index<S>(L).
+template <int S>
+__device__ __forceinline__ int rs_index(int lane)
+{
+    constexpr int b = S == 8 ? 3 : S == 16 ? 4 : 5;
+    return (lane >> (5 - b)) & (S - 1);
+}
+
+template <int S>
+__device__ __forceinline__ double warp_reduce_scatter(double (&v)[S], int lane)
+{
+    static_assert(S == 8 || S == 16 || S == 32, "reduce-scatter width");
+#pragma unroll
+    for (int lvl = 0; (S >> lvl) > 1; ++lvl) {
+        const int half = (S >> lvl) / 2, o = 16 >> lvl;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const double send = up ? v[i] : v[i + half];
+            const double keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 / S; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    return v[0];
+}
+
+// d2 = |D|^2 and zz = |U^T D|^2 from per-lane partial sums v[0..K-1] (U^T D)
+// and v[K] (|D|^2), delivered to every lane.
+template <int K>
+__device__ __forceinline__ void warp_ratio_parts(double (&v)[K + 1], int lane, double &zz, double &d2)
+{
+    constexpr int M = K + 1;
+    if constexpr (M <= 32) {
+        constexpr int S = M <= 8 ? 8 : M <= 16 ? 16 : 32;
+        constexpr int dup = 32 / S;  // lanes holding the same entry
+        double r[S];
+#pragma unroll
+        for (int q = 0; q < S; ++q) r[q] = q < M ? v[q < M ? q : 0] : 0.0;
+        const double t = warp_reduce_scatter<S>(r, lane);
+        const int idx = rs_index<S>(lane);
+        double sq = (idx < K && lane % dup == 0) ? t * t : 0.0;
+#pragma unroll
+        for (int o = 16; o >= dup; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        zz = __shfl_sync(0xffffffffu, sq, 0);
+        d2 = __shfl_sync(0xffffffffu, t, K * dup);
+    } else {
+        warp_sum_multi<double, K + 1>(v);
+        d2 = v[K];
+        zz = 0.0;
+#pragma unroll
+        for (int c = 0; c < K; ++c) zz = fma(v[c], v[c], zz);
+    }
+}
+
+// (q, i, j) ordering for q >= 0 (no NaN): the bit patterns of non-negative
+// doubles order like their values, so the compare stays off the FP64 pipe.
+__device__ __forceinline__ bool better_q(double q, int i, int j, double qb, int ib, int jb)
+{
+    const unsigned long long a = (unsigned long long)__double_as_longlong(q);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(qb);
+    if (a != b) return a < b;
+    if (i != ib) return i < ib;
+    return j < jb;
+}
+
+// Dynamic shared memory of phase 2 when the basis fits: U' (FP64), D (data
+// precision, padded to 8 bytes) and the FP32 final basis.
+template <typename TX>
+__host__ __device__ inline size_t su_dyn_bytes(int n, int K)
+{
+    return (size_t)n * K * 8 + ((size_t)n * sizeof(TX) + 7) / 8 * 8 + (size_t)n * K * 4;
+}
+
 template <typename WT, int K>
 struct Shared {
     double red_d[NW * (K + 1)];
@@ -98,7 +176,12 @@ struct Shared {
     WT Bw[K][K];                   // coefficient MGS result, column m = q_m
     WT av, asd, dnorm, nd2;        // direction coefficients, |D|, |dir|^2
     double G[K][K];                // Gram matrix (upper), then R (upper)
-    double T1[K][K], T2[K][K];     // series terms
+    double T1[K][K], T2[K][K];     // series terms (K > 8) 
+    static constexpr int KS = K <= 8 ? K : 1;
+    static constexpr int GW = K * (K + 1) / 2 <= 32 ? NW : 1;
+    float S1f[KS][KS];             // first-order term in FP32 (series, K <= 8)
+    double gred[GW][32];           // per-warp Gram partials (reduce-scatter, K <= 7)
+    float emaxw;
     double Ri[K][K];               // (I + R)^-1 (upper)
     double Rd[K];                  // 1 / R_jj (direct path)
     float seed[NW];
@@ -113,6 +196,12 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
     const int n = a.n;
     const int kk = a.k;            // actual k (<= K)
     ProbState *st = a.st;
+
+    // Programmatic launch: the next iteration's product may start its
+    // prologue (it waits for this kernel before reading the basis); this
+    // kernel's inputs are the explicit tier's list, so wait for it.
+    grid_dep_launch();
+    grid_dep_wait();
 
     // ---------------- phase 1: FP64 recheck of the candidate list ----------
     {
@@ -133,21 +222,18 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
                 for (int c = 0; c < K; ++c)
                     if (c < kk) v[c] = fma(a.U64[(size_t)c * n + l], D, v[c]);
             }
-            warp_sum_multi<double, K + 1>(v);
-            const double d2 = v[K];
+            double zz, d2;
+            warp_ratio_parts<K>(v, lane, zz, d2);
             if (d2 == 0.0 || d2 < a.eps2) continue;
-            double zz = 0.0;
-#pragma unroll
-            for (int c = 0; c < K; ++c) zz = fma(v[c], v[c], zz);
             const double q = zz / d2;  // squared ratio
-            if (better(q, ij.x, ij.y, best.r, best.i, best.j)) best = Partial{q, ij.x, ij.y};
+            if (better_q(q, ij.x, ij.y, best.r, best.i, best.j)) best = Partial{q, ij.x, ij.y};
         }
         if (lane == 0) sh.wb[w] = best;
         __syncthreads();
         if (tid == 0) {
             Partial b = sh.wb[0];
             for (int q = 1; q < NW; ++q)
-                if (better(sh.wb[q].r, sh.wb[q].i, sh.wb[q].j, b.r, b.i, b.j)) b = sh.wb[q];
+                if (better_q(sh.wb[q].r, sh.wb[q].i, sh.wb[q].j, b.r, b.i, b.j)) b = sh.wb[q];
             a.partials[blockIdx.x] = b;
             __threadfence();
             const unsigned int t = atomicAdd(&st->ticket, 1u);
@@ -165,7 +251,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         for (int p = lane; p < (int)gridDim.x; p += 32) {
             const volatile Partial *vp = &a.partials[p];
             const Partial q = {vp->r, vp->i, vp->j};
-            if (better(q.r, q.i, q.j, b.r, b.i, b.j)) b = q;
+            if (better_q(q.r, q.i, q.j, b.r, b.i, b.j)) b = q;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -173,7 +259,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             q.r = __shfl_xor_sync(0xffffffffu, b.r, o);
             q.i = __shfl_xor_sync(0xffffffffu, b.i, o);
             q.j = __shfl_xor_sync(0xffffffffu, b.j, o);
-            if (better(q.r, q.i, q.j, b.r, b.i, b.j)) b = q;
+            if (better_q(q.r, q.i, q.j, b.r, b.i, b.j)) b = q;
         }
         if (lane == 0) sh.wb[0] = b;
     } else if (w == 1) {
@@ -206,6 +292,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         st->last_cnt1 = sh.cnt1;
         st->last_cnt2 = sh.cnt2;
         st->cnt1 = 0;
+        st->tile_next = 0;
         st->cnt2 = 0;
         st->ticket = 0;
         st->run_ub1 = 0x7f800000u;
@@ -244,9 +331,11 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         }
     }
 
-    const bool in_smem = K <= 8 && (size_t)n * K * sizeof(double) <= kDynSmem;
+    const bool in_smem = K <= 8 && su_dyn_bytes<TX>(n, K) <= kDynSmem;
     double *Up = in_smem ? dyn : a.work;           // n x K: the new basis before QR
     WT *Ds = reinterpret_cast<WT *>(Up + (size_t)n * K);  // n
+    // FP32 copy of the final basis (n x K) for the seeds, when in shared memory
+    float *Uf = in_smem ? reinterpret_cast<float *>(dyn + (size_t)n * K + ((size_t)n * sizeof(WT) + 7) / 8) : nullptr;
 
     // 2. D = x_i - x_j, |D|^2 and U^T D in one multi-value reduction
     {
@@ -384,15 +473,54 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         __syncthreads();
     }
 
-    // 5. FP64 Gram matrix of U' (upper triangle), entries spread over the warps
+    // 5. FP64 Gram matrix of U' (upper triangle)
+    if constexpr (K * (K + 1) / 2 <= 32) {
+        // every thread sums the products of its rows; one reduce-scatter per
+        // warp; the warps' partials are added in shared memory
+        constexpr int M = K * (K + 1) / 2;
+        constexpr int S = M <= 8 ? 8 : M <= 16 ? 16 : 32;
+        constexpr int dup = 32 / S;
+        const int nrw = (min(n, SB) + 31) >> 5;  // warps holding rows
+        if (w < nrw) {
+            double g[S];
+#pragma unroll
+            for (int e = 0; e < S; ++e) g[e] = 0.0;
 #pragma unroll 1
-    for (int e = w; e < kk * kk; e += NW) {
-        const int p = e / kk, q = e % kk;
-        if (q < p) continue;
-        double s = 0.0;
-        for (int l = lane; l < n; l += 32) s = fma(Up[(size_t)l * K + p], Up[(size_t)l * K + q], s);
-        s = warp_sum(s);
-        if (lane == 0) sh.G[p][q] = s;
+            for (int l = tid; l < n; l += SB) {
+                double row[K];
+#pragma unroll
+                for (int m = 0; m < K; ++m) row[m] = m < kk ? Up[(size_t)l * K + m] : 0.0;
+                int e = 0;
+#pragma unroll
+                for (int p = 0; p < K; ++p)
+#pragma unroll
+                    for (int q = p; q < K; ++q) {
+                        g[e] = fma(row[p], row[q], g[e]);
+                        ++e;
+                    }
+            }
+            const double t = warp_reduce_scatter<S>(g, lane);
+            if (lane % dup == 0) sh.gred[w][rs_index<S>(lane)] = t;
+        }
+        __syncthreads();
+        if (tid < M) {
+            int p = 0, e = tid;
+            while (e >= K - p) { e -= K - p; ++p; }
+            double sum = 0.0;
+            for (int q = 0; q < nrw; ++q) sum += sh.gred[q][tid];
+            sh.G[p][p + e] = sum;
+        }
+    } else {
+        // entries spread over the warps
+#pragma unroll 1
+        for (int e = w; e < kk * kk; e += NW) {
+            const int p = e / kk, q = e % kk;
+            if (q < p) continue;
+            double s = 0.0;
+            for (int l = lane; l < n; l += 32) s = fma(Up[(size_t)l * K + p], Up[(size_t)l * K + q], s);
+            s = warp_sum(s);
+            if (lane == 0) sh.G[p][q] = s;
+        }
     }
     __syncthreads();
     if (w == 0) {
@@ -404,7 +532,32 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-        if (emax <= 1e-6) {
+        if (Shared<TX, K>::KS == K && emax <= 1e-6) {
+            // S1 = triu(E) with the diagonal halved (FP64), S2 = the same of
+            // -S1^T S1, R = S1 + S2, and (I + R)^-1 = I - S1 + [S1^2 - S2] +
+            // O(|E|^3).  The bracket is second order (<= k^2 1e-12): its FP32
+            // evaluation from FP32(S1) errs by ~1e-19, below FP64 rounding of
+            // the unit diagonal, so each lane forms its entries independently.
+            for (int e = lane; e < kk * kk; e += 32) {
+                const int p = e / kk, q = e % kk;
+                const double v = q > p ? sh.G[p][q] : (q == p ? 0.5 * (sh.G[p][p] - 1.0) : 0.0);
+                sh.T1[p][q] = v;
+                sh.S1f[p][q] = (float)v;
+            }
+            __syncwarp();
+            for (int e = lane; e < kk * kk; e += 32) {
+                const int p = e / kk, q = e % kk;
+                if (q < p) {
+                    sh.Ri[p][q] = 0.0;
+                    continue;
+                }
+                float sq = 0.f, tt = 0.f;
+                for (int m = p; m <= q; ++m) sq = fmaf(sh.S1f[p][m], sh.S1f[m][q], sq);  // (S1^2)_pq
+                for (int m = 0; m <= p; ++m) tt = fmaf(sh.S1f[m][p], sh.S1f[m][q], tt);  // (S1^T S1)_pq
+                const float second = sq + (q > p ? tt : 0.5f * tt);                      // S1^2 - S2
+                sh.Ri[p][q] = (p == q ? 1.0 : 0.0) - sh.T1[p][q] + (double)second;
+            }
+        } else if (emax <= 1e-6) {
             // R1 = triu(E) with the diagonal halved; R2 from -R1^T R1 the same
             // way; R = R1 + R2; (I + R)^-1 = I - R + R^2 (error O(|E|^3))
             for (int e = lane; e < kk * kk; e += 32) {
@@ -477,6 +630,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             a.U64[(size_t)m * n + l] = s;
             const float sf = (float)s;
             a.U32[(size_t)l * a.KP + m] = sf;
+            if (Uf) Uf[(size_t)l * K + m] = sf;
             if (a.U32lo) a.U32lo[(size_t)l * a.KP + m] = (float)(s - (double)sf);
             if (a.Uhi) {
                 // hi + lo * 2^-s of the FP32 value (the FP32 rounding adds 2^-24
@@ -528,7 +682,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
                     if (l < n) {
                         const float D = wxi[q] - wxj[q];
                         v[K] = fmaf(D, D, v[K]);
-                        const float *ur = a.U32 + (size_t)l * a.KP;
+                        const float *ur = Uf ? Uf + (size_t)l * K : a.U32 + (size_t)l * a.KP;
 #pragma unroll
                         for (int c = 0; c < K; ++c)
                             if (c < kk) v[c] = fmaf(ur[c], D, v[c]);
@@ -538,7 +692,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
                 for (int l = lane; l < n; l += 32) {
                     const float D = (float)ld_x<TX>(a.X, (size_t)pr.x * n + l) - (float)ld_x<TX>(a.X, (size_t)pr.y * n + l);
                     v[K] = fmaf(D, D, v[K]);
-                    const float *ur = a.U32 + (size_t)l * a.KP;
+                    const float *ur = Uf ? Uf + (size_t)l * K : a.U32 + (size_t)l * a.KP;
 #pragma unroll
                     for (int c = 0; c < K; ++c)
                         if (c < kk) v[c] = fmaf(ur[c], D, v[c]);
@@ -563,10 +717,9 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
 template <typename TX, int K>
 cudaError_t launch_su(const SelectUpdateArgs &a, cudaStream_t s)
 {
-    const size_t need = (size_t)a.n * K * sizeof(double) + (size_t)a.n * sizeof(TX);
-    const size_t shm = (K <= 8 && (size_t)a.n * K * sizeof(double) <= kDynSmem) ? need : 0;
-    select_update_kernel<TX, K><<<a.grid, SB, shm, s>>>(a);
-    return cudaGetLastError();
+    const size_t need = su_dyn_bytes<TX>(a.n, K);
+    const size_t shm = (K <= 8 && need <= kDynSmem) ? need : 0;
+    return launch_pdl(a.pdl != 0, select_update_kernel<TX, K>, dim3(a.grid), dim3(SB), shm, s, a);
 }
 
 template <typename TX>

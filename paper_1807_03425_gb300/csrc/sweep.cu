@@ -178,6 +178,7 @@ SelectUpdateArgs update_args(sap_handle h, SweepState &sw, SweepBasis &b, double
     u.hist = b.hist;
     u.argmin = b.am;
     u.seed_cert = handle_seed_cert(u.n, b.k);
+    u.pdl = handle_tune(h).pdl;
     return u;
 }
 

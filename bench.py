@@ -289,7 +289,7 @@ def run_native(args):
     sap.set_profiling(True)
     sap.run(alpha, Kk, history=False)
     kt = {name: sap.kernel_time(name) for name in
-          ("gemm_y", "restructured_pass", "explicit_recheck", "update")}
+          ("gemm_y", "ydf", "restructured_pass", "refine", "update")}
     sap.set_profiling(False)
     splain.set_basis(U0)
     splain.set_profiling(True)
@@ -506,7 +506,7 @@ def run_sweep(args):
     # kernel classes, launched one by one (the bases' chains still overlap)
     s.set_profiling(True)
     s.estimate_dim(U0, 16, alpha, thr)
-    kt = {name: _kernel_ms(s, name) for name in ("gemm_y", "restructured_pass", "explicit_recheck", "update")}
+    kt = {name: _kernel_ms(s, name) for name in ("gemm_y", "ydf", "restructured_pass", "refine", "update")}
     s.set_profiling(False)
     its = K
     it_s = its / (ms * 1e-3)

@@ -316,9 +316,9 @@ sap_status sap_run_batch(sap_handle h, double alpha, int32_t iters, double *hist
  * Cap of the per-pair error bound of the restructured pass (restructured
  * form of Sec. IV's argmin step, FP32/BF16 data).  The tensor-core Y gives
  * each pair's ratio a certified error b_ij = sqrt(k) eps_Y (|x_i - xbar| +
- * |x_j - xbar|) / d_ij; pairs with b_ij above the cap are re-evaluated from
- * explicit differences every iteration (the near list), the others are
- * filtered in the pass with their own b_ij.  A larger cap gives a shorter
+ * |x_j - xbar|) / d_ij; pairs with b_ij above the cap are skipped by the
+ * pass and re-evaluated every iteration by the second tier (the near list),
+ * the others are filtered in the pass with their own b_ij.  A larger cap gives a shorter
  * near list and a wider coarse filter; results do not depend on it.
  * Default 5e-4; 1e-6 <= b_cap <= 0.25, else SAP_E_ARG.  sap_autotune may
  * change it.  On a batch handle, every dataset.
@@ -333,12 +333,15 @@ sap_status sap_set_pass_bound(sap_handle h, double b_cap);
 typedef struct {
     double pass_bound;              /* cap of the restructured pass's per-pair bound (sap_set_pass_bound) */
     int32_t pass_stages;            /* TMA ring depth of the restructured pass: 2 or 3; 0 = as many as fit */
-    int32_t explicit_blocks_per_sm; /* explicit-difference tier grid, 1..8 blocks per SM */
+    int32_t explicit_blocks_per_sm; /* second-tier grid (candidates and near pairs), 1..8 blocks per SM */
     int32_t update_blocks;          /* FP64 recheck + update grid, 0 (one per SM) .. 304 */
     int32_t plain_blocks_per_sm;    /* plain pass grid, 1..8 blocks per SM (FP64 data: twice) */
     int32_t programmatic_launch;    /* 1: the kernels of an iteration are chained by programmatic
                                        dependent launch (each starts early and waits where it
                                        needs its predecessor's output); 0: ordinary launches */
+    int32_t refine_tier;            /* second tier of the restructured form: 1 double-float Y
+                                       (O(k) per pair), 0 explicit differences (O(n k) per pair),
+                                       -1 chosen by n (double-float above n = 256) */
     double us_per_iteration;        /* measured by sap_autotune; 0 when set by hand */
 } sap_tuning;
 
@@ -374,9 +377,10 @@ sap_status sap_get_stats(sap_handle h, sap_stats *out);
  * Kernel timing for measurement: while enabled, sap_step and sap_run launch
  * kernels one by one (no graph) with CUDA events around each launch on the
  * handle's stream; sap_get_kernel_time returns the accumulated device time
- * (ms) and launch count of one kernel class.  Classes: 0 Y = XU product,
- * 1 restructured all-pairs pass, 2 plain all-pairs pass, 3 explicit-difference
- * recheck, 5 FP64 recheck fused with the update (4 is unused), 6 soft-min
+ * (ms) and launch count of one kernel class.  Classes: 0 Y = XU product
+ * (tensor cores), 1 restructured all-pairs pass, 2 plain all-pairs pass,
+ * 3 second tier (explicit differences or the double-float refine),
+ * 4 double-float Y = XU, 5 FP64 recheck fused with the update, 6 soft-min
  * forward pass, 7 soft-min backward pass, 8 soft-min near pairs, 9 soft-min
  * other kernels (Y, gradient sums, ascent step).  Enabling resets the
  * accumulators.

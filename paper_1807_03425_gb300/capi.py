@@ -22,7 +22,7 @@ PLAIN, RESTRUCTURED = 0, 1
 UPDATE_LITERAL, UPDATE_ANGLE = 0, 1
 SPLIT_FP16, SPLIT_BF16 = 0, 1
 KERNEL_CLASSES = {"gemm_y": 0, "restructured_pass": 1, "plain_pass": 2,
-                  "explicit_recheck": 3, "select_update": 5, "update": 5,
+                  "second_tier": 3, "refine": 3, "explicit_recheck": 3, "ydf": 4, "select_update": 5, "update": 5,
                   "softmin_forward": 6, "softmin_backward": 7, "softmin_near": 8,
                   "softmin_other": 9}
 
@@ -51,7 +51,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("pass_bound", ctypes.c_double), ("pass_stages", ctypes.c_int32),
                 ("explicit_blocks_per_sm", ctypes.c_int32), ("update_blocks", ctypes.c_int32),
                 ("plain_blocks_per_sm", ctypes.c_int32), ("programmatic_launch", ctypes.c_int32),
-                ("us_per_iteration", ctypes.c_double)]
+                ("refine_tier", ctypes.c_int32), ("us_per_iteration", ctypes.c_double)]
 
 
 def _tuning_dict(t):

@@ -668,6 +668,7 @@ static void to_public(const TuneParams &p, sap_tuning *out)
     out->update_blocks = p.su_blocks;
     out->plain_blocks_per_sm = p.plain_per_sm;
     out->programmatic_launch = p.pdl;
+    out->refine_tier = p.refine;
     out->us_per_iteration = p.us_per_iter;
 }
 
@@ -688,7 +689,8 @@ sap_status sap_set_tuning(sap_handle h, const sap_tuning *in)
     if (!(in->pass_bound >= 1e-6 && in->pass_bound <= 0.25) || in->pass_stages < 0 || in->pass_stages > 3 ||
         in->explicit_blocks_per_sm < 1 || in->explicit_blocks_per_sm > 8 || in->update_blocks < 0 ||
         in->update_blocks > kRecheckBlocks || in->plain_blocks_per_sm < 1 || in->plain_blocks_per_sm > 8 ||
-        (in->programmatic_launch != 0 && in->programmatic_launch != 1))
+        (in->programmatic_launch != 0 && in->programmatic_launch != 1) || in->refine_tier < -1 ||
+        in->refine_tier > 1)
         return fail(h, SAP_E_ARG, "tuning parameter out of range");
     CK(cudaStreamSynchronize(h->stream));
     TuneParams p;
@@ -698,6 +700,7 @@ sap_status sap_set_tuning(sap_handle h, const sap_tuning *in)
     p.su_blocks = in->update_blocks;
     p.plain_per_sm = in->plain_blocks_per_sm;
     p.pdl = in->programmatic_launch;
+    p.refine = in->refine_tier;
     p.us_per_iter = 0;
     return tune_apply(h, p);
 }

@@ -106,6 +106,22 @@ __global__ void rownorm_kernel(const float *X, int N, int n, const float *center
     if (lane == 0) nu[row] = row < N ? __double2float_ru(sqrt(acc)) * (1.0f + 1e-6f) : 0.f;
 }
 
+// ||x_i|| of the points as given (not centred), rounded up; 0 for pad rows.
+__global__ void xnorm_kernel(const float *X, int N, int n, float *xn, int Npad)
+{
+    const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= Npad) return;
+    double acc = 0.0;
+    if (row < N)
+        for (int l = lane; l < n; l += 32) {
+            const double v = (double)X[(size_t)row * n + l];
+            acc = fma(v, v, acc);
+        }
+    acc = warp_sum(acc);
+    if (lane == 0) xn[row] = row < N ? __double2float_ru(sqrt(acc)) * (1.0f + 1e-6f) : 0.f;
+}
+
 struct WPrepArgs {
     const float *X;
     int N, n;
@@ -117,6 +133,7 @@ struct WPrepArgs {
     float beta_coef;         // sqrt(k) * eps_Y, rounded up
     float b_cap;
     int2 *near;
+    float *near_w;           // 1/d^2 of each near pair (+inf below FP32 range)
     unsigned int near_cap;
     unsigned int *counters;  // [0] near count, [1] excluded count (low), [2] status
 };
@@ -211,14 +228,19 @@ __global__ void __launch_bounds__(256) wprep_kernel(WPrepArgs a)
     __syncthreads();
     if (total > 0) {
         unsigned int pos = (unsigned int)base_sh + off;
-        for (int b = 0; b < 64; ++b)
-            if (near_bits >> b & 1ull) {
-                if (pos < a.near_cap)
-                    a.near[pos] = make_int2(i0 + ty * 8 + b / 8, j0 + tx * 8 + b % 8);
-                else
-                    atomicOr(&a.counters[2], 1u);
-                ++pos;
-            }
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (near_bits >> (p * 8 + q) & 1ull) {
+                    if (pos < a.near_cap) {
+                        a.near[pos] = make_int2(i0 + ty * 8 + p, j0 + tx * 8 + q);
+                        a.near_w[pos] = d2[p][q] < 1e-30f ? INFINITY : 1.0f / d2[p][q];
+                    } else {
+                        atomicOr(&a.counters[2], 1u);
+                    }
+                    ++pos;
+                }
     }
     int ex_total;
     block_exclusive_scan(nexcl, scan, &ex_total);
@@ -834,6 +856,282 @@ cudaError_t launch_explicit(const ExplArgs &x, bool df, int grid, cudaStream_t s
     return launch_expl_k<32>(x, df, grid, s);
 }
 
+// ------------------------------------------ the double-float refine tier ---
+//
+// Y is formed a second time per iteration in double-float arithmetic: every
+// entry an unevaluated sum hi + lo of two FP32 numbers, from the exact FP32
+// points (not centred: centring in FP32 would round the differences this
+// tier exists to resolve) and the basis split as U32 + U32lo.  Each step is
+// an error-free product x * uh (FMA residual), an error-free sum into hi, the
+// small terms added to lo, and a renormalisation (|lo| <= ulp(hi)/2), so a
+// step adds at most 9 * 2^-48 * S to the error, S = sum_l |x_l||u_l| <=
+// ||x|| (u a unit vector); the split residual of u adds 2^-48 S and the five
+// five lane merges 20 * 2^-48 S.  Hence |y~_c - y_c| <= eps_df ||x_i|| with
+// eps_df = 1.25 (9n + 60) 2^-48 (about 4e-12 at n = 100).
+//
+// The refine tier evaluates every candidate of the pass and every near pair
+// from these rows, one thread per pair, O(k) work: z_c = (yh_i - yh_j) +
+// (yl_i - yl_j) (relative FP32 roundings only), r~ = |z| sqrt(w_ij) with the
+// stored 1/d^2 (near pairs keep theirs in near_w).  Certified error
+// |r~ - r| <= A_p + rho r, A_p = sqrt(k) (eps_df + 2^-46)(||x_i|| + ||x_j||)
+// sqrt(w_ij): at least a thousand times below the pass's bound, and below the
+// FP32 rounding of explicit differences x_i - x_j.  Emission as in every
+// tier: r~_p <= U (1 + rho) + A_p against the running upper bound U.
+
+double df_error_unit(int n)
+{
+    return 1.25 * (9.0 * n + 60.0) * std::ldexp(1.0, -48);
+}
+
+__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) += x * (uh + ul), then renormalised.  The _rn intrinsics keep the
+// compiler from fusing the error-free steps into FMAs.
+__device__ __forceinline__ void df_step(float &hi, float &lo, float x, float uh, float ul)
+{
+    const float p = __fmul_rn(x, uh);
+    const float pe = fmaf(x, uh, -p);
+    float s, e;
+    df_two_sum(hi, p, s, e);
+    const float l = __fadd_rn(lo, __fadd_rn(e, fmaf(x, ul, pe)));
+    hi = __fadd_rn(s, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, s));
+}
+struct YdfArgs {
+    const float *X;          // N x n row-major FP32
+    int N, n;
+    const float *U32, *U32lo;  // n x KP: hi and lo parts of the basis
+    int KP;
+    int Npad;
+    float *Yh, *Yl;          // KY x Npad each, component-major; rows >= N zero
+    int KY;
+};
+
+__device__ __forceinline__ void df_merge_norm(float &hi, float &lo, float h2, float l2)
+{
+    float s, e;
+    df_two_sum(hi, h2, s, e);
+    const float l = __fadd_rn(lo, __fadd_rn(l2, e));
+    hi = __fadd_rn(s, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, s));
+}
+
+// A block of 16 warps computes 32 rows at a time, two per warp; the lanes of
+// a warp split the coordinates (l = lane, lane + 32, ...), and their partial
+// sums are merged by a 5-level shuffle tree at the end (within the error
+// allowance above).  The basis goes through shared memory in chunks of CH
+// coordinates, component-major (lanes read consecutive words), each chunk
+// serving all 32 rows.  K = compute width (U32's pad columns are zero).
+constexpr int kYdfWarps = 16;
+constexpr int kYdfRpw = 2;
+
+template <int K>
+struct YdfShape {
+    static constexpr int CH = K <= 8 ? 256 : 128;
+};
+
+template <int K>
+__global__ void __launch_bounds__(kYdfWarps * 32) ydf_warp_kernel(YdfArgs a)
+{
+    constexpr int CH = YdfShape<K>::CH;
+    __shared__ float us[2 * K][CH];  // [c][l] hi, [K + c][l] lo
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nchunks = (a.n + CH - 1) / CH;
+    for (int rbase = blockIdx.x * (kYdfWarps * kYdfRpw); rbase < a.Npad;
+         rbase += gridDim.x * (kYdfWarps * kYdfRpw)) {
+        float hi[kYdfRpw][K], lo[kYdfRpw][K];
+#pragma unroll
+        for (int q = 0; q < kYdfRpw; ++q)
+#pragma unroll
+            for (int c = 0; c < K; ++c) hi[q][c] = lo[q][c] = 0.f;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int c0 = ch * CH, nc = min(CH, a.n - c0);
+            if (nchunks > 1 || rbase == blockIdx.x * (kYdfWarps * kYdfRpw)) {
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < K * CH; idx += kYdfWarps * 32) {
+                    const int c = idx / CH, l = idx % CH;
+                    const bool in = l < nc;
+                    us[c][l] = in ? a.U32[(size_t)(c0 + l) * a.KP + c] : 0.f;
+                    us[K + c][l] = in ? a.U32lo[(size_t)(c0 + l) * a.KP + c] : 0.f;
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int q = 0; q < kYdfRpw; ++q) {
+                const int row = rbase + warp * kYdfRpw + q;
+                if (row >= a.N) continue;
+                const float *xr = a.X + (size_t)row * a.n + c0;
+#pragma unroll 2
+                for (int l = lane; l < nc; l += 32) {
+                    const float x = xr[l];
+#pragma unroll
+                    for (int c = 0; c < K; ++c) df_step(hi[q][c], lo[q][c], x, us[c][l], us[K + c][l]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kYdfRpw; ++q) {
+            const int row = rbase + warp * kYdfRpw + q;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    const float h2 = __shfl_xor_sync(0xffffffffu, hi[q][c], o);
+                    const float l2 = __shfl_xor_sync(0xffffffffu, lo[q][c], o);
+                    df_merge_norm(hi[q][c], lo[q][c], h2, l2);
+                }
+            if (row < a.Npad)
+#pragma unroll
+                for (int c = 0; c < K; ++c)
+                    if (lane == c % 32 && c < a.KY) {
+                        a.Yh[(size_t)c * a.Npad + row] = hi[q][c];
+                        a.Yl[(size_t)c * a.Npad + row] = lo[q][c];
+                    }
+        }
+    }
+}
+
+struct RefineArgs {
+    const float *Yh, *Yl;    // double-float Y, KY x Npad each
+    int Npad;
+    const float *w;          // stored 1/d^2, tile-major upper triangle
+    int nb;                  // point blocks per side (Npad / 128)
+    const float *xn;         // ||x_i||, rounded up
+    float beta;              // sqrt(k) (eps_df + 2^-46), rounded up
+    const int2 *cand1;
+    unsigned int cap1;
+    const int2 *near;
+    const float *near_w;     // 1/d^2 of the near pairs (+inf: too short for FP32)
+    int n_near;
+    Cert cert;               // rho (A unused: each pair has its own bound)
+    ProbState *st;
+    int2 *cand2;
+    long long cap2;
+    int pdl;
+};
+
+// One thread per pair; K = compute width (Y's pad components are zero).
+// Warps aggregate their bound and their emissions (one atomic each).
+template <int K>
+__global__ void __launch_bounds__(256) refine_kernel(RefineArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const float seed = load_pos_float(&a.st->seed_ub);
+    const float rho = a.cert.rho;
+    // With programmatic launch the near list is evaluated first (it needs
+    // only the previous iteration's results), the pass's candidates after
+    // the wait; otherwise one range covers both.
+    for (int seg = 0; seg < (a.pdl ? 2 : 1); ++seg) {
+        long long nn = a.n_near, total = a.n_near;
+        if (seg == 1 || !a.pdl) {
+            grid_dep_wait();
+            grid_dep_launch();
+            unsigned int c1 = *(volatile const unsigned int *)&a.st->cnt1;
+            if (c1 > a.cap1) c1 = a.cap1;
+            nn = a.pdl ? 0 : a.n_near;
+            total = nn + c1;
+        }
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        // rounds are warp-uniform: every lane of a warp runs the same count
+        for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+             base += stride) {
+            const long long idx = base + lane;
+            const float Uround = fminf(seed, load_pos_float(&a.st->run_ub2));  // issued early
+            int code = 0;  // 0 none, 1 evaluated, 2 too short for FP32 (always emitted)
+            int2 pr = make_int2(0, 0);
+            float r = INFINITY, bnd = 0.f;
+            if (idx < total) {
+                float wv;
+                if (idx < nn) {
+                    pr = __ldcg(a.near + idx);
+                    wv = __ldcg(a.near_w + idx);
+                } else {
+                    pr = __ldcg(a.cand1 + (idx - nn));
+                    const int I = pr.x >> 7, J = pr.y >> 7;
+                    const long long t = (long long)I * a.nb - (long long)I * (I - 1) / 2 + (J - I);
+                    wv = __ldg(a.w + t * (T * T) + (pr.x & (T - 1)) * T + (pr.y & (T - 1)));
+                }
+                if (!(wv < INFINITY)) {
+                    code = 2;
+                } else {
+                    float zz = 0.f;
+#pragma unroll
+                    for (int c = 0; c < K; ++c) {
+                        const size_t oi = (size_t)c * a.Npad + pr.x, oj = (size_t)c * a.Npad + pr.y;
+                        const float z = __fadd_rn(__fsub_rn(__ldcg(a.Yh + oi), __ldcg(a.Yh + oj)),
+                                                  __fsub_rn(__ldcg(a.Yl + oi), __ldcg(a.Yl + oj)));
+                        zz = fmaf(z, z, zz);
+                    }
+                    const float sw = sqrtf(wv);
+                    r = sqrtf(zz * wv);
+                    bnd = a.beta * (__ldg(a.xn + pr.x) + __ldg(a.xn + pr.y)) * sw * 1.000002f;
+                    code = 1;
+                }
+            }
+            // the warp's best upper bound tightens the running bound
+            const float ub = code == 1 ? (r + bnd) / (1.0f - rho) * 1.000001f : INFINITY;
+            const float wub = warp_min(ub);
+            float U = Uround;
+            if (wub < U) {
+                if (lane == 0) atomic_min_pos_float(&a.st->run_ub2, wub);
+                U = wub;
+            }
+            const bool emit = code == 2 || (code == 1 && r <= (U * (1.0f + rho) + bnd) * 1.000001f);
+            const unsigned m = __ballot_sync(0xffffffffu, emit);
+            if (m) {
+                unsigned int b = 0;
+                if (lane == 0) b = atomicAdd((unsigned int *)&a.st->cnt2, (unsigned int)__popc(m));
+                b = __shfl_sync(0xffffffffu, b, 0);
+                if (emit) {
+                    const long long pos = (long long)b + __popc(m & ((1u << lane) - 1u));
+                    if (pos < a.cap2) a.cand2[pos] = pr;
+                    else atomicOr(&a.st->status, ST_OVERFLOW);
+                }
+            }
+        }
+    }
+}
+
+template <int K>
+cudaError_t launch_ydf_refine_k(const YdfArgs &y, const RefineArgs &x, int ygrid, int rgrid, bool ydf,
+                                cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (ydf) {
+        const int need = (y.Npad + kYdfWarps * kYdfRpw - 1) / (kYdfWarps * kYdfRpw);
+        ydf_warp_kernel<K><<<std::min(need, ygrid), kYdfWarps * 32, 0, s>>>(y);
+        e = cudaGetLastError();
+    } else {
+        e = launch_pdl(x.pdl != 0, refine_kernel<K>, dim3(rgrid), dim3(256), 0, s, x);
+    }
+    return e;
+}
+
+// The double-float product (ydf = true) or the refine tier, for width k.
+cudaError_t launch_ydf_refine(const YdfArgs &y, const RefineArgs &x, int k, int ygrid, int rgrid, bool ydf,
+                              cudaStream_t s)
+{
+    switch (k) {
+    case 1: return launch_ydf_refine_k<1>(y, x, ygrid, rgrid, ydf, s);
+    case 2: return launch_ydf_refine_k<2>(y, x, ygrid, rgrid, ydf, s);
+    case 3: return launch_ydf_refine_k<3>(y, x, ygrid, rgrid, ydf, s);
+    case 4: return launch_ydf_refine_k<4>(y, x, ygrid, rgrid, ydf, s);
+    case 5: return launch_ydf_refine_k<5>(y, x, ygrid, rgrid, ydf, s);
+    case 6: return launch_ydf_refine_k<6>(y, x, ygrid, rgrid, ydf, s);
+    case 7: return launch_ydf_refine_k<7>(y, x, ygrid, rgrid, ydf, s);
+    case 8: return launch_ydf_refine_k<8>(y, x, ygrid, rgrid, ydf, s);
+    default: break;
+    }
+    if (k <= 12) return launch_ydf_refine_k<12>(y, x, ygrid, rgrid, ydf, s);
+    if (k <= 16) return launch_ydf_refine_k<16>(y, x, ygrid, rgrid, ydf, s);
+    if (k <= 24) return launch_ydf_refine_k<24>(y, x, ygrid, rgrid, ydf, s);
+    return launch_ydf_refine_k<32>(y, x, ygrid, rgrid, ydf, s);
+}
+
 // -------------------------------------------------------------- host side --
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -950,6 +1248,19 @@ Cert cert_explicit(int n, int k)
     return c;
 }
 
+// Refine tier: relative errors only besides each pair's own bound (the
+// rounding of the stored length, the FP32 differences, squares and sum of
+// the k components, the product with w and the square root).
+Cert cert_refine(int n, int k)
+{
+    const double u = std::ldexp(1.0, -24);
+    auto g = [&](double m) { return m * u / (1.0 - m * u); };
+    Cert c;
+    c.A = 0.f;
+    c.rho = (float)((g(n + 2) + g(k + 2) + 8 * u) * 1.05);
+    return c;
+}
+
 sap_status classify(sap_handle h, int k)
 {
     RestrState &r = restr_state(h);
@@ -969,6 +1280,7 @@ sap_status classify(sap_handle h, int k)
     a.beta_coef = (float)(std::sqrt((double)k) * r.y_eps * 1.02);
     a.b_cap = (float)r.b_cap;
     a.near = r.near;
+    a.near_w = r.near_w;
     a.near_cap = r.near_cap;
     a.counters = r.counters;
     wprep_kernel<<<r.nwtiles, 256, 0, s>>>(a);
@@ -1064,8 +1376,10 @@ sap_status restructured_prepare(sap_handle h)
         RCK(cudaMemcpy(r.wtiles, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice));
         RCK(cudaMalloc(&r.w, (size_t)r.nwtiles * T * T * sizeof(float)));
         const long long P = (long long)N * (N - 1) / 2;
-        r.near_cap = (unsigned int)std::min<long long>(P + 64, 1ll << 26);
+        r.near_cap = (unsigned int)std::min<long long>(P + 64, 1ll << 24);
         RCK(cudaMalloc(&r.near, (size_t)r.near_cap * sizeof(int2)));
+        RCK(cudaMalloc(&r.near_w, (size_t)r.near_cap * sizeof(float)));
+        RCK(cudaMalloc(&r.xn, r.Npad * sizeof(float)));
         RCK(gemm_configure());
         RCK(configure_pass_kernels());
     }
@@ -1093,6 +1407,8 @@ sap_status restructured_prepare(sap_handle h)
                                                      (__half *)r.Xlo, r.Npad, r.NP);
     RCK(cudaGetLastError());
     rownorm_kernel<<<(r.Npad + 7) / 8, 256, 0, s>>>(X, N, n, r.center, r.nu, r.Npad);
+    RCK(cudaGetLastError());
+    xnorm_kernel<<<(r.Npad + 7) / 8, 256, 0, s>>>(X, N, n, r.xn, r.Npad);
     RCK(cudaGetLastError());
     r.ksplit = pick_ksplit(r.NP / 64);
     r.y_eps = y_error_unit(r.NP, bf16, r.ksplit);
@@ -1127,6 +1443,12 @@ sap_status restructured_basis_alloc(sap_handle h)
     RCK(cudaMalloc(&r.Ulo, (size_t)r.KPG * r.NP * 2));
     RCK(cudaMalloc(&r.Y, (size_t)r.Npad * r.KY * sizeof(float)));
     RCK(cudaMemset(r.Y, 0, (size_t)r.Npad * r.KY * sizeof(float)));
+    dfree(r.Ydh);
+    dfree(r.Ydl);
+    RCK(cudaMalloc(&r.Ydh, (size_t)r.Npad * r.KY * sizeof(float)));
+    RCK(cudaMalloc(&r.Ydl, (size_t)r.Npad * r.KY * sizeof(float)));
+    RCK(cudaMemset(r.Ydh, 0, (size_t)r.Npad * r.KY * sizeof(float)));
+    RCK(cudaMemset(r.Ydl, 0, (size_t)r.Npad * r.KY * sizeof(float)));
     dfree(r.Ypart);
     if (r.ksplit > 1) RCK(cudaMalloc(&r.Ypart, (size_t)r.ksplit * r.Npad * r.KY * sizeof(float)));
     if (!make_map(&r.gemm.tb_hi, r.Uhi, bf16, r.NP, r.KPG, r.KPG) ||
@@ -1219,7 +1541,7 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         if (eb) cudaEventRecord(eb, s);
         handle_push_timing(h, 1, ea, eb);
     }
-    {
+    if (!restructured_uses_refine(h)) {
         ExplArgs x;
         x.X = handle_x32(h);
         x.N = (int)handle_n_points(h);
@@ -1243,6 +1565,48 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         RCK(launch_explicit(x, df, std::max(1, handle_tune(h).expl_per_sm) * handle_sms(h), s));
         if (eb) cudaEventRecord(eb, s);
         handle_push_timing(h, 3, ea, eb);
+    } else {
+        // double-float Y of this basis, then the refine tier
+        YdfArgs y;
+        y.X = handle_x32(h);
+        y.N = (int)handle_n_points(h);
+        y.n = n;
+        y.U32 = b.U32;
+        y.U32lo = b.U32lo;
+        y.KP = b.KP;
+        y.Npad = r.Npad;
+        y.Yh = b.Ydh;
+        y.Yl = b.Ydl;
+        y.KY = b.KY;
+        RefineArgs x;
+        x.Yh = b.Ydh;
+        x.Yl = b.Ydl;
+        x.Npad = r.Npad;
+        x.w = r.w;
+        x.nb = r.Npad / T;
+        x.xn = r.xn;
+        x.beta = (float)(std::sqrt((double)b.k) * (df_error_unit(n) + std::ldexp(1.0, -46)) * 1.02);
+        x.cand1 = b.cand1;
+        x.cap1 = (unsigned int)b.cap;
+        x.near = r.near;
+        x.near_w = r.near_w;
+        x.n_near = r.n_near;
+        x.cert = cert_refine(n, b.k);
+        x.st = b.st;
+        x.cand2 = b.cand2;
+        x.cap2 = b.cap;
+        x.pdl = handle_tune(h).pdl;
+        const int sms = handle_sms(h);
+        handle_count_launch(h, 4, &ea, &eb);
+        if (ea) cudaEventRecord(ea, s);
+        RCK(launch_ydf_refine(y, x, b.k, 2 * sms, 0, true, s));
+        if (eb) cudaEventRecord(eb, s);
+        handle_push_timing(h, 4, ea, eb);
+        handle_count_launch(h, 3, &ea, &eb);
+        if (ea) cudaEventRecord(ea, s);
+        RCK(launch_ydf_refine(y, x, b.k, 0, std::max(1, handle_tune(h).expl_per_sm) * sms, false, s));
+        if (eb) cudaEventRecord(eb, s);
+        handle_push_timing(h, 3, ea, eb);
     }
     return SAP_OK;
 }
@@ -1262,6 +1626,8 @@ sap_status restructured_enqueue(sap_handle h, double alpha)
     b.U32 = handle_u32(h);
     b.U32lo = handle_u32lo(h);
     b.Y = r.Y;
+    b.Ydh = r.Ydh;
+    b.Ydl = r.Ydl;
     b.st = handle_state(h);
     b.cand1 = handle_cand1(h);
     b.cand2 = handle_cand2(h);
@@ -1341,10 +1707,16 @@ sap_status restructured_project(sap_handle h, float *Y_out, int out_is_device)
     return SAP_OK;
 }
 
+bool restructured_uses_refine(sap_handle h)
+{
+    const int t = handle_tune(h).refine;
+    return t < 0 ? handle_n_dim(h) > 256 : t != 0;
+}
+
 int restructured_kernels_per_iteration(sap_handle h)
 {
-    (void)h;
-    return 3;
+    // product (+ slice sum), pass, explicit tier or (double-float product + refine tier)
+    return 3 + (restructured_uses_refine(h) ? 1 : 0) + (restr_state(h).ksplit > 1 ? 1 : 0);
 }
 
 void restructured_free(sap_handle h)
@@ -1352,6 +1724,7 @@ void restructured_free(sap_handle h)
     RestrState &r = restr_state(h);
     dfree(r.Xhi); dfree(r.Xlo); dfree(r.center); dfree(r.nu); dfree(r.w); dfree(r.wtiles);
     dfree(r.near); dfree(r.counters); dfree(r.Uhi); dfree(r.Ulo); dfree(r.Y); dfree(r.Ypart);
+    dfree(r.near_w); dfree(r.xn); dfree(r.Ydh); dfree(r.Ydl);
 }
 
 void restructured_stats(sap_handle h, sap_stats *out)

@@ -22,8 +22,10 @@ struct RestrState {
     float *w = nullptr;
     int2 *wtiles = nullptr;   // (I, J) per tile, I <= J
     int nwtiles = 0;
-    int2 *near = nullptr;     // pairs re-evaluated from explicit differences
+    int2 *near = nullptr;     // pairs the pass skips, evaluated by the refine tier
+    float *near_w = nullptr;  // their 1/d^2 (FP32; +inf when too short for FP32)
     unsigned int near_cap = 0;
+    float *xn = nullptr;      // ||x_i|| (not centred), rounded up (Npad)
     unsigned int *counters = nullptr;  // [0] near count, [1..2] excluded (u64)
     int n_near = 0;
     long long n_excluded = 0;
@@ -34,6 +36,7 @@ struct RestrState {
     void *Uhi = nullptr, *Ulo = nullptr;  // KPG x NP 16-bit
     int KPG = 0;              // k rounded up to the MMA N granule (16)
     float *Y = nullptr;       // Npad x KY
+    float *Ydh = nullptr, *Ydl = nullptr;  // double-float Y of the refine tier, KY x Npad each
     int KY = 0;               // k rounded up to 4
     int ksplit = 1;           // K slices of the product (shorter accumulation chains)
     float *Ypart = nullptr;   // ksplit x KY x Npad slice results (ksplit > 1)
@@ -71,6 +74,7 @@ struct BasisView {
     int k, KP, KY;            // width, FP32 basis stride, Y stride (components)
     const float *U32, *U32lo; // n x KP FP32 basis and its low part
     float *Y;                 // KY x Npad, component-major
+    float *Ydh, *Ydl;         // double-float Y (refine tier), KY x Npad each
     ProbState *st;
     int2 *cand1, *cand2;      // candidate lists of the pass and of the explicit tier
     long long cap;            // capacity of each list
@@ -88,6 +92,7 @@ sap_status restructured_basis_alloc(sap_handle h);      // U operands and Y for 
 sap_status restructured_upload_basis(sap_handle h, const double *U); // n x k col-major
 sap_status restructured_enqueue(sap_handle h, double alpha);
 int restructured_kernels_per_iteration(sap_handle h);
+bool restructured_uses_refine(sap_handle h);  // second tier: double-float refine (else explicit differences)
 void restructured_free(sap_handle h);
 void restructured_stats(sap_handle h, sap_stats *out);
 sap_status restructured_set_bound(sap_handle h, double b_cap);

@@ -89,6 +89,7 @@ struct TuneParams {
     int su_blocks = 0;       // FP64 recheck + update: blocks (0: one per SM)
     int plain_per_sm = 2;    // plain pass: blocks per SM (FP64 data: twice as many)
     int pdl = 0;             // programmatic dependent launch between the kernels of an iteration
+    int refine = -1;         // second tier: 1 double-float refine, 0 explicit differences, -1 by n (> 256: refine)
     double us_per_iter = 0;  // measured by the tuner (0: not tuned)
 };
 

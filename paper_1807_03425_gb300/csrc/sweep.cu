@@ -96,6 +96,10 @@ sap_status alloc_impl(sap_handle h, SweepState *&swp, int kmax, int hist_need)
         b.off = off;
         off += b.KY;
         WCK(cudaMalloc(&b.U64, (size_t)n * b.k * sizeof(double)));
+        WCK(cudaMalloc(&b.Ydh, (size_t)b.KY * r.Npad * sizeof(float)));
+        WCK(cudaMalloc(&b.Ydl, (size_t)b.KY * r.Npad * sizeof(float)));
+        WCK(cudaMemset(b.Ydh, 0, (size_t)b.KY * r.Npad * sizeof(float)));
+        WCK(cudaMemset(b.Ydl, 0, (size_t)b.KY * r.Npad * sizeof(float)));
         WCK(cudaMalloc(&b.U32, (size_t)n * b.KP * sizeof(float)));
         WCK(cudaMalloc(&b.U32lo, (size_t)n * b.KP * sizeof(float)));
         WCK(cudaMalloc(&b.work, (size_t)(kMaxK + 1) * n * sizeof(double)));
@@ -199,6 +203,8 @@ sap_status enqueue_iteration(sap_handle h, SweepState &sw, double alpha, int eva
         v.U32 = b.U32;
         v.U32lo = b.U32lo;
         v.Y = sw.Y + (size_t)b.off * r.Npad;
+        v.Ydh = b.Ydh;
+        v.Ydl = b.Ydl;
         v.st = b.st;
         v.cand1 = b.cand1;
         v.cand2 = b.cand2;
@@ -367,7 +373,7 @@ void sweep_free(SweepState *&s)
     for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
     s->graphs.clear();
     for (SweepBasis &b : s->b) {
-        wfree(b.U64); wfree(b.U32); wfree(b.U32lo); wfree(b.work); wfree(b.st);
+        wfree(b.U64); wfree(b.U32); wfree(b.U32lo); wfree(b.work); wfree(b.st); wfree(b.Ydh); wfree(b.Ydl);
         wfree(b.cand1); wfree(b.cand2); wfree(b.partials); wfree(b.hist); wfree(b.am);
         if (b.stream) cudaStreamDestroy(b.stream);
         if (b.done) cudaEventDestroy(b.done);

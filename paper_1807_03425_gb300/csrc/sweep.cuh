@@ -13,6 +13,7 @@ namespace sap {
 struct SweepBasis {
     int k = 0, KP = 0, KY = 0, off = 0;  // width, FP32 stride, Y stride, first component in the sweep's Y
     double *U64 = nullptr;               // n x k column-major
+    float *Ydh = nullptr, *Ydl = nullptr;  // double-float Y of the refine tier, KY x Npad
     float *U32 = nullptr, *U32lo = nullptr;
     double *work = nullptr;
     ProbState *st = nullptr;

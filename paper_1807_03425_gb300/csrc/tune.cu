@@ -4,8 +4,10 @@
 // per-pair error bound (which pairs go on the near list and which are
 // filtered by their own bound), the depth of the pass's TMA ring, the grid
 // sizes of the explicit-difference tier, of the FP64 recheck + update and of
-// the plain pass, and whether the kernels of an iteration are chained by
-// programmatic dependent launch.  None of them changes a result: each choice
+// the plain pass, whether the kernels of an iteration are chained by
+// programmatic dependent launch, and which second tier filters the pass's
+// candidates and the near pairs (explicit differences or the double-float
+// refine tier).  None of them changes a result: each choice
 // evaluates certified candidate sets and takes the same FP64 decisions, so
 // tuning only moves time.
 //
@@ -50,8 +52,8 @@ const char *cache_file()
     return (p && *p) ? p : nullptr;
 }
 
-// One line per entry: "sap-tune 2 N n k dt path split eps_bits b_cap stages
-// expl_per_sm su_blocks plain_per_sm pdl us_per_iter".
+// One line per entry: "sap-tune 3 N n k dt path split eps_bits b_cap stages
+// expl_per_sm su_blocks plain_per_sm pdl refine us_per_iter".
 void load_locked()
 {
     if (g_loaded) return;
@@ -65,10 +67,10 @@ void load_locked()
         TuneKey k;
         TuneParams p;
         int ver = 0;
-        if (std::sscanf(line, "sap-tune %d %lld %d %d %d %d %d %llx %lf %d %d %d %d %d %lf", &ver, &k.N, &k.n,
+        if (std::sscanf(line, "sap-tune %d %lld %d %d %d %d %d %llx %lf %d %d %d %d %d %d %lf", &ver, &k.N, &k.n,
                         &k.k, &k.dt, &k.path, &k.split, &k.eps_bits, &p.b_cap, &p.pass_stages, &p.expl_per_sm,
-                        &p.su_blocks, &p.plain_per_sm, &p.pdl, &p.us_per_iter) == 15 &&
-            ver == 2 && p.b_cap >= 1e-6 && p.b_cap <= 0.25 && p.expl_per_sm >= 1 && p.expl_per_sm <= 8 &&
+                        &p.su_blocks, &p.plain_per_sm, &p.pdl, &p.refine, &p.us_per_iter) == 16 &&
+            ver == 3 && p.refine >= -1 && p.refine <= 1 && p.b_cap >= 1e-6 && p.b_cap <= 0.25 && p.expl_per_sm >= 1 && p.expl_per_sm <= 8 &&
             p.plain_per_sm >= 1 && p.plain_per_sm <= 8 && p.su_blocks >= 0 && p.su_blocks <= kRecheckBlocks &&
             p.pass_stages >= 0 && p.pass_stages <= 3 && (p.pdl == 0 || p.pdl == 1))
             g_cache[k] = p;
@@ -83,16 +85,17 @@ void save_locked(const TuneKey &k, const TuneParams &p)
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "sap-tune 2 %lld %d %d %d %d %d %llx %.9g %d %d %d %d %d %.6g\n", k.N, k.n, k.k, k.dt, k.path,
-                 k.split, k.eps_bits, p.b_cap, p.pass_stages, p.expl_per_sm, p.su_blocks, p.plain_per_sm, p.pdl,
-                 p.us_per_iter);
+    std::fprintf(f, "sap-tune 3 %lld %d %d %d %d %d %llx %.9g %d %d %d %d %d %d %.6g\n", k.N, k.n, k.k, k.dt,
+                 k.path, k.split, k.eps_bits, p.b_cap, p.pass_stages, p.expl_per_sm, p.su_blocks, p.plain_per_sm,
+                 p.pdl, p.refine, p.us_per_iter);
     std::fclose(f);
 }
 
 bool same_launch(const TuneParams &a, const TuneParams &b)
 {
     return a.b_cap == b.b_cap && a.pass_stages == b.pass_stages && a.expl_per_sm == b.expl_per_sm &&
-           a.su_blocks == b.su_blocks && a.plain_per_sm == b.plain_per_sm && a.pdl == b.pdl;
+           a.su_blocks == b.su_blocks && a.plain_per_sm == b.plain_per_sm && a.pdl == b.pdl &&
+           a.refine == b.refine;
 }
 
 } // namespace
@@ -185,6 +188,11 @@ sap_status tune_handle(sap_handle h, double alpha, int iters)
     };
     const bool restr = handle_path_restructured(h);
     if (restr) {
+        for (int rf : {0, 1}) {
+            TuneParams c = best;
+            c.refine = rf;
+            consider(c);
+        }
         for (int pdl : {0, 1}) {
             TuneParams c = best;
             c.pdl = pdl;

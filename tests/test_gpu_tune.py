@@ -37,11 +37,13 @@ def trajectory(s, U0, alpha, T):
 
 EXTREMES = [
     dict(pass_bound=0.05, pass_stages=2, explicit_blocks_per_sm=1, update_blocks=38, plain_blocks_per_sm=1,
-         programmatic_launch=1),
+         programmatic_launch=1, refine_tier=1),
     dict(pass_bound=1e-4, pass_stages=3, explicit_blocks_per_sm=4, update_blocks=304, plain_blocks_per_sm=4,
-         programmatic_launch=0),
+         programmatic_launch=0, refine_tier=0),
     dict(pass_bound=2e-3, pass_stages=0, explicit_blocks_per_sm=2, update_blocks=0, plain_blocks_per_sm=2,
-         programmatic_launch=1),
+         programmatic_launch=1, refine_tier=-1),
+    dict(pass_bound=4e-3, pass_stages=0, explicit_blocks_per_sm=1, update_blocks=76, plain_blocks_per_sm=2,
+         programmatic_launch=0, refine_tier=1),
 ]
 
 
@@ -135,10 +137,10 @@ def test_tuning_cache_file_across_processes(P, tmp_path):
     code = CHILD % {"root": ROOT}
     a = json.loads(subprocess.run([sys.executable, "-c", code, "tune"], env=env, check=True,
                                   capture_output=True, text=True).stdout)
-    assert path.exists() and path.read_text().startswith("sap-tune 2 900 20 3 ")
+    assert path.exists() and path.read_text().startswith("sap-tune 3 900 20 3 ")
     b = json.loads(subprocess.run([sys.executable, "-c", code, "load"], env=env, check=True,
                                   capture_output=True, text=True).stdout)
     launch = ("pass_bound", "pass_stages", "explicit_blocks_per_sm", "update_blocks", "plain_blocks_per_sm",
-              "programmatic_launch")
+              "programmatic_launch", "refine_tier")
     assert {k: b["before"][k] for k in launch} == {k: a["after"][k] for k in launch}
     assert b["before"]["us_per_iteration"] > 0

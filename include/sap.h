@@ -97,6 +97,7 @@ typedef struct {
     int64_t kernel_launches; /* kernels launched since create (graph nodes count) */
     double cert_bound;       /* absolute ratio bound of the restructured pass */
     double y_error_unit;     /* bound on |y~ - y| per unit ||x - mean|| */
+    double ydf_error_unit;   /* bound on |(yh + yl) - y| per unit ||x|| (sap_project_df) */
 } sap_stats;
 
 /* Library version string. */
@@ -223,6 +224,17 @@ sap_status sap_get_sweep_basis(sap_handle h, int32_t k, double *U_out, int out_i
  * FP32/BF16 datasets only.  Synchronises.
  */
 sap_status sap_project(sap_handle h, float *Y_out, int out_is_device);
+
+/*
+ * The projected data in extended precision: Yh_out[i*k + c] + Yl_out[i*k + c]
+ * (two FP32 numbers per entry, N x k row-major each) = <x_i, u_c> for the
+ * points as given (not centred), within sap_stats.ydf_error_unit * ||x_i||
+ * (about 1.25 (9n + 60) 2^-48: error-free products and renormalised sums
+ * of the FP32 points and the FP64 basis).  This is the Y the double-float
+ * second tier of the restructured form evaluates pairs from.  FP32/BF16
+ * datasets only.  Synchronises.
+ */
+sap_status sap_project_df(sap_handle h, float *Yh_out, float *Yl_out, int out_is_device);
 
 /*
  * The argmin step without any device allocation, for callers that cannot

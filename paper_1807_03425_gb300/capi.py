@@ -44,7 +44,7 @@ class Stats(ctypes.Structure):
                 ("n_excluded", ctypes.c_int64), ("n_near", ctypes.c_int64),
                 ("last_tier1", ctypes.c_int64), ("last_tier2", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("cert_bound", ctypes.c_double),
-                ("y_error_unit", ctypes.c_double)]
+                ("y_error_unit", ctypes.c_double), ("ydf_error_unit", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -109,6 +109,7 @@ def load_library():
         "sap_softmin_backward": ([vp, f64, f64, vp, i32], i32),
         "sap_softmin_ascent": ([vp, f64, f64, i32, vp], i32),
         "sap_set_pass_bound": ([vp, f64], i32),
+        "sap_project_df": ([vp, vp, vp, i32], i32),
         "sap_autotune": ([vp, f64, i32, ctypes.POINTER(Tuning)], i32),
         "sap_get_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
         "sap_set_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
@@ -322,6 +323,17 @@ def sap_project(h, out):
     return out
 
 
+def sap_project_df(h, out_hi, out_lo):
+    """Extended-precision projection (hi + lo FP32 pairs, N x k each)."""
+    lib = load_library()
+    if hasattr(out_hi, "data_ptr"):
+        _check(h, lib.sap_project_df(h, ctypes.c_void_p(out_hi.data_ptr()), ctypes.c_void_p(out_lo.data_ptr()), 1))
+    else:
+        _check(h, lib.sap_project_df(h, out_hi.ctypes.data_as(ctypes.c_void_p),
+                                     out_lo.ctypes.data_as(ctypes.c_void_p), 0))
+    return out_hi, out_lo
+
+
 def sap_min_secant_noalloc(X, U, eps=0.0, stream=None):
     """Allocation-free argmin for callers that must not allocate device
     memory: X (N, n) float32 and U (k, n) float64 torch CUDA tensors; returns
@@ -526,6 +538,11 @@ class Sap:
 
     def sweep_basis(self, k):
         return sap_get_sweep_basis(self.h, k, self.n)
+
+    def project_df(self):
+        hi = np.empty((self.N, self.k), dtype=np.float32)
+        lo = np.empty((self.N, self.k), dtype=np.float32)
+        return sap_project_df(self.h, hi, lo)
 
     def project(self, out=None):
         if out is None:

@@ -937,6 +937,18 @@ sap_status sap_project(sap_handle h, float *Y_out, int out_is_device)
     return sync_and_status(h);
 }
 
+sap_status sap_project_df(sap_handle h, float *Yh_out, float *Yl_out, int out_is_device)
+{
+    CHECK_HANDLE(h);
+    NOT_BATCH(h);
+    if (!Yh_out || !Yl_out) return fail(h, SAP_E_ARG, "null output");
+    if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
+    if (h->dt == SAP_F64) return fail(h, SAP_E_UNSUPPORTED, "FP32 or BF16 data only");
+    sap_status s = restructured_project_df(h, Yh_out, Yl_out, out_is_device);
+    if (s != SAP_OK) return s;
+    return sync_and_status(h);
+}
+
 sap_status sap_get_stats(sap_handle h, sap_stats *out)
 {
     if (!h || !out) return SAP_E_ARG;
@@ -959,6 +971,7 @@ sap_status sap_get_stats(sap_handle h, sap_stats *out)
             out->last_tier2 = ks.last_tier2;
             out->cert_bound = ks.cert_bound;
             out->y_error_unit = std::max(out->y_error_unit, ks.y_error_unit);
+            out->ydf_error_unit = std::max(out->ydf_error_unit, ks.ydf_error_unit);
         }
         return SAP_OK;
     }

@@ -1707,6 +1707,42 @@ sap_status restructured_project(sap_handle h, float *Y_out, int out_is_device)
     return SAP_OK;
 }
 
+sap_status restructured_project_df(sap_handle h, float *Yh_out, float *Yl_out, int out_is_device)
+{
+    RestrState &r = restr_state(h);
+    cudaStream_t s = handle_stream(h);
+    const int k = handle_k(h);
+    const int N = (int)handle_n_points(h);
+    YdfArgs y;
+    y.X = handle_x32(h);
+    y.N = N;
+    y.n = handle_n_dim(h);
+    y.U32 = handle_u32(h);
+    y.U32lo = handle_u32lo(h);
+    y.KP = handle_kp(h);
+    y.Npad = r.Npad;
+    y.Yh = r.Ydh;
+    y.Yl = r.Ydl;
+    y.KY = r.KY;
+    RefineArgs unused;
+    std::memset(&unused, 0, sizeof(unused));
+    RCK(launch_ydf_refine(y, unused, k, 2 * handle_sms(h), 0, true, s));
+    std::vector<float> th((size_t)k * r.Npad), tl((size_t)k * r.Npad);
+    RCK(cudaMemcpyAsync(th.data(), r.Ydh, th.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    RCK(cudaMemcpyAsync(tl.data(), r.Ydl, tl.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    RCK(cudaStreamSynchronize(s));
+    std::vector<float> oh((size_t)N * k), ol((size_t)N * k);
+    for (int i = 0; i < N; ++i)
+        for (int c = 0; c < k; ++c) {
+            oh[(size_t)i * k + c] = th[(size_t)c * r.Npad + i];
+            ol[(size_t)i * k + c] = tl[(size_t)c * r.Npad + i];
+        }
+    const cudaMemcpyKind kind = out_is_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    RCK(cudaMemcpy(Yh_out, oh.data(), oh.size() * sizeof(float), kind));
+    RCK(cudaMemcpy(Yl_out, ol.data(), ol.size() * sizeof(float), kind));
+    return SAP_OK;
+}
+
 bool restructured_uses_refine(sap_handle h)
 {
     const int t = handle_tune(h).refine;
@@ -1734,6 +1770,7 @@ void restructured_stats(sap_handle h, sap_stats *out)
     out->n_excluded = r.n_excluded;
     out->cert_bound = r.b_cap;
     out->y_error_unit = r.y_eps;
+    out->ydf_error_unit = df_error_unit(handle_n_dim(h));
 }
 
 } // namespace sap

@@ -97,5 +97,6 @@ void restructured_free(sap_handle h);
 void restructured_stats(sap_handle h, sap_stats *out);
 sap_status restructured_set_bound(sap_handle h, double b_cap);
 sap_status restructured_project(sap_handle h, float *Y_out, int out_is_device);
+sap_status restructured_project_df(sap_handle h, float *Yh_out, float *Yl_out, int out_is_device);
 
 } // namespace sap

@@ -48,6 +48,32 @@ def test_projection_error_within_certified_bound(P, split, N, n, k):
     assert (err / nu[:, None]).max() > eps * 1e-4
 
 
+@pytest.mark.parametrize("N,n,k", [(700, 20, 4), (300, 100, 5), (130, 7, 1), (257, 300, 12), (200, 1100, 20)])
+def test_df_projection_within_certified_bound(P, N, n, k):
+    """The double-float projection of the second tier (hi + lo FP32 pairs from
+    error-free products of the exact points and the FP64 basis) is within
+    ydf_error_unit * ||x_i|| of <x_i, u_c> for every entry: checked against
+    an FP64 product on ragged row counts, n across the 256 boundary and
+    beyond 1024, and k from 1 to 20."""
+    g = np.random.default_rng(7 * N + n + k)
+    X = (g.standard_normal((N, n)) + 3.0).astype(np.float32)
+    U = W.random_basis(n, k, N + 1)
+    with P.Sap(X) as s:
+        s.set_basis(U)
+        hi, lo = s.project_df()
+        eps = s.stats()["ydf_error_unit"]
+    assert 0 < eps < 2e-10
+    X64 = X.astype(np.float64)
+    exact = X64 @ U.T
+    got = hi.astype(np.float64) + lo.astype(np.float64)
+    xn = np.linalg.norm(X64, axis=1)
+    err = np.abs(got - exact)
+    assert np.all(err <= eps * xn[:, None]), (err / xn[:, None]).max() / eps
+    # far more accurate than one FP32 number, and the comparison is not vacuous
+    assert (err / xn[:, None]).max() < 1e-10
+    assert np.abs(hi).max() > 0 and np.any(lo != 0)
+
+
 @pytest.mark.parametrize("N,m,k,seed", [(700, 10, 4, 3), (300, 50, 5, 5), (129, 4, 2, 7), (520, 8, 1, 9)])
 def test_restructured_lockstep(P, N, m, k, seed):
     X = W.moment_curve(N, m, seed, np.float32)
@@ -126,3 +152,25 @@ def test_c2_restructured_full_size(P):
     m = O.min_secant(X64, Uf)
     check_pair(X64, Uf, m, int(am[-1, 0]), int(am[-1, 1]), hist[-1])
     assert st["n_near"] > 0 and st["last_tier2"] >= 1
+
+
+@pytest.mark.parametrize("tier", [0, 1])
+@pytest.mark.parametrize("N,n,k", [(600, 300, 3), (450, 40, 1)])
+def test_second_tiers_lockstep(P, tier, N, n, k):
+    """Both second tiers (explicit differences, double-float refine) give the
+    oracle's argmin, ratio and update in lock-step, for n on both sides of
+    the 256 default switch and k = 1 (where ties in the ratio are dense)."""
+    g = np.random.default_rng(N + n)
+    t = g.random(N) * 2 * np.pi
+    # a curve on a 2-torus linearly embedded in R^n (short secants abound)
+    base = np.stack([np.cos(t), np.sin(t), np.cos(3 * t), np.sin(3 * t), np.cos(7 * t) * 0.5], axis=1)
+    Q, _ = np.linalg.qr(g.standard_normal((n, 5)))
+    X = (base @ Q.T + 0.5).astype(np.float32)
+    X64 = X.astype(np.float64)
+    U = W.random_basis(n, k, N + 3)
+    with P.Sap(X) as s:
+        s.set_path("restructured")
+        s.set_tuning(pass_bound=2e-3, pass_stages=0, explicit_blocks_per_sm=2, update_blocks=0,
+                     plain_blocks_per_sm=2, programmatic_launch=0, refine_tier=tier)
+        for _ in range(5):
+            U, _ = lockstep(s, X64, U, 0.01)

@@ -9,7 +9,7 @@ the FP64 argmin and the FP64 basis update.  Steps run as replays of captured
 CUDA graphs on a stream owned here, timed with CUDA events on that stream.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                        [--workload moment_curve|fp64_small|sweep|batch|softmin]
+                        [--workload moment_curve|fp64_small|sweep|batch|softmin|subsample]
 Under torchrun every rank runs its own replica (the workload does not need a
 collective); the time is the max over ranks and value counts all ranks.
 
@@ -22,7 +22,9 @@ forms of the hot path, one JSON line each, on their own synthetic inputs:
   batch      -- 32 hyperspectral scenes (n = 224, N log-uniform in
                 [500, 20000], BF16, eps = 0.05), k = 10, all advancing together;
   softmin    -- soft-min Riemannian ascent, moment curve N = 16384, n = 100,
-                k = 5, tau = 0.01, 200 steps.
+                k = 5, tau = 0.01, 200 steps;
+  subsample  -- 10 random 512-point subsets of a 21,025-pixel synthetic
+                hyperspectral cube (n = 200), dimension sweep k = 1..10 each.
 """
 from __future__ import annotations
 
@@ -62,7 +64,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="moment_curve",
-                    choices=["moment_curve", "fp64_small", "sweep", "batch", "softmin"])
+                    choices=["moment_curve", "fp64_small", "sweep", "batch", "softmin", "subsample"])
     return ap.parse_args()
 
 
@@ -725,6 +727,72 @@ def run_softmin(args):
     s.close()
 
 
+def run_subsample(args):
+    """Repeated point subsampling (Sec. VI-C protocol on a synthetic
+    hyperspectral cube): 10 random 512-pixel subsets of 21,025 pixels in
+    R^200, the dimension sweep k = 1..10 of each, 100 iterations."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1807_03425_gb300 import SapBatch
+    _, rank, local = dist()
+    torch.cuda.set_device(local)
+    cfg = W.CONFIGS["subsample"]
+    N, n, R, m, kmax, alpha, thr = cfg["N"], cfg["n"], cfg["R"], cfg["m"], cfg["kmax"], cfg["alpha"], cfg["threshold"]
+    X = W.hyperspectral(N, cfg["data_seed"], W.endmembers(cfg["data_seed"] + 1, n), noise=0.01, bf16=False)
+    idx = W.subsample_indices(N, R, m, cfg["index_seed"])
+    U0 = W.random_basis(n, kmax, cfg["basis_seed"])
+    T = args.steps if args.steps else cfg["T"]
+    Wm = max(args.warmup if args.warmup is not None else 3, 3)
+    P = m * (m - 1) // 2
+    sb = SapBatch.from_subsamples(X, idx)
+    for b in range(R):
+        sb.estimate_dim(b, U0, Wm, alpha, thr)
+        sb.estimate_dim(b, U0, T, alpha, thr)  # captures the chunk graphs the timed call replays
+    st0 = sb.stats()["kernel_launches"]
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    tw0 = time.time()
+    t0 = time.perf_counter()
+    res = [sb.estimate_dim(b, U0, T, alpha, thr) for b in range(R)]
+    wall = time.perf_counter() - t0
+    clk = clocks.stop(tw0, time.time())
+    launches = sb.stats()["kernel_launches"] - st0
+    if rank != 0:
+        return
+    its = R * T
+    line = _common(args, cfg["workload"], its / wall, "sweep iterations/s", 1e3 * wall / its, its, Wm, "f32",
+                   {"N": N, "n": n, "subsets": R, "points_per_subset": m, "k": "1..%d" % kmax, "alpha": alpha,
+                    "threshold": thr, "timing": "wall clock around the R sweeps (each synchronises)",
+                    "l2": "each subset's problem is L2-resident (131 K pairs)"})
+    line.update({
+        "sap_iterations_per_s": its * kmax / wall,
+        "secant_evals_per_s": its * kmax * P / wall,
+        "k_estimates": [int(r[0]) for r in res],
+        "ratio_curves": [[float(v) for v in r[1]] for r in res],
+        "roofline": {"bound": "latency", "achieved": 1e6 * wall / its, "unit": "us per sweep iteration",
+                     "peak": None, "frac": None, "traffic": None,
+                     "note": "131 K pairs per subset: every kernel of an iteration is launch/latency bound"},
+        "e2e": {"value": its / wall, "unit": "sweep iterations/s", "h2d_bytes_per_step": n * kmax * 8 / T,
+                "d2h_bytes_per_step": kmax * 8 / T},
+        "gpu_launches": launches,
+    })
+    if clk:
+        line["clocks"] = clk
+    import oracle as O
+    Xs = X[idx[0]].astype(np.float64)
+    t0 = time.perf_counter()
+    for k in range(1, kmax + 1):
+        O.step(Xs, U0[:k], alpha)
+    dt = time.perf_counter() - t0
+    line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "sweep iterations/s", "cores": O.num_threads(),
+                            "kind": "oracle",
+                            "sample": "one FP64 step of each k = 1..%d on one 512-point subset" % kmax}
+    print(json.dumps(line), flush=True)
+    sb.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference" or args.workload == "moment_curve":
@@ -738,7 +806,7 @@ def main():
         run_native(args)
     else:
         {"fp64_small": run_fp64_small, "sweep": run_sweep, "batch": run_batch,
-         "softmin": run_softmin}[args.workload](args)
+         "softmin": run_softmin, "subsample": run_subsample}[args.workload](args)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.impl != "reference":
         import torch.distributed as tdist
         if tdist.is_initialized():

@@ -382,6 +382,23 @@ sap_status sap_get_tuning(sap_handle h, sap_tuning *out);
  * SAP_E_ARG).  On a batch handle, every dataset. */
 sap_status sap_set_tuning(sap_handle h, const sap_tuning *in);
 
+/*
+ * Repeated point subsampling (Sec. VI-C: SAP on many random subsets of a
+ * large point set, e.g. 10 subsets of 512 of 21,025 pixels, and the
+ * dimension-estimation curves compared across subsets).  Creates a batch
+ * handle of R datasets, dataset b holding the rows idx[b*m + 0 .. m-1] of X
+ * (N x n row-major in dtype dt, host or device as x_is_device; idx is a
+ * host array of R*m indices in [0, N), drawn by the caller; a repeated
+ * index yields a duplicate point, whose pairs are excluded as usual).
+ * 1 <= R <= 4096, 2 <= m <= min(N, 92681).  The handle behaves as one from
+ * sap_create_batch; sap_estimate_dim_b runs the dimension sweep of one
+ * dataset (as sap_estimate_dim does on an ordinary handle).
+ */
+sap_status sap_create_subsamples(const void *X, int64_t N, int32_t n, sap_dtype dt, int x_is_device,
+                                 const int64_t *idx, int32_t R, int32_t m, sap_handle *out);
+sap_status sap_estimate_dim_b(sap_handle h, int32_t b, const double *U0, int32_t k_max, int32_t iters,
+                              double alpha, double threshold, int32_t *k_out, double *ratios_out);
+
 /* Read the handle's statistics. */
 sap_status sap_get_stats(sap_handle h, sap_stats *out);
 

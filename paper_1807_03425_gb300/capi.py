@@ -109,6 +109,8 @@ def load_library():
         "sap_softmin_backward": ([vp, f64, f64, vp, i32], i32),
         "sap_softmin_ascent": ([vp, f64, f64, i32, vp], i32),
         "sap_set_pass_bound": ([vp, f64], i32),
+        "sap_create_subsamples": ([vp, i64, i32, i32, i32, vp, i32, i32, ctypes.POINTER(vp)], i32),
+        "sap_estimate_dim_b": ([vp, i32, vp, i32, i32, f64, f64, ctypes.POINTER(i32), vp], i32),
         "sap_project_df": ([vp, vp, vp, i32], i32),
         "sap_autotune": ([vp, f64, i32, ctypes.POINTER(Tuning)], i32),
         "sap_get_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
@@ -412,6 +414,41 @@ def sap_create_batch(Xs, dtype=None):
     return h
 
 
+def sap_create_subsamples(X, idx, dtype=None):
+    """X: (N, n) NumPy array (float32, float64 or uint16 BF16 bits); idx:
+    (R, m) int64 row indices.  Returns a batch handle of the R subsets."""
+    lib = load_library()
+    if dtype is None:
+        dt = str(X.dtype)
+        dtype = F64 if "float64" in dt else (BF16 if "uint16" in dt or "bfloat16" in dt or "int16" in dt else F32)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    R, m = idx.shape
+    h = ctypes.c_void_p()
+    if hasattr(X, "data_ptr"):  # a contiguous CUDA tensor: rows gathered on the device
+        ptr, dev = ctypes.c_void_p(X.contiguous().data_ptr()), 1
+    else:
+        want = {F32: np.float32, F64: np.float64, BF16: np.uint16}[dtype]
+        X = np.ascontiguousarray(X, dtype=want)
+        ptr, dev = X.ctypes.data_as(ctypes.c_void_p), 0
+    code = lib.sap_create_subsamples(ptr, X.shape[0], X.shape[1], dtype, dev,
+                                     idx.ctypes.data_as(ctypes.c_void_p), R, m, ctypes.byref(h))
+    if code != 0:
+        raise SapError(code, "sap_create_subsamples(N=%d, R=%d, m=%d)" % (X.shape[0], R, m))
+    return h
+
+
+def sap_estimate_dim_b(h, b, U0, iters, alpha, threshold):
+    """Dimension sweep of dataset b of a batch; as sap_estimate_dim."""
+    U0 = np.ascontiguousarray(U0, dtype=np.float64)
+    kmax = U0.shape[0]
+    ratios = np.empty(kmax, dtype=np.float64)
+    kout = ctypes.c_int32()
+    _check(h, load_library().sap_estimate_dim_b(h, int(b), U0.ctypes.data_as(ctypes.c_void_p), kmax, int(iters),
+                                                float(alpha), float(threshold), ctypes.byref(kout),
+                                                ratios.ctypes.data_as(ctypes.c_void_p)))
+    return kout.value, ratios
+
+
 def sap_batch_count(h):
     b = ctypes.c_int32()
     _check(h, load_library().sap_batch_count(h, ctypes.byref(b)))
@@ -571,12 +608,22 @@ class Sap:
 class SapBatch:
     """Several datasets of one dimension run together (uneven sizes)."""
 
-    def __init__(self, Xs, dtype=None):
+    def __init__(self, Xs, dtype=None, _handle=None):
         self.Ns = [int(X.shape[0]) for X in Xs]
         self.n = int(Xs[0].shape[1])
         self.B = len(Xs)
-        self.h = sap_create_batch(Xs, dtype)
+        self.h = _handle if _handle is not None else sap_create_batch(Xs, dtype)
         self.ks = [0] * self.B
+
+    @classmethod
+    def from_subsamples(cls, X, idx, dtype=None):
+        """R subsets of the rows of X (idx: (R, m) indices), Sec. VI-C."""
+        h = sap_create_subsamples(X, idx, dtype)
+        idx = np.asarray(idx)
+        return cls([np.empty((idx.shape[1], X.shape[1]))] * idx.shape[0], dtype, _handle=h)
+
+    def estimate_dim(self, b, U0, iters, alpha, threshold):
+        return sap_estimate_dim_b(self.h, b, U0, iters, alpha, threshold)
 
     def close(self):
         if self.h is not None:

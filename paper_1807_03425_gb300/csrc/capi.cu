@@ -1108,6 +1108,46 @@ sap_status sap_create_batch(const void *const *Xs, const int64_t *Ns, int32_t B,
     return SAP_OK;
 }
 
+sap_status sap_create_subsamples(const void *X, int64_t N, int32_t n, sap_dtype dt, int x_is_device,
+                                 const int64_t *idx, int32_t R, int32_t m, sap_handle *out)
+{
+    if (!out) return SAP_E_ARG;
+    *out = nullptr;
+    if (!X || !idx || N < 2 || n < 1 || n > 16384 || R < 1 || R > 4096 || m < 2 || m > N || m > 92681)
+        return SAP_E_ARG;
+    if (dt != SAP_F32 && dt != SAP_BF16 && dt != SAP_F64) return SAP_E_ARG;
+    for (long long q = 0; q < (long long)R * m; ++q)
+        if (idx[q] < 0 || idx[q] >= N) return SAP_E_ARG;
+    const size_t es = dt == SAP_F64 ? 8 : dt == SAP_BF16 ? 2 : 4;
+    const size_t row = (size_t)n * es;
+    // gather each subset's rows into one staging buffer on the side X lives on
+    std::vector<unsigned char> host;
+    unsigned char *dev = nullptr;
+    if (x_is_device) {
+        if (cudaMalloc(&dev, (size_t)R * m * row) != cudaSuccess) {
+            cudaGetLastError();
+            return SAP_E_OOM;
+        }
+        for (long long q = 0; q < (long long)R * m; ++q)
+            if (cudaMemcpy(dev + q * row, static_cast<const unsigned char *>(X) + idx[q] * row, row,
+                           cudaMemcpyDeviceToDevice) != cudaSuccess) {
+                cudaFree(dev);
+                return SAP_E_CUDA;
+            }
+    } else {
+        host.resize((size_t)R * m * row);
+        for (long long q = 0; q < (long long)R * m; ++q)
+            std::memcpy(host.data() + q * row, static_cast<const unsigned char *>(X) + idx[q] * row, row);
+    }
+    const unsigned char *base = x_is_device ? dev : host.data();
+    std::vector<const void *> Xs(R);
+    std::vector<int64_t> Ns(R, m);
+    for (int b = 0; b < R; ++b) Xs[b] = base + (size_t)b * m * row;
+    const sap_status st = sap_create_batch(Xs.data(), Ns.data(), R, n, dt, x_is_device, out);
+    if (dev) cudaFree(dev);  // each dataset copied its rows
+    return st;
+}
+
 sap_status sap_batch_count(sap_handle h, int32_t *B)
 {
     CHECK_HANDLE(h);
@@ -1128,6 +1168,16 @@ static sap_status kid_result(sap_handle h, int32_t b, sap_handle kid, sap_status
 {
     if (st != SAP_OK) h->err = "dataset " + std::to_string(b) + ": " + kid->err;
     return st;
+}
+
+sap_status sap_estimate_dim_b(sap_handle h, int32_t b, const double *U0, int32_t k_max, int32_t iters,
+                              double alpha, double threshold, int32_t *k_out, double *ratios_out)
+{
+    CHECK_HANDLE(h);
+    sap_handle kid;
+    sap_status st = kid_of(h, b, &kid);
+    if (st != SAP_OK) return st;
+    return kid_result(h, b, kid, sap_estimate_dim(kid, U0, k_max, iters, alpha, threshold, k_out, ratios_out));
 }
 
 sap_status sap_set_basis_b(sap_handle h, int32_t b, const double *U, int32_t k, int u_is_device)

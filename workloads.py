@@ -128,6 +128,13 @@ def hyperspectral_batch(B: int, seed: int, n_min: int = 500,
     return Xs, Ns
 
 
+def subsample_indices(N: int, R: int, m: int, seed: int) -> np.ndarray:
+    """R subsets of m distinct row indices of range(N) (Sec. VI-C: repeated
+    random subsamples of a large point set), as an (R, m) int64 array."""
+    g = rng(seed)
+    return np.stack([np.sort(g.permutation(N)[:m]) for _ in range(R)]).astype(np.int64)
+
+
 # The benchmark configurations (sizes as stated for each workload).
 CONFIGS = {
     "c1": dict(workload="moment_curve_fp64_N200_n10_k3", N=200, m=5, k=3,
@@ -140,6 +147,9 @@ CONFIGS = {
     "c4": dict(workload="hyperspectral_32x_N500to20000_n224_k10_eps0.05",
                B=32, n=224, k=10, eps=0.05, T=500, alpha=0.01, dtype="bf16",
                data_seed=5, basis_seed=6),
+    "subsample": dict(workload="hyperspectral_N21025_n200_10x512_k1to10", N=21025, n=200, R=10,
+                      m=512, kmax=10, T=100, alpha=0.01, threshold=0.1, dtype="f32", data_seed=7,
+                      basis_seed=8, index_seed=9),
     "c5": dict(workload="moment_curve_softmin_N16384_n100_k5", N=16384, m=50,
                k=5, tau=0.01, steps=200, eta=0.005, dtype="f32", data_seed=1,
                basis_seed=2),

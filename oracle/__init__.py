@@ -81,6 +81,8 @@ def _load():
         lib.orc_softmin.argtypes = [dp, i64, i32, dp, i32, f64, f64, dp, dp]
         lib.orc_softmin.restype = i32
         lib.orc_num_threads.restype = i32
+        lib.orc_secant_gram.argtypes = [dp, i64, i32, f64, dp]
+        lib.orc_secant_gram.restype = i64
         _lib = lib
         return lib
 
@@ -251,3 +253,31 @@ def softmin_ascent_step(X, U, tau: float, eta: float, eps: float = 0.0):
     if nr == 0.0:
         return U.copy(), L, 0.0
     return qf(U + eta * GR / nr), L, nr
+
+
+def secant_gram(X, eps: float = 0.0):
+    """C = S S^T = sum over kept pairs of s s^T (unit secants s; Sec. IV),
+    n x n FP64, and the number of kept pairs."""
+    X = _x(X)
+    n = X.shape[1]
+    C = np.empty((n, n), dtype=np.float64)
+    kept = _load().orc_secant_gram(_dp(X), X.shape[0], n, eps, _dp(C))
+    if kept < 0:
+        raise NoSecantError("every pair is excluded")
+    return C, int(kept)
+
+
+def secant_pca(X, k: int, eps: float = 0.0):
+    """The PCA start of Algorithm 1 (Sec. IV): the top k left singular vectors
+    of the unit-secant matrix S, i.e. the eigenvectors of S S^T with the k
+    largest eigenvalues (numpy's symmetric eigensolver serves as the step),
+    each signed so that its entry of largest magnitude is positive.  Returns
+    (U as (k, n), the k singular values sqrt(lambda), descending)."""
+    C, _ = secant_gram(X, eps)
+    lam, V = np.linalg.eigh(C)
+    order = np.argsort(lam)[::-1][:k]
+    U = V[:, order].T.copy()
+    for c in range(k):
+        if U[c, np.argmax(np.abs(U[c]))] < 0:
+            U[c] = -U[c]
+    return np.ascontiguousarray(U), np.sqrt(np.maximum(lam[order], 0.0))

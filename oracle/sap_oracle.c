@@ -409,6 +409,47 @@ int orc_softmin(const double *X, int64_t N, int n, const double *U, int k,
     return 0;
 }
 
+/*
+ * Secant Gram matrix for the PCA initialisation of Algorithm 1 (Sec. IV: the
+ * first basis is made of the top k left singular vectors of the n x p matrix
+ * S whose columns are the unit secants).  C = S S^T = sum over kept pairs of
+ * s s^T, s = (x_i - x_j)/||x_i - x_j||, written out pair by pair (n x n,
+ * row-major, symmetric).  Rows of C are summed per thread over i and then in
+ * a fixed order.  Returns the number of kept pairs, or -1 if none.
+ */
+int64_t orc_secant_gram(const double *X, int64_t N, int n, double eps, double *C)
+{
+    const size_t nn = (size_t)n * n;
+    memset(C, 0, sizeof(double) * nn);
+    int64_t kept = 0;
+    double *Cp = (double *)calloc((size_t)N * nn, sizeof(double));
+    int64_t *kp = (int64_t *)calloc((size_t)N, sizeof(int64_t));
+#pragma omp parallel
+    {
+        double *s = (double *)malloc(sizeof(double) * n);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < N; ++i) {
+            double *Ci = Cp + (size_t)i * nn;
+            for (int64_t j = i + 1; j < N; ++j) {
+                const double d2 = secant_len2(X, n, i, j);
+                if (!pair_kept(d2, eps)) continue;
+                orc_unit_secant(X, n, i, j, s);
+                for (int a = 0; a < n; ++a)
+                    for (int b = 0; b < n; ++b) Ci[(size_t)a * n + b] += s[a] * s[b];
+                kp[i] += 1;
+            }
+        }
+        free(s);
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        for (size_t q = 0; q < nn; ++q) C[q] += Cp[(size_t)i * nn + q];
+        kept += kp[i];
+    }
+    free(Cp);
+    free(kp);
+    return kept > 0 ? kept : -1;
+}
+
 /* Number of threads OpenMP will use (reported beside CPU timings). */
 int orc_num_threads(void)
 {

@@ -313,3 +313,74 @@ def test_softmin_ascent_step_stays_orthonormal():
     assert nr > 0
     assert np.abs(Un @ Un.T - np.eye(3)).max() <= 1e-14
     assert O.softmin(X, Un, 0.05, grad=False) > L
+
+
+# ---------------------------------------------------------------- secant PCA --
+# The PCA start of Algorithm 1 (Sec. IV): top-k left singular vectors of the
+# unit-secant matrix S.
+
+
+def test_secant_pca_hand_triangle():
+    """Points (0,0), (1,0), (0,1): unit secants (-1,0), (0,-1), (1,-1)/sqrt2,
+    so S S^T = [[3/2, -1/2], [-1/2, 3/2]] with eigenvalues 2 and 1; the first
+    direction is (1,-1)/sqrt2 (first entry positive), singular value sqrt2."""
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    C, kept = O.secant_gram(X)
+    assert kept == 3
+    assert np.allclose(C, [[1.5, -0.5], [-0.5, 1.5]], atol=1e-15)
+    U, sv = O.secant_pca(X, 1)
+    assert np.allclose(U, [[2 ** -0.5, -(2 ** -0.5)]], atol=1e-15)
+    assert abs(sv[0] - 2 ** 0.5) < 1e-15
+
+
+@pytest.mark.parametrize("N,n,k,seed", [(6, 3, 2, 1), (7, 5, 3, 2), (8, 4, 1, 3)])
+def test_secant_pca_matches_svd_of_explicit_secants(N, n, k, seed):
+    """Against numpy's SVD of the explicitly built n x p secant matrix."""
+    X = np.random.default_rng(seed).standard_normal((N, n))
+    cols = [(X[i] - X[j]) / np.linalg.norm(X[i] - X[j]) for i in range(N) for j in range(i + 1, N)]
+    S = np.array(cols).T
+    Us, sv, _ = np.linalg.svd(S, full_matrices=False)
+    U, svo = O.secant_pca(X, k)
+    assert np.allclose(svo, sv[:k], rtol=1e-12)
+    Pu, Ps = U.T @ U, Us[:, :k] @ Us[:, :k].T
+    assert np.abs(Pu - Ps).max() < 1e-10
+    assert np.abs(U @ U.T - np.eye(k)).max() < 1e-13
+
+
+def test_secant_gram_trace_counts_kept_pairs():
+    """trace(S S^T) = number of kept unit secants: duplicates and pairs
+    shorter than eps do not count (Sec. II, Sec. VII)."""
+    g = np.random.default_rng(4)
+    X = g.standard_normal((30, 6))
+    X[7] = X[3]
+    X[12] = X[11] + 1e-3
+    C, kept = O.secant_gram(X)
+    assert kept == 30 * 29 // 2 - 1 and abs(np.trace(C) - kept) < 1e-10
+    C2, kept2 = O.secant_gram(X, eps=0.01)
+    assert kept2 == kept - 1 and abs(np.trace(C2) - kept2) < 1e-10
+
+
+def test_secant_pca_of_subspace_data_is_isometric():
+    """Points in a k0-dimensional affine subspace: the top k0 secant
+    directions span it, every unit secant keeps its length (min ratio 1) and
+    the next singular value is zero."""
+    g = np.random.default_rng(5)
+    A = np.linalg.qr(g.standard_normal((9, 3)))[0].T  # 3 x 9, orthonormal rows
+    X = g.standard_normal((40, 3)) @ A + 0.7
+    U, sv = O.secant_pca(X, 4)
+    assert sv[3] < 1e-6 * sv[0]
+    m = O.min_secant(X, U[:3])
+    assert abs(m["r"] - 1.0) < 1e-12
+    assert np.abs(U[:3].T @ U[:3] - A.T @ A).max() < 1e-10
+
+
+def test_secant_pca_rotation_equivariance():
+    g = np.random.default_rng(6)
+    X = g.standard_normal((25, 5)) * np.array([3.0, 2.0, 1.0, 0.5, 0.2])
+    Q = np.linalg.qr(g.standard_normal((5, 5)))[0]
+    U, sv = O.secant_pca(X, 2)
+    V, sv2 = O.secant_pca(X @ Q, 2)
+    assert np.allclose(sv, sv2, rtol=1e-12)
+    # rows of U are vectors: the rotated data's directions are U Q, up to sign
+    dots = np.abs(np.sum((U @ Q) * V, axis=1))
+    assert np.allclose(dots, 1.0, atol=1e-10)

@@ -153,6 +153,25 @@ sap_status sap_set_min_secant_length(sap_handle h, double eps);
 sap_status sap_set_basis(sap_handle h, const double *U, int32_t k,
                          int u_is_device);
 
+/*
+ * The PCA start of Algorithm 1 (Sec. IV): set the basis to the top k left
+ * singular vectors of the n x p matrix S of unit secants of the kept pairs
+ * (distinct points, Sec. II; d >= eps after sap_set_min_secant_length,
+ * Sec. VII), i.e. the eigenvectors of S S^T = sum_{i<j} s s^T with the k
+ * largest eigenvalues, each signed so that its entry of largest magnitude is
+ * positive.  S S^T is formed in FP64 on the device as Xc^T L X (L the
+ * 1/d^2-weighted graph Laplacian of the pairs, lengths from explicit FP64
+ * differences), never storing S; the n x n symmetric eigenproblem is solved
+ * by cuSOLVER (FP64), loaded at the first call (SAP_E_UNSUPPORTED if
+ * libcusolver cannot be loaded).  U_out (nullable, host, n x k
+ * column-major) receives the basis, sigma_out (nullable, k) the singular
+ * values sqrt(lambda) in descending order.  1 <= k <= min(n, 32).  Resets
+ * the iteration counter, like sap_set_basis.  Work memory: 8 B per pair
+ * (the FP64 lengths) plus 8 N n + 8 n^2 bytes, freed before returning.
+ * Synchronises.
+ */
+sap_status sap_secant_pca(sap_handle h, int32_t k, double *U_out, double *sigma_out);
+
 /* Copy the current basis (n x k column-major FP64) into U_out. */
 sap_status sap_get_basis(sap_handle h, double *U_out, int out_is_device);
 

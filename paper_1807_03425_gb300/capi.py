@@ -109,6 +109,7 @@ def load_library():
         "sap_softmin_backward": ([vp, f64, f64, vp, i32], i32),
         "sap_softmin_ascent": ([vp, f64, f64, i32, vp], i32),
         "sap_set_pass_bound": ([vp, f64], i32),
+        "sap_secant_pca": ([vp, i32, vp, vp], i32),
         "sap_create_subsamples": ([vp, i64, i32, i32, i32, vp, i32, i32, ctypes.POINTER(vp)], i32),
         "sap_estimate_dim_b": ([vp, i32, vp, i32, i32, f64, f64, ctypes.POINTER(i32), vp], i32),
         "sap_project_df": ([vp, vp, vp, i32], i32),
@@ -210,6 +211,16 @@ def sap_set_split(h, split):
 
 def sap_set_min_secant_length(h, eps):
     _check(h, load_library().sap_set_min_secant_length(h, float(eps)))
+
+
+def sap_secant_pca(h, k, n):
+    """PCA start (Sec. IV): sets and returns the basis ((k, n) FP64) and the
+    k singular values of the unit-secant matrix."""
+    U = np.empty((k, n), dtype=np.float64)
+    sv = np.empty(k, dtype=np.float64)
+    _check(h, load_library().sap_secant_pca(h, int(k), U.ctypes.data_as(ctypes.c_void_p),
+                                            sv.ctypes.data_as(ctypes.c_void_p)))
+    return U, sv
 
 
 def sap_set_pass_bound(h, b_cap):
@@ -538,6 +549,11 @@ class Sap:
 
     def set_pass_bound(self, b_cap):
         sap_set_pass_bound(self.h, b_cap)
+
+    def secant_pca(self, k):
+        U, sv = sap_secant_pca(self.h, k, self.n)
+        self.k = int(k)
+        return U, sv
 
     def autotune(self, alpha, iters=16):
         return sap_autotune(self.h, alpha, iters)

@@ -353,6 +353,8 @@ cudaStream_t handle_stream(sap_handle h) { return h->stream; }
 int handle_sms(sap_handle h) { return h->sms; }
 ProbState *handle_state(sap_handle h) { return h->st; }
 const float *handle_x32(sap_handle h) { return h->X32; }
+const double *handle_x64(sap_handle h) { return h->X64; }
+sap_status secant_pca(sap_handle h, int k, double *U_out, double *sigma_out);  // pca.cu
 const float *handle_u32(sap_handle h) { return h->U32; }
 const float *handle_u32lo(sap_handle h) { return h->U32lo; }
 int2 *handle_cand1(sap_handle h) { return h->cand1; }
@@ -645,6 +647,19 @@ sap_status sap_set_min_secant_length(sap_handle h, double eps)
     sap_status s = tune_lookup(h);
     if (s != SAP_OK) return s;
     return reset_state(h);
+}
+
+sap_status sap_secant_pca(sap_handle h, int32_t k, double *U_out, double *sigma_out)
+{
+    CHECK_HANDLE(h);
+    NOT_BATCH(h);
+    std::vector<double> U((size_t)h->n * std::max(k, 1));
+    sap_status s = secant_pca(h, k, U.data(), sigma_out);
+    if (s != SAP_OK) return s;
+    s = sap_set_basis(h, U.data(), k, 0);
+    if (s != SAP_OK) return s;
+    if (U_out) std::memcpy(U_out, U.data(), U.size() * sizeof(double));
+    return SAP_OK;
 }
 
 sap_status sap_set_pass_bound(sap_handle h, double b_cap)

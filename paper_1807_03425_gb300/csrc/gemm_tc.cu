@@ -142,10 +142,11 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
             if (row < a.Npad) {
                 // component-major (Y^T): consecutive lanes write consecutive rows
                 if (a.ksplit == 1) {
+                    // block-major: the KY components of each 128-row block are contiguous
+                    float *yb = a.Y + (size_t)(row >> 7) * ((size_t)a.KY * 128) + (row & 127);
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
-                        if (c0 + q < a.KY)
-                            a.Y[(size_t)(c0 + q) * a.Npad + row] = fmaf(d2[q], a.lo_scale, d1[q]) * a.out_scale;
+                        if (c0 + q < a.KY) yb[(size_t)(c0 + q) * 128] = fmaf(d2[q], a.lo_scale, d1[q]) * a.out_scale;
                 } else {
                     float *dst = a.Ypart + (size_t)blockIdx.y * a.KY * a.Npad;
 #pragma unroll
@@ -162,13 +163,16 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
     if (warp == 0) tc::tmem_dealloc(tbase, ncols);
 }
 
-// Y = (sum of the K slices, in slice order) * out_scale.
-__global__ void ksum_kernel(const float *Ypart, int ksplit, size_t count, float out_scale, float *Y)
+// Y = (sum of the K slices, in slice order) * out_scale; the slices are
+// component-major (c * Npad + row), Y block-major like the product's output.
+__global__ void ksum_kernel(const float *Ypart, int ksplit, int KY, int Npad, float out_scale, float *Y)
 {
+    const size_t count = (size_t)KY * Npad;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
         float s = Ypart[e];
         for (int q = 1; q < ksplit; ++q) s += Ypart[(size_t)q * count + e];
-        Y[e] = s * out_scale;
+        const size_t c = e / Npad, row = e % Npad;
+        Y[(row >> 7) * ((size_t)KY * 128) + c * 128 + (row & 127)] = s * out_scale;
     }
 }
 
@@ -202,7 +206,7 @@ cudaError_t launch_gemm_y(const GemmArgs &a, cudaStream_t s)
     cudaError_t e = launch_pdl(a.pdl != 0, gemm_y_kernel, dim3(a.Npad / GM, ksplit), dim3(128), shm, s, b);
     if (e != cudaSuccess || ksplit == 1) return e;
     const size_t count = (size_t)a.KY * a.Npad;
-    ksum_kernel<<<(unsigned)std::min<size_t>((count + 255) / 256, 2048), 256, 0, s>>>(a.Ypart, ksplit, count,
+    ksum_kernel<<<(unsigned)std::min<size_t>((count + 255) / 256, 2048), 256, 0, s>>>(a.Ypart, ksplit, a.KY, a.Npad,
                                                                                     a.out_scale, a.Y);
     return cudaGetLastError();
 }

@@ -9,7 +9,7 @@ namespace sap {
 struct GemmArgs {
     CUtensorMap ta_hi, ta_lo;   // X split parts: Npad x NP, 16-bit, box 64 x 128
     CUtensorMap tb_hi, tb_lo;   // U split parts: KPG x NP, 16-bit, box 64 x KPG
-    float *Y;                   // Y^T: KY x Npad, FP32, component-major
+    float *Y;                   // FP32, block-major: [Npad/128][KY][128]
     int KY;                     // components written (multiple of 4, <= KPG)
     int Npad;                   // rows (multiple of 128)
     int nkb;                    // K blocks of 64

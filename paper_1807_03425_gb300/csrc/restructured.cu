@@ -256,8 +256,9 @@ struct PassArgs {
     const float *w;
     const int2 *wtiles;
     int ntiles;
-    const float *Y;   // Y^T, KY x Npad
-    int KY;
+    const float *Y;   // this basis's first component in block 0 of the block-major Y
+    int KY;           // components of this basis
+    int Ykt;          // components per block of the Y buffer (block stride / 128)
     int Npad;
     const float *nu;  // ||fl(x_i - mean)||, rounded up (Npad)
     float beta;       // sqrt(k) eps_Y, rounded up: per-pair bound beta (nu_i + nu_j) / d_ij
@@ -362,12 +363,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
             for (int it = 0; it < pre; ++it) {
                 const int2 IJ = sIJ[it];
                 unsigned char *base = sm + (size_t)it * sbytes;
-                for (int c = 0; c < KY; ++c) {
-                    tc::bulk_g2s(base + wbytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.x * T, T * 4,
-                                 &full[it]);
-                    tc::bulk_g2s(base + wbytes + ybytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.y * T,
-                                 T * 4, &full[it]);
-                }
+                tc::bulk_g2s(base + wbytes, a.Y + (size_t)IJ.x * a.Ykt * T, ybytes, &full[it]);
+                tc::bulk_g2s(base + wbytes + ybytes, a.Y + (size_t)IJ.y * a.Ykt * T, ybytes, &full[it]);
             }
             int issued = pre;
             bool marked = false;
@@ -405,12 +402,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 unsigned char *base = sm + (size_t)s * sbytes;
                 tc::mbar_expect_tx(&full[s], sbytes);
                 tc::bulk_g2s(base, a.w + (size_t)t * T * T, wbytes, &full[s]);
-                for (int c = 0; c < KY; ++c) {
-                    tc::bulk_g2s(base + wbytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.x * T, T * 4,
-                                 &full[s]);
-                    tc::bulk_g2s(base + wbytes + ybytes + c * T * 4, a.Y + (size_t)c * a.Npad + (size_t)IJ.y * T,
-                                 T * 4, &full[s]);
-                }
+                // one copy per side: the basis's components of the point block
+                tc::bulk_g2s(base + wbytes, a.Y + (size_t)IJ.x * a.Ykt * T, ybytes, &full[s]);
+                tc::bulk_g2s(base + wbytes + ybytes, a.Y + (size_t)IJ.y * a.Ykt * T, ybytes, &full[s]);
                 tc::bulk_g2s(base + wbytes + 2 * ybytes, a.nu + (size_t)IJ.x * T, T * 4, &full[s]);
                 tc::bulk_g2s(base + wbytes + 2 * ybytes + T * 4, a.nu + (size_t)IJ.y * T, T * 4, &full[s]);
                 ++issued;
@@ -1168,12 +1162,13 @@ bool make_map(CUtensorMap *m, void *base, bool bf16, uint64_t inner, uint64_t ou
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-__global__ void transpose_y_kernel(const float *Yt, int Npad, int N, int k, float *out)
+// block-major Y ([Npad/128][KY][128]) -> N x k row-major
+__global__ void transpose_y_kernel(const float *Yb, int KY, int N, int k, float *out)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N * k) return;
     const int i = e / k, c = e % k;
-    out[e] = Yt[(size_t)c * Npad + i];
+    out[e] = Yb[(size_t)(i >> 7) * KY * 128 + (size_t)c * 128 + (i & 127)];
 }
 
 template <typename T_>
@@ -1525,6 +1520,7 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         p.ntiles = r.nwtiles;
         p.Y = b.Y;
         p.KY = b.KY;
+        p.Ykt = b.Ykt;
         p.Npad = r.Npad;
         p.nu = r.nu;
         p.beta = (float)(std::sqrt((double)b.k) * r.y_eps * 1.02);
@@ -1626,6 +1622,7 @@ sap_status restructured_enqueue(sap_handle h, double alpha)
     b.U32 = handle_u32(h);
     b.U32lo = handle_u32lo(h);
     b.Y = r.Y;
+    b.Ykt = r.KY;
     b.Ydh = r.Ydh;
     b.Ydl = r.Ydl;
     b.st = handle_state(h);
@@ -1694,15 +1691,16 @@ sap_status restructured_project(sap_handle h, float *Y_out, int out_is_device)
     handle_push_timing(h, 0, ea, eb);
     // Y^T (component-major) -> N x k row-major
     if (out_is_device) {
-        transpose_y_kernel<<<(N * k + 255) / 256, 256, 0, s>>>(r.Y, r.Npad, N, k, Y_out);
+        transpose_y_kernel<<<(N * k + 255) / 256, 256, 0, s>>>(r.Y, r.KY, N, k, Y_out);
         RCK(cudaGetLastError());
         RCK(cudaStreamSynchronize(s));
     } else {
-        std::vector<float> yt((size_t)k * r.Npad);
+        std::vector<float> yt((size_t)r.KY * r.Npad);  // the whole block-major buffer
         RCK(cudaMemcpyAsync(yt.data(), r.Y, yt.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
         RCK(cudaStreamSynchronize(s));
         for (int i = 0; i < N; ++i)
-            for (int c = 0; c < k; ++c) Y_out[(size_t)i * k + c] = yt[(size_t)c * r.Npad + i];
+            for (int c = 0; c < k; ++c)
+                Y_out[(size_t)i * k + c] = yt[(size_t)(i >> 7) * r.KY * 128 + (size_t)c * 128 + (i & 127)];
     }
     return SAP_OK;
 }

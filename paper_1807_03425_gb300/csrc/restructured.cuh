@@ -35,7 +35,7 @@ struct RestrState {
     // basis operands
     void *Uhi = nullptr, *Ulo = nullptr;  // KPG x NP 16-bit
     int KPG = 0;              // k rounded up to the MMA N granule (16)
-    float *Y = nullptr;       // Npad x KY
+    float *Y = nullptr;       // block-major [Npad/128][KY][128]
     float *Ydh = nullptr, *Ydl = nullptr;  // double-float Y of the refine tier, KY x Npad each
     int KY = 0;               // k rounded up to 4
     int ksplit = 1;           // K slices of the product (shorter accumulation chains)
@@ -73,7 +73,8 @@ TuneParams &handle_tune(sap_handle h);
 struct BasisView {
     int k, KP, KY;            // width, FP32 basis stride, Y stride (components)
     const float *U32, *U32lo; // n x KP FP32 basis and its low part
-    float *Y;                 // KY x Npad, component-major
+    float *Y;                 // this basis's first component in block 0 of a block-major Y
+    int Ykt;                  // components per 128-point block of that Y buffer
     float *Ydh, *Ydl;         // double-float Y (refine tier), KY x Npad each
     ProbState *st;
     int2 *cand1, *cand2;      // candidate lists of the pass and of the explicit tier

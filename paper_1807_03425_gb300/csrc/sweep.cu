@@ -202,7 +202,8 @@ sap_status enqueue_iteration(sap_handle h, SweepState &sw, double alpha, int eva
         v.KY = b.KY;
         v.U32 = b.U32;
         v.U32lo = b.U32lo;
-        v.Y = sw.Y + (size_t)b.off * r.Npad;
+        v.Y = sw.Y + (size_t)b.off * 128;  // block-major: the basis's components within each block
+        v.Ykt = sw.KY;
         v.Ydh = b.Ydh;
         v.Ydl = b.Ydl;
         v.st = b.st;

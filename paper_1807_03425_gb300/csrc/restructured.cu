@@ -128,6 +128,7 @@ struct WPrepArgs {
     const float *nu;
     const int2 *wtiles;
     float *w;
+    __half *wh;              // FP16 1/d of the stored pairs (NaN elsewhere)
     float eps2_lo, eps2_hi;  // FP32 window around eps^2 (0,0: no threshold)
     double eps2;
     float beta_coef;         // sqrt(k) * eps_Y, rounded up
@@ -193,15 +194,18 @@ __global__ void __launch_bounds__(256) wprep_kernel(WPrepArgs a)
     int nnear = 0, nexcl = 0;
     unsigned long long near_bits = 0ull;  // bit p*8+q marks a near pair
     float *wt = a.w + (size_t)blockIdx.x * T * T;
+    __half *ht = a.wh + (size_t)blockIdx.x * T * T;
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
         const int i = i0 + ty * 8 + p;
         float out[8];
+        __half hout[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int j = j0 + tx * 8 + q;
             const float dd = d2[p][q];
             float wv = __int_as_float(0x7fc00000);  // NaN: skipped by the pass
+            __half hv = __ushort_as_half((unsigned short)0x7e00);
             if (i < j && j < a.N) {
                 int cls;  // 0 excluded, 1 near, 2 stored
                 if (epson && dd < a.eps2_lo) cls = 0;
@@ -209,18 +213,27 @@ __global__ void __launch_bounds__(256) wprep_kernel(WPrepArgs a)
                     cls = excluded_fp64(a.X, a.n, i, j, a.eps2) ? 0 : 1;
                 else {
                     const float inv = 1.0f / dd;
-                    const float beta = a.beta_coef * (a.nu[i] + a.nu[j]) * sqrtf(inv);
-                    if (beta > a.b_cap) cls = 1;
-                    else { cls = 2; wv = inv; }
+                    const float id = 1.0f / sqrtf(dd);  // 1/d for the FP16 form
+                    const float beta = a.beta_coef * (a.nu[i] + a.nu[j]) * id;
+                    // near: the bound exceeds the cap, or 1/d leaves the FP16 range
+                    if (beta > a.b_cap || id > 6.0e4f) cls = 1;
+                    else { cls = 2; wv = inv; hv = __float2half_rn(id); }
                 }
                 if (cls == 0) ++nexcl;
                 if (cls == 1) { ++nnear; near_bits |= 1ull << (p * 8 + q); }
             }
             out[q] = wv;
+            hout[q] = hv;
         }
         float4 *dst = reinterpret_cast<float4 *>(wt + (size_t)(ty * 8 + p) * T + tx * 8);
         dst[0] = make_float4(out[0], out[1], out[2], out[3]);
         dst[1] = make_float4(out[4], out[5], out[6], out[7]);
+        uint4 hp;
+        hp.x = (unsigned)__half_as_ushort(hout[0]) | ((unsigned)__half_as_ushort(hout[1]) << 16);
+        hp.y = (unsigned)__half_as_ushort(hout[2]) | ((unsigned)__half_as_ushort(hout[3]) << 16);
+        hp.z = (unsigned)__half_as_ushort(hout[4]) | ((unsigned)__half_as_ushort(hout[5]) << 16);
+        hp.w = (unsigned)__half_as_ushort(hout[6]) | ((unsigned)__half_as_ushort(hout[7]) << 16);
+        *reinterpret_cast<uint4 *>(ht + (size_t)(ty * 8 + p) * T + tx * 8) = hp;
     }
     int total;
     const int off = block_exclusive_scan(nnear, scan, &total);
@@ -250,10 +263,10 @@ __global__ void __launch_bounds__(256) wprep_kernel(WPrepArgs a)
 
 // ------------------------------------------------------- all-pairs pass ---
 
-constexpr int kPassStagesMax = 3;
+constexpr int kPassStagesMax = 5;
 
 struct PassArgs {
-    const float *w;
+    const __half *wh;  // FP16 1/d tiles (tile-major upper triangle; NaN: skipped)
     const int2 *wtiles;
     int ntiles;
     const float *Y;   // this basis's first component in block 0 of the block-major Y
@@ -270,19 +283,21 @@ struct PassArgs {
     int pdl;
 };
 
-// One ring stage: the w tile, then for each side one 512-byte segment per
-// component of Y^T, then the 128 point norms nu of each side.
+// One ring stage: the FP16 1/d tile (32 KB), then for each side the basis's
+// components of the point block (block-major Y: one copy), then the 128 point
+// norms nu of each side.
 __host__ __device__ inline uint32_t pass_stage_bytes(int KY)
 {
-    return (uint32_t)T * T * 4 + 2u * T * KY * 4 + 2u * T * 4;
+    return (uint32_t)T * T * 2 + 2u * T * KY * 4 + 2u * T * 4;
 }
 
 // Certified error of one stored pair's ratio from the tensor-core Y:
-// |r~ - r| <= beta (nu_i + nu_j) / d_ij + rho r, with 1/d_ij = sqrt(w_ij).
-// The same product the length preparation compares with b_cap, rounded up.
-__device__ __forceinline__ float pair_bound(float beta, float nui, float nuj, float w)
+// |r~ - r| <= beta (nu_i + nu_j) / d_ij + rho r, with the stored FP16 h =
+// 1/d_ij (relative error < 2^-11 + 2^-23, so the bound is inflated by 2^-10).
+// The same product the length preparation compares with b_cap.
+__device__ __forceinline__ float pair_bound(float beta, float nui, float nuj, float h)
 {
-    return beta * (nui + nuj) * sqrtf(w) * 1.000002f;
+    return beta * (nui + nuj) * h * 1.001f;
 }
 
 // Persistent, warp-specialised pass: one block per SM.  Each block's first
@@ -326,7 +341,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int KY = a.KY, S = a.stages;
-    const uint32_t wbytes = T * T * 4, ybytes = T * KY * 4, sbytes = wbytes + 2 * ybytes + 2 * T * 4;
+    const uint32_t wbytes = T * T * 2, ybytes = T * KY * 4, sbytes = wbytes + 2 * ybytes + 2 * T * 4;
     // tiles below gridDim.x * S are static (it < S); the rest are dynamic
     const int nall = blockIdx.x < (unsigned)a.ntiles ? (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     const int nstatic = nall < S ? nall : S;
@@ -354,7 +369,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 sIJ[it] = IJ;  // published by the mbarrier completion
                 unsigned char *base = sm + (size_t)it * sbytes;
                 tc::mbar_expect_tx(&full[it], sbytes);
-                tc::bulk_g2s(base, a.w + (size_t)t * T * T, wbytes, &full[it]);
+                tc::bulk_g2s(base, a.wh + (size_t)t * T * T, wbytes, &full[it]);
                 tc::bulk_g2s(base + wbytes + 2 * ybytes, a.nu + (size_t)IJ.x * T, T * 4, &full[it]);
                 tc::bulk_g2s(base + wbytes + 2 * ybytes + T * 4, a.nu + (size_t)IJ.y * T, T * 4, &full[it]);
             }
@@ -401,7 +416,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 sIJ[s] = IJ;  // published by the mbarrier completion below
                 unsigned char *base = sm + (size_t)s * sbytes;
                 tc::mbar_expect_tx(&full[s], sbytes);
-                tc::bulk_g2s(base, a.w + (size_t)t * T * T, wbytes, &full[s]);
+                tc::bulk_g2s(base, a.wh + (size_t)t * T * T, wbytes, &full[s]);
                 // one copy per side: the basis's components of the point block
                 tc::bulk_g2s(base + wbytes, a.Y + (size_t)IJ.x * a.Ykt * T, ybytes, &full[s]);
                 tc::bulk_g2s(base + wbytes + ybytes, a.Y + (size_t)IJ.y * a.Ykt * T, ybytes, &full[s]);
@@ -437,8 +452,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
         const int2 IJ = sIJ[s];
         if (IJ.x < 0) break;  // the producer has no more tiles
         const float gnow = load_pos_float(&a.st->run_ub1);  // consumed after the tile
-        const float *ws = reinterpret_cast<const float *>(sm + (size_t)s * sbytes);
-        const float *yI = ws + T * T;   // yI[c * T + a]: component c of point I*T + a
+        const __half *hs = reinterpret_cast<const __half *>(sm + (size_t)s * sbytes);
+        const float *yI = reinterpret_cast<const float *>(sm + (size_t)s * sbytes + wbytes);  // yI[c * T + a]
         const float *yJ = yI + T * KY;
 
         float v[RPW][CPT];
@@ -459,7 +474,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
 #pragma unroll
             for (int r = 0; r < RPW; ++r) {
                 const int row = row0 + r * RSTEP;
-                const float *wr = ws + row * T + col0;
+                const __half *hr = hs + row * T + col0;
                 uint64_t s2[NPR > 0 ? NPR : 1];
 #pragma unroll
                 for (int p = 0; p < NPR; ++p) s2[p] = 0ull;
@@ -473,17 +488,20 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                         s2[p] = tc::fma2(e, e, s2[p]);
                     }
                 }
-                float wv[CPT];
+                float wv[CPT];  // 1/d of the thread's columns
                 if (CPT == 4) {
-                    const float4 t = *reinterpret_cast<const float4 *>(wr);
-                    wv[0] = t.x; wv[1 % CPT] = t.y; wv[2 % CPT] = t.z; wv[3 % CPT] = t.w;
+                    const uint2 raw = *reinterpret_cast<const uint2 *>(hr);
+                    const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
+                    const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
+                    wv[0] = f0.x; wv[1 % CPT] = f0.y; wv[2 % CPT] = f1.x; wv[3 % CPT] = f1.y;
                 } else {
-                    const float2 t = *reinterpret_cast<const float2 *>(wr);
-                    wv[0] = t.x; wv[1 % CPT] = t.y;
+                    const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(hr));
+                    wv[0] = f0.x; wv[1 % CPT] = f0.y;
                 }
 #pragma unroll
                 for (int p = 0; p < NPR; ++p) {
-                    const float2 q = tc::upk2(tc::mul2(s2[p], tc::pk2(wv[2 * p], wv[(2 * p + 1) % CPT])));
+                    const uint64_t hh = tc::pk2(wv[2 * p], wv[(2 * p + 1) % CPT]);
+                    const float2 q = tc::upk2(tc::mul2(s2[p], tc::mul2(hh, hh)));
                     v[r][(2 * p) % CPT] = q.x;
                     v[r][(2 * p + 1) % CPT] = q.y;
                     mymin = fminf(mymin, fminf(q.x, q.y));
@@ -502,7 +520,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                     const float e = yI[c * T + row] - yj[c];
                     sacc = fmaf(e, e, sacc);
                 }
-                v[r][0] = sacc * ws[row * T + col0];
+                const float hv = __half2float(hs[row * T + col0]);
+                v[r][0] = sacc * (hv * hv);
                 mymin = fminf(mymin, v[r][0]);
             }
         }
@@ -530,7 +549,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
 #pragma unroll
                     for (int q = 0; q < CPT; ++q)
                         if (v[r][q] == wmin) { prow = row0 + r * RSTEP; pcol = col0 + q; }
-                const float b = pair_bound(a.beta, nuI[prow], nuJ[pcol], ws[prow * T + pcol]);
+                const float b = pair_bound(a.beta, nuI[prow], nuJ[pcol], __half2float(hs[prow * T + pcol]));
                 ub = (sqrtf(wmin) + b) / (1.0f - a.cert.rho) * 1.000001f;
             }
             ub = __shfl_sync(0xffffffffu, ub, src);
@@ -551,7 +570,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 for (int q = 0; q < CPT; ++q)
                     if (v[r][q] <= thc2) {
                         const int prow = row0 + r * RSTEP, pcol = col0 + q;
-                        const float th = (ut + pair_bound(a.beta, nuI[prow], nuJ[pcol], ws[prow * T + pcol])) *
+                        const float th = (ut + pair_bound(a.beta, nuI[prow], nuJ[pcol], __half2float(hs[prow * T + pcol]))) *
                                          1.000001f;
                         if (v[r][q] <= th * th * 1.000001f) {
                             emit |= 1u << (r * CPT + q);
@@ -1210,8 +1229,9 @@ Cert cert_pass(int n, int k, double b_cap)
     const double u = std::ldexp(1.0, -24);
     auto g = [&](double m) { return m * u / (1.0 - m * u); };
     Cert c;
-    c.A = (float)(b_cap * 1.0001);  // >= every stored pair's own bound after FP32 rounding
-    c.rho = (float)((g(n + 2) + g(k) + 6 * u) * 1.05);
+    c.A = (float)(b_cap * 1.002);  // >= every stored pair's own bound (FP16 1/d, FP32 rounding)
+    // 2^-11: the FP16 rounding of 1/d; the rest as for explicit differences
+    c.rho = (float)((std::ldexp(1.0, -11) + g(n + 2) + g(k) + 8 * u) * 1.05);
     return c;
 }
 
@@ -1269,6 +1289,7 @@ sap_status classify(sap_handle h, int k)
     a.nu = r.nu;
     a.wtiles = r.wtiles;
     a.w = r.w;
+    a.wh = reinterpret_cast<__half *>(r.wh);
     a.eps2_lo = handle_eps2_lo(h);
     a.eps2_hi = handle_eps2_hi(h);
     a.eps2 = handle_eps2(h);
@@ -1370,6 +1391,7 @@ sap_status restructured_prepare(sap_handle h)
         RCK(cudaMalloc(&r.wtiles, t.size() * sizeof(int2)));
         RCK(cudaMemcpy(r.wtiles, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice));
         RCK(cudaMalloc(&r.w, (size_t)r.nwtiles * T * T * sizeof(float)));
+        RCK(cudaMalloc(&r.wh, (size_t)r.nwtiles * T * T * sizeof(uint16_t)));
         const long long P = (long long)N * (N - 1) / 2;
         r.near_cap = (unsigned int)std::min<long long>(P + 64, 1ll << 24);
         RCK(cudaMalloc(&r.near, (size_t)r.near_cap * sizeof(int2)));
@@ -1515,7 +1537,7 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
     cudaEvent_t ea, eb;
     {
         PassArgs p;
-        p.w = r.w;
+        p.wh = reinterpret_cast<const __half *>(r.wh);
         p.wtiles = r.wtiles;
         p.ntiles = r.nwtiles;
         p.Y = b.Y;
@@ -1758,7 +1780,7 @@ void restructured_free(sap_handle h)
     RestrState &r = restr_state(h);
     dfree(r.Xhi); dfree(r.Xlo); dfree(r.center); dfree(r.nu); dfree(r.w); dfree(r.wtiles);
     dfree(r.near); dfree(r.counters); dfree(r.Uhi); dfree(r.Ulo); dfree(r.Y); dfree(r.Ypart);
-    dfree(r.near_w); dfree(r.xn); dfree(r.Ydh); dfree(r.Ydl);
+    dfree(r.near_w); dfree(r.xn); dfree(r.Ydh); dfree(r.Ydl); dfree(r.wh);
 }
 
 void restructured_stats(sap_handle h, sap_stats *out)

@@ -363,7 +363,7 @@ sap_status sap_set_pass_bound(sap_handle h, double b_cap);
  */
 typedef struct {
     double pass_bound;              /* cap of the restructured pass's per-pair bound (sap_set_pass_bound) */
-    int32_t pass_stages;            /* TMA ring depth of the restructured pass: 2 or 3; 0 = as many as fit */
+    int32_t pass_stages;            /* TMA ring depth of the restructured pass: 2..5; 0 = as many as fit */
     int32_t explicit_blocks_per_sm; /* second-tier grid (candidates and near pairs), 1..8 blocks per SM */
     int32_t update_blocks;          /* FP64 recheck + update grid, 0 (one per SM) .. 304 */
     int32_t plain_blocks_per_sm;    /* plain pass grid, 1..8 blocks per SM (FP64 data: twice) */

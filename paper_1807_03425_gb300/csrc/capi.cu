@@ -701,7 +701,7 @@ sap_status sap_set_tuning(sap_handle h, const sap_tuning *in)
     CHECK_HANDLE(h);
     if (!in) return fail(h, SAP_E_ARG, "null input");
     FORWARD_BATCH(h, sap_set_tuning(kid, in));
-    if (!(in->pass_bound >= 1e-6 && in->pass_bound <= 0.25) || in->pass_stages < 0 || in->pass_stages > 3 ||
+    if (!(in->pass_bound >= 1e-6 && in->pass_bound <= 0.25) || in->pass_stages < 0 || in->pass_stages > 5 ||
         in->explicit_blocks_per_sm < 1 || in->explicit_blocks_per_sm > 8 || in->update_blocks < 0 ||
         in->update_blocks > kRecheckBlocks || in->plain_blocks_per_sm < 1 || in->plain_blocks_per_sm > 8 ||
         (in->programmatic_launch != 0 && in->programmatic_launch != 1) || in->refine_tier < -1 ||

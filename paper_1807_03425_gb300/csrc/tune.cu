@@ -72,7 +72,7 @@ void load_locked()
                         &p.su_blocks, &p.plain_per_sm, &p.pdl, &p.refine, &p.us_per_iter) == 16 &&
             ver == 3 && p.refine >= -1 && p.refine <= 1 && p.b_cap >= 1e-6 && p.b_cap <= 0.25 && p.expl_per_sm >= 1 && p.expl_per_sm <= 8 &&
             p.plain_per_sm >= 1 && p.plain_per_sm <= 8 && p.su_blocks >= 0 && p.su_blocks <= kRecheckBlocks &&
-            p.pass_stages >= 0 && p.pass_stages <= 3 && (p.pdl == 0 || p.pdl == 1))
+            p.pass_stages >= 0 && p.pass_stages <= 5 && (p.pdl == 0 || p.pdl == 1))
             g_cache[k] = p;
     }
     std::fclose(f);
@@ -203,7 +203,7 @@ sap_status tune_handle(sap_handle h, double alpha, int iters)
             c.b_cap = b;
             consider(c);
         }
-        for (int stg : {0, 2}) {
+        for (int stg : {0, 2, 3}) {
             TuneParams c = best;
             c.pass_stages = stg;
             consider(c);

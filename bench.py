@@ -345,7 +345,7 @@ def run_native(args):
 
     hbm, sm_max, peak_src = peaks()
     pass_ms = kt["restructured_pass"][0] / max(1, kt["restructured_pass"][1])
-    alg_bytes = 2 * P  # the pass streams one FP16 1/d_ij per pair
+    alg_bytes = 2 * P  # the pass streams one BF16 w_ij = 1/d_ij^2 per pair
     achieved = alg_bytes / (pass_ms * 1e-3) / 1e9
     traffic = PASS_TRAFFIC_BYTES if PASS_SOURCE_SHA == kernel_source_sha() else None
     plain_ms = kt_plain[0] / max(1, kt_plain[1])
@@ -360,7 +360,7 @@ def run_native(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": cfg["workload"], "N": N, "n": n, "k": k, "alpha": alpha,
                    "path": "restructured", "split": "fp16x2 operands, FP32 accumulate",
-                   "l2": "not flushed between the graph-replayed steps of `value`: each step streams the stored FP16 1/d (68 MB, below the 126 MB L2) and reads the FP32 lengths (136 MB) only for candidates; `l2_flushed` repeats the steps with a 256 MB write before each",
+                   "l2": "not flushed between the graph-replayed steps of `value`: each step streams the stored BF16 1/d^2 (68 MB, below the 126 MB L2) and reads the FP32 lengths (136 MB) only for candidates; `l2_flushed` repeats the steps with a 256 MB write before each",
                    "parallelism": "replicas" if ws > 1 else "single",
                    "tuning": tuning, "tuning_plain": tuning_plain},
         "secant_evals_per_s": value * P,
@@ -631,13 +631,13 @@ def run_batch(args):
     its = K
     it_s = its / (ms * 1e-3)
     hbm = peaks()[0]
-    alg = 4 * (Ptot - st1["n_excluded"] - st1["n_near"])
+    alg = 2 * (Ptot - st1["n_excluded"] - st1["n_near"])  # BF16 w per stored pair
     if rank != 0:
         return
     line = _common(args, cfg["workload"], it_s, "batch iterations/s", ms / its, its, Wm, "f32",
                    {"datasets": B, "N_min": min(Ns), "N_max": max(Ns), "n": n, "k": k, "alpha": alpha,
                     "eps": eps, "input": "BF16 data, FP32 arithmetic",
-                    "l2": "inputs larger than L2: %.2f GB of stored lengths streamed every iteration" % (4 * Ptot / 1e9)})
+                    "l2": "inputs larger than L2: %.2f GB of stored lengths streamed every iteration" % (2 * Ptot / 1e9)})
     line.update({
         "sap_iterations_per_s": it_s * B,
         "secant_evals_per_s": it_s * Ptot,

@@ -128,7 +128,7 @@ struct WPrepArgs {
     const float *nu;
     const int2 *wtiles;
     float *w;
-    __half *wh;              // FP16 1/d of the stored pairs (NaN elsewhere)
+    __nv_bfloat16 *wb;       // BF16 1/d^2 of the stored pairs (NaN elsewhere)
     float eps2_lo, eps2_hi;  // FP32 window around eps^2 (0,0: no threshold)
     double eps2;
     float beta_coef;         // sqrt(k) * eps_Y, rounded up
@@ -194,18 +194,18 @@ __global__ void __launch_bounds__(256) wprep_kernel(WPrepArgs a)
     int nnear = 0, nexcl = 0;
     unsigned long long near_bits = 0ull;  // bit p*8+q marks a near pair
     float *wt = a.w + (size_t)blockIdx.x * T * T;
-    __half *ht = a.wh + (size_t)blockIdx.x * T * T;
+    __nv_bfloat16 *ht = a.wb + (size_t)blockIdx.x * T * T;
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
         const int i = i0 + ty * 8 + p;
         float out[8];
-        __half hout[8];
+        __nv_bfloat16 hout[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int j = j0 + tx * 8 + q;
             const float dd = d2[p][q];
             float wv = __int_as_float(0x7fc00000);  // NaN: skipped by the pass
-            __half hv = __ushort_as_half((unsigned short)0x7e00);
+            __nv_bfloat16 hv = __ushort_as_bfloat16((unsigned short)0x7fc0);
             if (i < j && j < a.N) {
                 int cls;  // 0 excluded, 1 near, 2 stored
                 if (epson && dd < a.eps2_lo) cls = 0;
@@ -213,11 +213,11 @@ __global__ void __launch_bounds__(256) wprep_kernel(WPrepArgs a)
                     cls = excluded_fp64(a.X, a.n, i, j, a.eps2) ? 0 : 1;
                 else {
                     const float inv = 1.0f / dd;
-                    const float id = 1.0f / sqrtf(dd);  // 1/d for the FP16 form
+                    const float id = 1.0f / sqrtf(dd);
                     const float beta = a.beta_coef * (a.nu[i] + a.nu[j]) * id;
-                    // near: the bound exceeds the cap, or 1/d leaves the FP16 range
-                    if (beta > a.b_cap || id > 6.0e4f) cls = 1;
-                    else { cls = 2; wv = inv; hv = __float2half_rn(id); }
+                    // near: the bound exceeds the cap
+                    if (beta > a.b_cap) cls = 1;
+                    else { cls = 2; wv = inv; hv = __float2bfloat16_rn(inv); }
                 }
                 if (cls == 0) ++nexcl;
                 if (cls == 1) { ++nnear; near_bits |= 1ull << (p * 8 + q); }
@@ -229,10 +229,10 @@ __global__ void __launch_bounds__(256) wprep_kernel(WPrepArgs a)
         dst[0] = make_float4(out[0], out[1], out[2], out[3]);
         dst[1] = make_float4(out[4], out[5], out[6], out[7]);
         uint4 hp;
-        hp.x = (unsigned)__half_as_ushort(hout[0]) | ((unsigned)__half_as_ushort(hout[1]) << 16);
-        hp.y = (unsigned)__half_as_ushort(hout[2]) | ((unsigned)__half_as_ushort(hout[3]) << 16);
-        hp.z = (unsigned)__half_as_ushort(hout[4]) | ((unsigned)__half_as_ushort(hout[5]) << 16);
-        hp.w = (unsigned)__half_as_ushort(hout[6]) | ((unsigned)__half_as_ushort(hout[7]) << 16);
+        hp.x = (unsigned)__bfloat16_as_ushort(hout[0]) | ((unsigned)__bfloat16_as_ushort(hout[1]) << 16);
+        hp.y = (unsigned)__bfloat16_as_ushort(hout[2]) | ((unsigned)__bfloat16_as_ushort(hout[3]) << 16);
+        hp.z = (unsigned)__bfloat16_as_ushort(hout[4]) | ((unsigned)__bfloat16_as_ushort(hout[5]) << 16);
+        hp.w = (unsigned)__bfloat16_as_ushort(hout[6]) | ((unsigned)__bfloat16_as_ushort(hout[7]) << 16);
         *reinterpret_cast<uint4 *>(ht + (size_t)(ty * 8 + p) * T + tx * 8) = hp;
     }
     int total;
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(256) wprep_kernel(WPrepArgs a)
 constexpr int kPassStagesMax = 5;
 
 struct PassArgs {
-    const __half *wh;  // FP16 1/d tiles (tile-major upper triangle; NaN: skipped)
+    const uint16_t *wb;  // BF16 1/d^2 tiles (tile-major upper triangle; NaN: skipped)
     const int2 *wtiles;
     int ntiles;
     const float *Y;   // this basis's first component in block 0 of the block-major Y
@@ -283,7 +283,7 @@ struct PassArgs {
     int pdl;
 };
 
-// One ring stage: the FP16 1/d tile (32 KB), then for each side the basis's
+// One ring stage: the BF16 1/d^2 tile (32 KB), then for each side the basis's
 // components of the point block (block-major Y: one copy), then the 128 point
 // norms nu of each side.
 __host__ __device__ inline uint32_t pass_stage_bytes(int KY)
@@ -292,26 +292,35 @@ __host__ __device__ inline uint32_t pass_stage_bytes(int KY)
 }
 
 // Certified error of one stored pair's ratio from the tensor-core Y:
-// |r~ - r| <= beta (nu_i + nu_j) / d_ij + rho r, with the stored FP16 h =
-// 1/d_ij (relative error < 2^-11 + 2^-23, so the bound is inflated by 2^-10).
-// The same product the length preparation compares with b_cap.
-__device__ __forceinline__ float pair_bound(float beta, float nui, float nuj, float h)
+// |r~ - r| <= beta (nu_i + nu_j) / d_ij + rho r.  1/d_ij is taken as the
+// square root of the stored BF16 w = 1/d^2 (relative error of w <= 2^-8, so
+// of its root <= 2^-9 + 2^-23 with the FP32 root: inflated by 3 10^-3).  The
+// same product the length preparation compares with b_cap.
+__device__ __forceinline__ float pair_bound(float beta, float nui, float nuj, float w)
 {
-    return beta * (nui + nuj) * h * 1.001f;
+    return beta * (nui + nuj) * sqrtf(w) * 1.003f;
 }
+
+// Two BF16 values packed in a 32-bit word, widened exactly to FP32 (a BF16
+// value is the upper half of the FP32 value): integer-pipe operations only.
+__device__ __forceinline__ float bf16_lo(uint32_t x) { return __uint_as_float(x << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t x) { return __uint_as_float(x & 0xffff0000u); }
+__device__ __forceinline__ float bf16_at(const uint16_t *p) { return __uint_as_float((uint32_t)*p << 16); }
 
 // Persistent, warp-specialised pass: one block per SM.  Each block's first
 // `stages` tiles are blockIdx.x + it * gridDim.x (their constant parts are
 // fetched before the previous kernel has finished); the remaining tiles
 // are handed out from a counter, so a block that starts late (its SM still
 // busy with the previous kernels) takes fewer.  A producer warp keeps a ring of
-// `stages` shared-memory buffers filled by 1-D TMA bulk copies (the 64 KB w
-// tile and, for each side, one 512-byte segment per component of Y^T); 16
+// `stages` shared-memory buffers filled by 1-D TMA bulk copies (the 32 KB
+// BF16 w tile, for each side the basis's components of the point block and
+// the point norms); 16
 // consumer warps evaluate the tiles.  Full/empty mbarriers hand the buffers
 // over, so the loop has no block-wide barrier.  Each consumer thread owns CPT
 // adjacent columns (j) of rows spaced 16/(4/CPT) apart (32 pairs per tile);
 // K = compute width (k, or k rounded up for large k: Y's pad components are
-// zero).  q = ||y_i - y_j||^2 w is formed with packed FP32 pairs.  Every warp
+// zero).  q = ||y_i - y_j||^2 w is formed with packed FP32 pairs; w is
+// widened from BF16 by integer operations, off the FP32 pipe.  Every warp
 // bounds the minimum from its own pairs (a valid upper bound like any other),
 // tightens the global running bound with a fire-and-forget atomic, and
 // emits its candidates with one atomic per warp when it has any.
@@ -369,7 +378,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 sIJ[it] = IJ;  // published by the mbarrier completion
                 unsigned char *base = sm + (size_t)it * sbytes;
                 tc::mbar_expect_tx(&full[it], sbytes);
-                tc::bulk_g2s(base, a.wh + (size_t)t * T * T, wbytes, &full[it]);
+                tc::bulk_g2s(base, a.wb + (size_t)t * T * T, wbytes, &full[it]);
                 tc::bulk_g2s(base + wbytes + 2 * ybytes, a.nu + (size_t)IJ.x * T, T * 4, &full[it]);
                 tc::bulk_g2s(base + wbytes + 2 * ybytes + T * 4, a.nu + (size_t)IJ.y * T, T * 4, &full[it]);
             }
@@ -416,7 +425,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 sIJ[s] = IJ;  // published by the mbarrier completion below
                 unsigned char *base = sm + (size_t)s * sbytes;
                 tc::mbar_expect_tx(&full[s], sbytes);
-                tc::bulk_g2s(base, a.wh + (size_t)t * T * T, wbytes, &full[s]);
+                tc::bulk_g2s(base, a.wb + (size_t)t * T * T, wbytes, &full[s]);
                 // one copy per side: the basis's components of the point block
                 tc::bulk_g2s(base + wbytes, a.Y + (size_t)IJ.x * a.Ykt * T, ybytes, &full[s]);
                 tc::bulk_g2s(base + wbytes + ybytes, a.Y + (size_t)IJ.y * a.Ykt * T, ybytes, &full[s]);
@@ -443,16 +452,18 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     const int col0 = seg * 32 * CPT + lane * CPT;
     const float seed = load_pos_float(&a.st->seed_ub);
     float uwarp = INFINITY;  // best upper bound this warp has produced
-    for (int it = 0;; ++it) {
-        const int s = it % S;
-        if (!tc::mbar_wait_bounded(&full[s], (it / S) & 1, budget)) {
+    // ring position and barrier phase, advanced without integer division
+    int s = 0;
+    uint32_t phase = 0;
+    for (;; s = (s + 1 == S) ? 0 : s + 1, phase ^= (s == 0) ? 1u : 0u) {
+        if (!tc::mbar_wait_bounded(&full[s], phase, budget)) {
             if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
             break;
         }
         const int2 IJ = sIJ[s];
         if (IJ.x < 0) break;  // the producer has no more tiles
         const float gnow = load_pos_float(&a.st->run_ub1);  // consumed after the tile
-        const __half *hs = reinterpret_cast<const __half *>(sm + (size_t)s * sbytes);
+        const uint16_t *hs = reinterpret_cast<const uint16_t *>(sm + (size_t)s * sbytes);
         const float *yI = reinterpret_cast<const float *>(sm + (size_t)s * sbytes + wbytes);  // yI[c * T + a]
         const float *yJ = yI + T * KY;
 
@@ -474,7 +485,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
 #pragma unroll
             for (int r = 0; r < RPW; ++r) {
                 const int row = row0 + r * RSTEP;
-                const __half *hr = hs + row * T + col0;
+                const uint16_t *hr = hs + row * T + col0;
                 uint64_t s2[NPR > 0 ? NPR : 1];
 #pragma unroll
                 for (int p = 0; p < NPR; ++p) s2[p] = 0ull;
@@ -488,20 +499,19 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                         s2[p] = tc::fma2(e, e, s2[p]);
                     }
                 }
-                float wv[CPT];  // 1/d of the thread's columns
+                float wv[CPT];  // 1/d^2 of the thread's columns
                 if (CPT == 4) {
                     const uint2 raw = *reinterpret_cast<const uint2 *>(hr);
-                    const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
-                    const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
-                    wv[0] = f0.x; wv[1 % CPT] = f0.y; wv[2 % CPT] = f1.x; wv[3 % CPT] = f1.y;
+                    wv[0] = bf16_lo(raw.x); wv[1 % CPT] = bf16_hi(raw.x);
+                    wv[2 % CPT] = bf16_lo(raw.y); wv[3 % CPT] = bf16_hi(raw.y);
                 } else {
-                    const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(hr));
-                    wv[0] = f0.x; wv[1 % CPT] = f0.y;
+                    const uint32_t raw = *reinterpret_cast<const uint32_t *>(hr);
+                    wv[0] = bf16_lo(raw); wv[1 % CPT] = bf16_hi(raw);
                 }
 #pragma unroll
                 for (int p = 0; p < NPR; ++p) {
-                    const uint64_t hh = tc::pk2(wv[2 * p], wv[(2 * p + 1) % CPT]);
-                    const float2 q = tc::upk2(tc::mul2(s2[p], tc::mul2(hh, hh)));
+                    const uint64_t ww = tc::pk2(wv[2 * p], wv[(2 * p + 1) % CPT]);
+                    const float2 q = tc::upk2(tc::mul2(s2[p], ww));
                     v[r][(2 * p) % CPT] = q.x;
                     v[r][(2 * p + 1) % CPT] = q.y;
                     mymin = fminf(mymin, fminf(q.x, q.y));
@@ -520,8 +530,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                     const float e = yI[c * T + row] - yj[c];
                     sacc = fmaf(e, e, sacc);
                 }
-                const float hv = __half2float(hs[row * T + col0]);
-                v[r][0] = sacc * (hv * hv);
+                v[r][0] = sacc * bf16_at(hs + row * T + col0);
                 mymin = fminf(mymin, v[r][0]);
             }
         }
@@ -549,7 +558,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
 #pragma unroll
                     for (int q = 0; q < CPT; ++q)
                         if (v[r][q] == wmin) { prow = row0 + r * RSTEP; pcol = col0 + q; }
-                const float b = pair_bound(a.beta, nuI[prow], nuJ[pcol], __half2float(hs[prow * T + pcol]));
+                const float b = pair_bound(a.beta, nuI[prow], nuJ[pcol], bf16_at(hs + prow * T + pcol));
                 ub = (sqrtf(wmin) + b) / (1.0f - a.cert.rho) * 1.000001f;
             }
             ub = __shfl_sync(0xffffffffu, ub, src);
@@ -570,7 +579,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 for (int q = 0; q < CPT; ++q)
                     if (v[r][q] <= thc2) {
                         const int prow = row0 + r * RSTEP, pcol = col0 + q;
-                        const float th = (ut + pair_bound(a.beta, nuI[prow], nuJ[pcol], __half2float(hs[prow * T + pcol]))) *
+                        const float th = (ut + pair_bound(a.beta, nuI[prow], nuJ[pcol], bf16_at(hs + prow * T + pcol))) *
                                          1.000001f;
                         if (v[r][q] <= th * th * 1.000001f) {
                             emit |= 1u << (r * CPT + q);
@@ -670,6 +679,9 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
             valid[e] = idx < total;
             pr[e] = valid[e] ? (idx < nn ? __ldcg(a.near + idx) : __ldcg(a.cand1 + (idx - nn))) : make_int2(0, 0);
         }
+        // any earlier value of the running bound is a valid (looser) bound:
+        // read it now, so its latency overlaps the loads below
+        const float ub2 = load_pos_float(&a.st->run_ub2);
         float acc[EPW * (K + 1)];
 #pragma unroll
         for (int q = 0; q < EPW * (K + 1); ++q) acc[q] = 0.f;
@@ -689,49 +701,63 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
                 for (int c = 0; c < K; ++c) acc[e * (K + 1) + c] = fmaf(u[c], D, acc[e * (K + 1) + c]);
             }
         }
+        // lane e < EPW finishes entry e: |D|^2 in z[K], U^T D in z[0..K-1]
+        float z[K + 1];
+        constexpr int M = EPW * (K + 1);
+        if constexpr (M <= 32) {
+            // reduce-scatter (M - 1 + a few shuffles instead of 5 M), then
+            // each finishing lane gathers its entry's K + 1 totals
+            constexpr int S = M <= 8 ? 8 : M <= 16 ? 16 : 32;
+            constexpr int dup = 32 / S;  // lanes holding the same total
+            float r[S];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
+            for (int q = 0; q < S; ++q) r[q] = q < M ? acc[q < M ? q : 0] : 0.f;
+            const float t = warp_reduce_scatter<S>(r, lane);
+            const int e = lane < EPW ? lane : 0;
 #pragma unroll
-            for (int q = 0; q < EPW * (K + 1); ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-        float rr[EPW];
-        int code[EPW];
-        float mymin = INFINITY;
+            for (int c = 0; c <= K; ++c) z[c] = __shfl_sync(0xffffffffu, t, (e * (K + 1) + c) * dup);
+        } else {
 #pragma unroll
-        for (int e = 0; e < EPW; ++e) {
-            const float dd = acc[e * (K + 1) + K];
-            float zz = 0.f;
+            for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-            for (int c = 0; c < K; ++c) zz = fmaf(acc[e * (K + 1) + c], acc[e * (K + 1) + c], zz);
-            code[e] = !valid[e] ? 0 : (dd < 1e-30f ? 2 : 1);  // 2: too short for FP32
-            rr[e] = code[e] == 1 ? sqrtf(zz / dd) : INFINITY;
-            mymin = fminf(mymin, rr[e]);
+                for (int q = 0; q < M; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+#pragma unroll
+            for (int c = 0; c <= K; ++c) z[c] = acc[c];
+#pragma unroll
+            for (int e = 1; e < EPW; ++e)
+                if (lane == e)
+#pragma unroll
+                    for (int c = 0; c <= K; ++c) z[c] = acc[e * (K + 1) + c];
         }
-        const float bmin = block_min(mymin, red);
-        float U = fminf(seed, load_pos_float(&a.st->run_ub2));
+        int2 mypr = pr[0];
+        bool myvalid = valid[0];
+#pragma unroll
+        for (int e = 1; e < EPW; ++e)
+            if (lane == e) { mypr = pr[e]; myvalid = valid[e]; }
+        const float dd = z[K];
+        float zz = 0.f;
+#pragma unroll
+        for (int c = 0; c < K; ++c) zz = fmaf(z[c], z[c], zz);
+        const int code = (lane >= EPW || !myvalid) ? 0 : (dd < 1e-30f ? 2 : 1);  // 2: too short for FP32
+        const float rr = code == 1 ? sqrtf(zz / dd) : INFINITY;
+        const float bmin = block_min(rr, red);
+        float U = fminf(seed, ub2);
         if (bmin < INFINITY) {
             const float ub = cert_upper(bmin, a.cert);
             if (threadIdx.x == 0) atomic_min_pos_float(&a.st->run_ub2, ub);
             U = fminf(U, ub);
         }
         const float th = cert_emit_threshold(U, a.cert);
-        int cnt = 0;
-        if (lane == 0)
-#pragma unroll
-            for (int e = 0; e < EPW; ++e) cnt += (code[e] == 2 || (code[e] == 1 && rr[e] <= th)) ? 1 : 0;
+        const int cnt = (code == 2 || (code == 1 && rr <= th)) ? 1 : 0;
         int tot;
         const int off = block_exclusive_scan(cnt, scan, &tot);
         if (tot == 0) continue;
         if (threadIdx.x == 0) base_sh = (int)atomicAdd((unsigned int *)&a.st->cnt2, (unsigned int)tot);
         __syncthreads();
-        if (lane == 0) {
-            long long pos = (long long)(unsigned int)base_sh + off;
-#pragma unroll
-            for (int e = 0; e < EPW; ++e)
-                if (code[e] == 2 || (code[e] == 1 && rr[e] <= th)) {
-                    if (pos < a.cap2) a.cand2[pos] = pr[e];
-                    else atomicOr(&a.st->status, ST_OVERFLOW);
-                    ++pos;
-                }
+        if (cnt) {
+            const long long pos = (long long)(unsigned int)base_sh + off;
+            if (pos < a.cap2) a.cand2[pos] = mypr;
+            else atomicOr(&a.st->status, ST_OVERFLOW);
         }
         __syncthreads();
     }
@@ -1229,9 +1255,10 @@ Cert cert_pass(int n, int k, double b_cap)
     const double u = std::ldexp(1.0, -24);
     auto g = [&](double m) { return m * u / (1.0 - m * u); };
     Cert c;
-    c.A = (float)(b_cap * 1.002);  // >= every stored pair's own bound (FP16 1/d, FP32 rounding)
-    // 2^-11: the FP16 rounding of 1/d; the rest as for explicit differences
-    c.rho = (float)((std::ldexp(1.0, -11) + g(n + 2) + g(k) + 8 * u) * 1.05);
+    c.A = (float)(b_cap * 1.002);  // >= every stored pair's own bound (FP32 rounding)
+    // 2^-9: the BF16 rounding of w = 1/d^2 (halved by the square root); the
+    // rest as for explicit differences
+    c.rho = (float)((std::ldexp(1.0, -9) + g(n + 2) + g(k) + 8 * u) * 1.05);
     return c;
 }
 
@@ -1289,7 +1316,7 @@ sap_status classify(sap_handle h, int k)
     a.nu = r.nu;
     a.wtiles = r.wtiles;
     a.w = r.w;
-    a.wh = reinterpret_cast<__half *>(r.wh);
+    a.wb = reinterpret_cast<__nv_bfloat16 *>(r.wb);
     a.eps2_lo = handle_eps2_lo(h);
     a.eps2_hi = handle_eps2_hi(h);
     a.eps2 = handle_eps2(h);
@@ -1391,7 +1418,7 @@ sap_status restructured_prepare(sap_handle h)
         RCK(cudaMalloc(&r.wtiles, t.size() * sizeof(int2)));
         RCK(cudaMemcpy(r.wtiles, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice));
         RCK(cudaMalloc(&r.w, (size_t)r.nwtiles * T * T * sizeof(float)));
-        RCK(cudaMalloc(&r.wh, (size_t)r.nwtiles * T * T * sizeof(uint16_t)));
+        RCK(cudaMalloc(&r.wb, (size_t)r.nwtiles * T * T * sizeof(uint16_t)));
         const long long P = (long long)N * (N - 1) / 2;
         r.near_cap = (unsigned int)std::min<long long>(P + 64, 1ll << 24);
         RCK(cudaMalloc(&r.near, (size_t)r.near_cap * sizeof(int2)));
@@ -1537,7 +1564,7 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
     cudaEvent_t ea, eb;
     {
         PassArgs p;
-        p.wh = reinterpret_cast<const __half *>(r.wh);
+        p.wb = r.wb;
         p.wtiles = r.wtiles;
         p.ntiles = r.nwtiles;
         p.Y = b.Y;
@@ -1780,7 +1807,7 @@ void restructured_free(sap_handle h)
     RestrState &r = restr_state(h);
     dfree(r.Xhi); dfree(r.Xlo); dfree(r.center); dfree(r.nu); dfree(r.w); dfree(r.wtiles);
     dfree(r.near); dfree(r.counters); dfree(r.Uhi); dfree(r.Ulo); dfree(r.Y); dfree(r.Ypart);
-    dfree(r.near_w); dfree(r.xn); dfree(r.Ydh); dfree(r.Ydl); dfree(r.wh);
+    dfree(r.near_w); dfree(r.xn); dfree(r.Ydh); dfree(r.Ydl); dfree(r.wb);
 }
 
 void restructured_stats(sap_handle h, sap_stats *out)

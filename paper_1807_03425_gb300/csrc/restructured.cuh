@@ -20,9 +20,9 @@ struct RestrState {
     // inverse squared lengths, tile-major upper triangle (kTile x kTile tiles);
     // NaN marks a pair the pass skips (invalid, excluded, or near)
     float *w = nullptr;
-    // the same tiles as FP16 1/d_ij (raw half bits), the form the pass streams
+    // the same tiles as BF16 w_ij (raw bits), the form the pass streams
     // (2 bytes per pair); NaN where w is NaN
-    uint16_t *wh = nullptr;
+    uint16_t *wb = nullptr;
     int2 *wtiles = nullptr;   // (I, J) per tile, I <= J
     int nwtiles = 0;
     int2 *near = nullptr;     // pairs the pass skips, evaluated by the refine tier

@@ -159,6 +159,37 @@ __device__ __forceinline__ bool better(double r, int i, int j, double rb, int ib
     return j < jb;
 }
 
+// Reduce-scatter of S per-lane values (S a power of two, 8..32) over a warp:
+// halving exchanges (each level adds half of the remaining values), then
+// butterfly adds; S - 1 + log2(32/S) additions instead of 5 per value.  On
+// return v[0] of lane L holds the warp total of entry rs_index<S>(L).
+template <int S>
+__device__ __forceinline__ int rs_index(int lane)
+{
+    constexpr int b = S == 8 ? 3 : S == 16 ? 4 : 5;
+    return (lane >> (5 - b)) & (S - 1);
+}
+
+template <int S, typename V>
+__device__ __forceinline__ V warp_reduce_scatter(V (&v)[S], int lane)
+{
+    static_assert(S == 8 || S == 16 || S == 32, "reduce-scatter width");
+#pragma unroll
+    for (int lvl = 0; (S >> lvl) > 1; ++lvl) {
+        const int half = (S >> lvl) / 2, o = 16 >> lvl;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const V send = up ? v[i] : v[i + half];
+            const V keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 / S; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    return v[0];
+}
+
 __device__ __forceinline__ float warp_min(float v)
 {
 #pragma unroll

@@ -84,37 +84,6 @@ __device__ __forceinline__ void block_sum_multi(V (&v)[M], V *scratch /* NW*M */
     __syncthreads();
 }
 
-// Reduce-scatter of S per-lane values (S a power of two, 8..32) over a warp:
-// halving exchanges (each level adds half of the remaining values), then
-// butterfly adds; S - 1 + log2(32/S) additions instead of 5 per value.  On
-// return v[0] of lane L holds the warp total of entry rs_index<S>(L).
-template <int S>
-__device__ __forceinline__ int rs_index(int lane)
-{
-    constexpr int b = S == 8 ? 3 : S == 16 ? 4 : 5;
-    return (lane >> (5 - b)) & (S - 1);
-}
-
-template <int S>
-__device__ __forceinline__ double warp_reduce_scatter(double (&v)[S], int lane)
-{
-    static_assert(S == 8 || S == 16 || S == 32, "reduce-scatter width");
-#pragma unroll
-    for (int lvl = 0; (S >> lvl) > 1; ++lvl) {
-        const int half = (S >> lvl) / 2, o = 16 >> lvl;
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < half; ++i) {
-            const double send = up ? v[i] : v[i + half];
-            const double keep = up ? v[i + half] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-#pragma unroll
-    for (int o = 16 / S; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
-    return v[0];
-}
-
 // d2 = |D|^2 and zz = |U^T D|^2 from per-lane partial sums v[0..K-1] (U^T D)
 // and v[K] (|D|^2), delivered to every lane.
 template <int K>

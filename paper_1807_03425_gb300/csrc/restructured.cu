@@ -483,38 +483,46 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 }
             }
 #pragma unroll
-            for (int r = 0; r < RPW; ++r) {
-                const int row = row0 + r * RSTEP;
-                const uint16_t *hr = hs + row * T + col0;
-                uint64_t s2[NPR > 0 ? NPR : 1];
+            for (int r0 = 0; r0 < RPW; r0 += 2) {
+                uint64_t s2[2][NPR > 0 ? NPR : 1];
 #pragma unroll
-                for (int p = 0; p < NPR; ++p) s2[p] = 0ull;
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int p = 0; p < NPR; ++p) s2[h][p] = 0ull;
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
-                    const float yc = yI[c * T + row];  // broadcast
-                    const uint64_t yy = tc::pk2(yc, yc);
+                    const float yca = yI[c * T + row0 + r0 * RSTEP];        // broadcast
+                    const float ycb = yI[c * T + row0 + (r0 + 1) * RSTEP];  // broadcast
+                    const uint64_t yya = tc::pk2(yca, yca), yyb = tc::pk2(ycb, ycb);
 #pragma unroll
                     for (int p = 0; p < NPR; ++p) {
-                        const uint64_t e = tc::sub2(yy, yj2[p][c]);
-                        s2[p] = tc::fma2(e, e, s2[p]);
+                        const uint64_t ea = tc::sub2(yya, yj2[p][c]);
+                        const uint64_t eb = tc::sub2(yyb, yj2[p][c]);
+                        s2[0][p] = tc::fma2(ea, ea, s2[0][p]);
+                        s2[1][p] = tc::fma2(eb, eb, s2[1][p]);
                     }
                 }
-                float wv[CPT];  // 1/d^2 of the thread's columns
-                if (CPT == 4) {
-                    const uint2 raw = *reinterpret_cast<const uint2 *>(hr);
-                    wv[0] = bf16_lo(raw.x); wv[1 % CPT] = bf16_hi(raw.x);
-                    wv[2 % CPT] = bf16_lo(raw.y); wv[3 % CPT] = bf16_hi(raw.y);
-                } else {
-                    const uint32_t raw = *reinterpret_cast<const uint32_t *>(hr);
-                    wv[0] = bf16_lo(raw); wv[1 % CPT] = bf16_hi(raw);
-                }
 #pragma unroll
-                for (int p = 0; p < NPR; ++p) {
-                    const uint64_t ww = tc::pk2(wv[2 * p], wv[(2 * p + 1) % CPT]);
-                    const float2 q = tc::upk2(tc::mul2(s2[p], ww));
-                    v[r][(2 * p) % CPT] = q.x;
-                    v[r][(2 * p + 1) % CPT] = q.y;
-                    mymin = fminf(mymin, fminf(q.x, q.y));
+                for (int h = 0; h < 2; ++h) {
+                    const int r = r0 + h;
+                    const uint16_t *hr = hs + (row0 + r * RSTEP) * T + col0;
+                    float wv[CPT];  // 1/d^2 of the thread's columns
+                    if (CPT == 4) {
+                        const uint2 raw = *reinterpret_cast<const uint2 *>(hr);
+                        wv[0] = bf16_lo(raw.x); wv[1 % CPT] = bf16_hi(raw.x);
+                        wv[2 % CPT] = bf16_lo(raw.y); wv[3 % CPT] = bf16_hi(raw.y);
+                    } else {
+                        const uint32_t raw = *reinterpret_cast<const uint32_t *>(hr);
+                        wv[0] = bf16_lo(raw); wv[1 % CPT] = bf16_hi(raw);
+                    }
+#pragma unroll
+                    for (int p = 0; p < NPR; ++p) {
+                        const uint64_t ww = tc::pk2(wv[2 * p], wv[(2 * p + 1) % CPT]);
+                        const float2 q = tc::upk2(tc::mul2(s2[h][p], ww));
+                        v[r][(2 * p) % CPT] = q.x;
+                        v[r][(2 * p + 1) % CPT] = q.y;
+                        mymin = fminf(mymin, fminf(q.x, q.y));
+                    }
                 }
             }
         } else {

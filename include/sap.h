@@ -372,7 +372,9 @@ typedef struct {
                                        needs its predecessor's output); 0: ordinary launches */
     int32_t refine_tier;            /* second tier of the restructured form: 1 double-float Y
                                        (O(k) per pair), 0 explicit differences (O(n k) per pair),
-                                       -1 chosen by n (double-float above n = 256) */
+                                       2 explicit differences fused into the FP64 recheck (one
+                                       launch fewer; n <= 256, else as 0), -1 chosen by n
+                                       (double-float above n = 256) */
     double us_per_iteration;        /* measured by sap_autotune; 0 when set by hand */
 } sap_tuning;
 

@@ -272,6 +272,14 @@ sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only)
         u.grid = std::min(h->tune.su_blocks > 0 ? h->tune.su_blocks : h->sms, kRecheckBlocks);
         u.work = h->work; u.st = h->st; u.hist = h->hist; u.argmin = h->am; u.seed_cert = c32;
         u.pdl = h->tune.pdl;
+        if (h->path == SAP_PLAIN) {
+            u.fused = 0; u.near = nullptr; u.n_near = 0; u.cert2 = c32;
+        } else {
+            BasisView bv;
+            bv.k = h->k;
+            bv.cand1 = h->cand1;
+            restructured_fuse_args(h, bv, u);
+        }
         Timed t(h, K_UPDATE);
         CK(launch_select_update(u, s));
     }
@@ -705,7 +713,7 @@ sap_status sap_set_tuning(sap_handle h, const sap_tuning *in)
         in->explicit_blocks_per_sm < 1 || in->explicit_blocks_per_sm > 8 || in->update_blocks < 0 ||
         in->update_blocks > kRecheckBlocks || in->plain_blocks_per_sm < 1 || in->plain_blocks_per_sm > 8 ||
         (in->programmatic_launch != 0 && in->programmatic_launch != 1) || in->refine_tier < -1 ||
-        in->refine_tier > 1)
+        in->refine_tier > 2)
         return fail(h, SAP_E_ARG, "tuning parameter out of range");
     CK(cudaStreamSynchronize(h->stream));
     TuneParams p;

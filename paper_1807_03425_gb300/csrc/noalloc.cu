@@ -204,6 +204,10 @@ extern "C" sap_status sap_min_secant_noalloc(const float *X, int64_t N, int32_t 
     q.argmin = g->argmin;
     q.seed_cert = a.cert;
     q.pdl = 0;
+    q.fused = 0;
+    q.near = nullptr;
+    q.n_near = 0;
+    q.cert2 = a.cert;
     if (launch_select_update(q, s) != cudaSuccess) return SAP_E_CUDA;
 
     ProbState st;

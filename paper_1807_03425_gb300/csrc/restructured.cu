@@ -1594,7 +1594,10 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         if (eb) cudaEventRecord(eb, s);
         handle_push_timing(h, 1, ea, eb);
     }
-    if (!restructured_uses_refine(h)) {
+    const int tier = restructured_tier(h);
+    if (tier == 2) {
+        // the explicit tier runs inside the FP64 recheck (restructured_fuse_args)
+    } else if (tier == 0) {
         ExplArgs x;
         x.X = handle_x32(h);
         x.N = (int)handle_n_points(h);
@@ -1798,16 +1801,37 @@ sap_status restructured_project_df(sap_handle h, float *Yh_out, float *Yl_out, i
     return SAP_OK;
 }
 
-bool restructured_uses_refine(sap_handle h)
+int restructured_tier(sap_handle h)
 {
     const int t = handle_tune(h).refine;
-    return t < 0 ? handle_n_dim(h) > 256 : t != 0;
+    const int n = handle_n_dim(h);
+    if (t == 2) return explicit_uses_df(n) ? 0 : 2;
+    return (t < 0 ? n > 256 : t != 0) ? 1 : 0;
+}
+
+bool restructured_uses_refine(sap_handle h) { return restructured_tier(h) == 1; }
+
+void restructured_fuse_args(sap_handle h, const BasisView &b, SelectUpdateArgs &u)
+{
+    u.fused = 0;
+    u.near = nullptr;
+    u.n_near = 0;
+    u.cert2 = cert_explicit(handle_n_dim(h), b.k);
+    if (restructured_tier(h) != 2) return;
+    RestrState &r = restr_state(h);
+    u.fused = 1;
+    u.near = r.near;
+    u.n_near = r.n_near;
+    u.list = b.cand1;
+    u.which = 1;
 }
 
 int restructured_kernels_per_iteration(sap_handle h)
 {
-    // product (+ slice sum), pass, explicit tier or (double-float product + refine tier)
-    return 3 + (restructured_uses_refine(h) ? 1 : 0) + (restr_state(h).ksplit > 1 ? 1 : 0);
+    // product (+ slice sum), pass, and the explicit tier, or the double-float
+    // product + refine tier, or nothing (fused into the FP64 recheck)
+    const int tier = restructured_tier(h);
+    return 2 + (tier == 1 ? 2 : tier == 0 ? 1 : 0) + (restr_state(h).ksplit > 1 ? 1 : 0);
 }
 
 void restructured_free(sap_handle h)

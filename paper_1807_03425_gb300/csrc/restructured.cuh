@@ -96,7 +96,15 @@ sap_status restructured_basis_alloc(sap_handle h);      // U operands and Y for 
 sap_status restructured_upload_basis(sap_handle h, const double *U); // n x k col-major
 sap_status restructured_enqueue(sap_handle h, double alpha);
 int restructured_kernels_per_iteration(sap_handle h);
-bool restructured_uses_refine(sap_handle h);  // second tier: double-float refine (else explicit differences)
+// Second tier of the restructured form: 0 explicit differences (own
+// launch), 1 double-float Y + refine, 2 explicit differences fused into the
+// FP64 recheck (tuning value 2; only where the plain FP32 explicit tier
+// applies, n <= 256, else 0).
+int restructured_tier(sap_handle h);
+bool restructured_uses_refine(sap_handle h);
+// Fills the fused-tier fields of the FP64 recheck of basis b (fused = 0
+// unless the tier is 2; then list/which name the pass's candidates).
+void restructured_fuse_args(sap_handle h, const BasisView &b, SelectUpdateArgs &u);
 void restructured_free(sap_handle h);
 void restructured_stats(sap_handle h, sap_stats *out);
 sap_status restructured_set_bound(sap_handle h, double b_cap);

@@ -323,6 +323,14 @@ struct SelectUpdateArgs {
     int2 *argmin;          // hist_cap entries
     Cert seed_cert;        // error model of the seed evaluation
     int pdl;               // launch with programmatic stream serialization
+    // fused second tier (restructured form): phase 1 takes the near pairs and
+    // the pass's candidates (list, count in st->cnt1), filters each by
+    // explicit FP32 differences under cert2 and evaluates the survivors in
+    // FP64 at once (FP32 data only)
+    int fused;
+    const int2 *near;
+    int n_near;
+    Cert cert2;
 };
 cudaError_t launch_select_update(const SelectUpdateArgs &a, cudaStream_t s);
 

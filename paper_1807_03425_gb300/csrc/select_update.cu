@@ -174,11 +174,9 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
 
     // ---------------- phase 1: FP64 recheck of the candidate list ----------
     {
-        unsigned int cnt = a.which == 1 ? (unsigned int)st->cnt1 : (unsigned int)st->cnt2;
-        if (cnt > a.cap) cnt = a.cap;
         Partial best = {INFINITY, 0x7fffffff, 0x7fffffff};
-        for (unsigned int e = blockIdx.x + gridDim.x * w; e < cnt; e += gridDim.x * NW) {
-            const int2 ij = a.list[e];
+        // the FP64 evaluation of one pair by the warp; keeps the best
+        auto eval64 = [&](int2 ij) {
             double v[K + 1];
 #pragma unroll
             for (int q = 0; q <= K; ++q) v[q] = 0.0;
@@ -193,9 +191,116 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             }
             double zz, d2;
             warp_ratio_parts<K>(v, lane, zz, d2);
-            if (d2 == 0.0 || d2 < a.eps2) continue;
+            if (d2 == 0.0 || d2 < a.eps2) return;
             const double q = zz / d2;  // squared ratio
             if (better_q(q, ij.x, ij.y, best.r, best.i, best.j)) best = Partial{q, ij.x, ij.y};
+        };
+        bool fused = false;
+        if constexpr (sizeof(TX) == 4) fused = a.fused != 0;  // FP32 data only
+        if (fused) {
+            // Fused second tier: the near pairs and the pass's candidates,
+            // each first from explicit FP32 differences (the explicit tier's
+            // arithmetic and error model), then, if it can still be the
+            // argmin against the running bound, in FP64 by the same warp.
+            // The bound is valid whenever it is read, so no list of
+            // survivors and no second launch are needed.
+            constexpr int EPW = 4;                 // pairs per warp per round
+            constexpr int KU = (K + 3) / 4 * 4;    // U32 row stride covers KU
+            constexpr int M = EPW * (K + 1);
+            unsigned int c1 = *(volatile const unsigned int *)&st->cnt1;
+            if (c1 > a.cap) c1 = a.cap;
+            const long long nn = a.n_near, total = nn + c1;
+            const float seed = load_pos_float(&st->seed_ub);
+            const float *X32 = static_cast<const float *>(a.X);
+            for (long long base = ((long long)blockIdx.x * NW + w) * EPW; base < total;
+                 base += (long long)gridDim.x * NW * EPW) {
+                int2 pr[EPW];
+                bool valid[EPW];
+#pragma unroll
+                for (int e = 0; e < EPW; ++e) {
+                    const long long idx = base + e;
+                    valid[e] = idx < total;
+                    pr[e] = valid[e] ? (idx < nn ? __ldcg(a.near + idx) : __ldcg(a.list + (idx - nn))) : make_int2(0, 0);
+                }
+                const float ub2 = load_pos_float(&st->run_ub2);
+                float acc[M];
+#pragma unroll
+                for (int q = 0; q < M; ++q) acc[q] = 0.f;
+#pragma unroll 2
+                for (int l = lane; l < n; l += 32) {
+                    float u[KU];
+#pragma unroll
+                    for (int c = 0; c < KU; c += 4) {
+                        const float4 t = __ldcg(reinterpret_cast<const float4 *>(a.U32 + (size_t)l * a.KP + c));
+                        u[c] = t.x; u[c + 1] = t.y; u[c + 2] = t.z; u[c + 3] = t.w;
+                    }
+#pragma unroll
+                    for (int e = 0; e < EPW; ++e) {
+                        const float D = X32[(size_t)pr[e].x * n + l] - X32[(size_t)pr[e].y * n + l];
+                        acc[e * (K + 1) + K] = fmaf(D, D, acc[e * (K + 1) + K]);
+#pragma unroll
+                        for (int c = 0; c < K; ++c) acc[e * (K + 1) + c] = fmaf(u[c], D, acc[e * (K + 1) + c]);
+                    }
+                }
+                // lane e < EPW finishes pair e
+                float z[K + 1];
+                if constexpr (M <= 32) {
+                    constexpr int S = M <= 8 ? 8 : M <= 16 ? 16 : 32;
+                    constexpr int dup = 32 / S;
+                    float r[S];
+#pragma unroll
+                    for (int q = 0; q < S; ++q) r[q] = q < M ? acc[q < M ? q : 0] : 0.f;
+                    const float t = warp_reduce_scatter<S>(r, lane);
+                    const int e = lane < EPW ? lane : 0;
+#pragma unroll
+                    for (int c = 0; c <= K; ++c) z[c] = __shfl_sync(0xffffffffu, t, (e * (K + 1) + c) * dup);
+                } else {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int q = 0; q < M; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+#pragma unroll
+                    for (int c = 0; c <= K; ++c) z[c] = acc[c];
+#pragma unroll
+                    for (int e = 1; e < EPW; ++e)
+                        if (lane == e)
+#pragma unroll
+                            for (int c = 0; c <= K; ++c) z[c] = acc[e * (K + 1) + c];
+                }
+                int2 mypr = pr[0];
+                bool myvalid = valid[0];
+#pragma unroll
+                for (int e = 1; e < EPW; ++e)
+                    if (lane == e) { mypr = pr[e]; myvalid = valid[e]; }
+                const float dd = z[K];
+                float zz = 0.f;
+#pragma unroll
+                for (int c = 0; c < K; ++c) zz = fmaf(z[c], z[c], zz);
+                const int code = (lane >= EPW || !myvalid) ? 0 : (dd < 1e-30f ? 2 : 1);  // 2: too short for FP32
+                const float rr = code == 1 ? sqrtf(zz / dd) : INFINITY;
+                const float wmin = warp_min(rr);
+                float U = fminf(seed, ub2);
+                if (wmin < INFINITY) {
+                    const float ub = cert_upper(wmin, a.cert2);
+                    if (lane == 0) atomic_min_pos_float(&st->run_ub2, ub);
+                    U = fminf(U, ub);
+                }
+                const float th = cert_emit_threshold(U, a.cert2);
+                unsigned int m = __ballot_sync(0xffffffffu, code == 2 || (code == 1 && rr <= th));
+                if (m && lane == 0) atomicAdd((unsigned int *)&st->cnt2, (unsigned int)__popc(m));
+                while (m) {
+                    const int e = __ffs(m) - 1;
+                    m &= m - 1;
+                    int2 ij;
+                    ij.x = __shfl_sync(0xffffffffu, mypr.x, e);
+                    ij.y = __shfl_sync(0xffffffffu, mypr.y, e);
+                    eval64(ij);
+                }
+            }
+        } else {
+            unsigned int cnt = a.which == 1 ? (unsigned int)st->cnt1 : (unsigned int)st->cnt2;
+            if (cnt > a.cap) cnt = a.cap;
+            for (unsigned int e = blockIdx.x + gridDim.x * w; e < cnt; e += gridDim.x * NW) eval64(a.list[e]);
         }
         if (lane == 0) sh.wb[w] = best;
         __syncthreads();

@@ -183,6 +183,10 @@ SelectUpdateArgs update_args(sap_handle h, SweepState &sw, SweepBasis &b, double
     u.argmin = b.am;
     u.seed_cert = handle_seed_cert(u.n, b.k);
     u.pdl = handle_tune(h).pdl;
+    BasisView v;
+    v.k = b.k;
+    v.cand1 = b.cand1;
+    restructured_fuse_args(h, v, u);
     return u;
 }
 

@@ -153,6 +153,10 @@ __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgsF32 a)
 // FP64 form (FP64 datasets): one thread per pair of a 16 x 16 block, X rows
 // read through the cache.  The ratio is exact up to FP64 rounding; it is
 // rounded to FP32 for the selection, hence the error model {0, 2^-23}.
+// K is the basis width for k <= 8 (exactly k FP64 FMAs per coordinate:
+// FP64 issue, not latency, is what a block of this kernel waits on), else
+// kMaxK with the columns past k skipped.
+template <int K>
 __global__ void __launch_bounds__(256) plain_f64_kernel(PlainArgsF64 a)
 {
     __shared__ float red[32];
@@ -167,25 +171,25 @@ __global__ void __launch_bounds__(256) plain_f64_kernel(PlainArgsF64 a)
         float rt = INFINITY;
         if (cd) {
             double d2 = 0.0;
-            double z[kMaxK];
+            double z[K];
 #pragma unroll
-            for (int c = 0; c < kMaxK; ++c) z[c] = 0.0;
+            for (int c = 0; c < K; ++c) z[c] = 0.0;
             const double *xi = a.X + (size_t)i * a.n;
             const double *xj = a.X + (size_t)j * a.n;
             for (int l = 0; l < a.n; ++l) {
                 const double D = xi[l] - xj[l];
                 d2 = fma(D, D, d2);
 #pragma unroll
-                for (int c = 0; c < kMaxK; ++c)
-                    if (c < a.k) z[c] = fma(a.U64[(size_t)c * a.n + l], D, z[c]);
+                for (int c = 0; c < K; ++c)
+                    if (K <= 8 || c < a.k) z[c] = fma(a.U64[(size_t)c * a.n + l], D, z[c]);
             }
             if (d2 == 0.0 || d2 < a.eps2) {
                 cd = 0;
             } else {
                 double zz = 0.0;
 #pragma unroll
-                for (int c = 0; c < kMaxK; ++c)
-                    if (c < a.k) zz = fma(z[c], z[c], zz);
+                for (int c = 0; c < K; ++c)
+                    if (K <= 8 || c < a.k) zz = fma(z[c], z[c], zz);
                 rt = (float)sqrt(zz / d2);
             }
         }
@@ -236,7 +240,13 @@ cudaError_t launch_plain_f32(const PlainArgsF32 &a, cudaStream_t s)
 
 cudaError_t launch_plain_f64(const PlainArgsF64 &a, cudaStream_t s)
 {
-    plain_f64_kernel<<<a.grid, 256, 0, s>>>(a);
+    switch (a.k) {
+#define SAP_CASE(KK) case KK: plain_f64_kernel<KK><<<a.grid, 256, 0, s>>>(a); break;
+        SAP_CASE(1) SAP_CASE(2) SAP_CASE(3) SAP_CASE(4)
+        SAP_CASE(5) SAP_CASE(6) SAP_CASE(7) SAP_CASE(8)
+#undef SAP_CASE
+    default: plain_f64_kernel<kMaxK><<<a.grid, 256, 0, s>>>(a); break;
+    }
     return cudaGetLastError();
 }
 

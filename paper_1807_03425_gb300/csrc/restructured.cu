@@ -668,7 +668,7 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
     // candidates); otherwise one segment covering both.
     const float seed = load_pos_float(&a.st->seed_ub);
     for (int seg = 0; seg < (a.pdl ? 2 : 1); ++seg) {
-    long long nn = a.n_near, total = a.n_near;
+    long long nn = a.n_near, total = a.n_near, lim = a.n_near;
     if (seg == 1 || !a.pdl) {
         grid_dep_wait();
         grid_dep_launch();
@@ -676,16 +676,25 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
         if (c1 > a.cap1) c1 = a.cap1;
         nn = a.pdl ? 0 : a.n_near;
         total = nn + c1;
+        lim = nn + a.cap1;  // bound of the lists' storage
     }
-    for (long long base = (long long)blockIdx.x * 8 * EPW; base < total;
+    // A round's pairs are read up to the lists' storage bound before the
+    // count is needed (entries past the count are read but not used), so the
+    // count's load and the pairs' loads overlap.
+    for (long long base = (long long)blockIdx.x * 8 * EPW; base < lim;
          base += (long long)gridDim.x * 8 * EPW) {
         int2 pr[EPW];
         bool valid[EPW];
 #pragma unroll
         for (int e = 0; e < EPW; ++e) {
             const long long idx = base + warp * EPW + e;
-            valid[e] = idx < total;
-            pr[e] = valid[e] ? (idx < nn ? __ldcg(a.near + idx) : __ldcg(a.cand1 + (idx - nn))) : make_int2(0, 0);
+            pr[e] = idx < lim ? (idx < nn ? __ldcg(a.near + idx) : __ldcg(a.cand1 + (idx - nn))) : make_int2(0, 0);
+        }
+        if (base >= total) break;  // uniform over the block
+#pragma unroll
+        for (int e = 0; e < EPW; ++e) {
+            valid[e] = base + warp * EPW + e < total;
+            if (!valid[e]) pr[e] = make_int2(0, 0);
         }
         // any earlier value of the running bound is a valid (looser) bound:
         // read it now, so its latency overlaps the loads below

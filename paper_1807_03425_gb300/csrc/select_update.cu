@@ -300,7 +300,13 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         } else {
             unsigned int cnt = a.which == 1 ? (unsigned int)st->cnt1 : (unsigned int)st->cnt2;
             if (cnt > a.cap) cnt = a.cap;
-            for (unsigned int e = blockIdx.x + gridDim.x * w; e < cnt; e += gridDim.x * NW) eval64(a.list[e]);
+            // the pair is read (within the list's storage) before the count
+            // is needed, so the two loads overlap
+            for (unsigned int e = blockIdx.x + gridDim.x * w; e < a.cap; e += gridDim.x * NW) {
+                const int2 ij = a.list[e];
+                if (e >= cnt) break;  // uniform over the warp
+                eval64(ij);
+            }
         }
         if (lane == 0) sh.wb[w] = best;
         __syncthreads();
@@ -320,6 +326,22 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
 
     // ---------------- phase 2: argmin, record, update ----------------------
     using WT = TX;  // working precision of the pivot, MGS and rotation
+    // this thread's row of the current basis (n <= SB, k <= 8), loaded now so
+    // that the loads overlap the argmin over the blocks' results
+    constexpr int KR = K <= 8 ? K : 1;
+    WT urow[KR];
+    const bool have_row = K <= 8 && n <= SB && tid < n;
+    if (have_row) {
+#pragma unroll
+        for (int c = 0; c < KR; ++c)
+            urow[c] = c < kk ? (sizeof(WT) == 8 ? (WT)a.U64[(size_t)c * n + tid] : (WT)a.U32[(size_t)tid * a.KP + c])
+                             : (WT)0;
+    }
+    // the basis entry (l, c) as the working precision reads it
+    auto ucol = [&](int l, int c) -> WT {
+        if (K <= 8 && have_row && l == tid) return urow[c < KR ? c : 0];
+        return sizeof(WT) == 8 ? (WT)a.U64[(size_t)c * n + l] : (WT)a.U32[(size_t)l * a.KP + c];
+    };
     if (w == 0) {
         Partial b = {INFINITY, 0x7fffffff, 0x7fffffff};
         for (int p = lane; p < (int)gridDim.x; p += 32) {
@@ -423,7 +445,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             v[K] += D * D;
 #pragma unroll
             for (int c = 0; c < K; ++c)
-                if (c < kk) v[c] += (sizeof(WT) == 8 ? (WT)a.U64[(size_t)c * n + l] : (WT)a.U32[(size_t)l * a.KP + c]) * D;
+                if (c < kk) v[c] += ucol(l, c) * D;
         }
         WT *scr = sizeof(WT) == 8 ? (WT *)sh.red_d : (WT *)sh.red_f;
         warp_sum_multi<WT, K + 1>(v);
@@ -513,7 +535,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             WT u[K];
 #pragma unroll
             for (int c = 0; c < K; ++c)
-                u[c] = c < kk ? (sizeof(WT) == 8 ? (WT)a.U64[(size_t)c * n + l] : (WT)a.U32[(size_t)l * a.KP + c]) : (WT)0;
+                u[c] = c < kk ? ucol(l, c) : (WT)0;
             WT v0 = 0;
 #pragma unroll
             for (int c = 0; c < K; ++c) v0 += u[c] * sh.cw[c];
@@ -598,15 +620,15 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
     }
     __syncthreads();
     if (w == 0) {
-        // E = G - I; the series needs max|E| small
-        double emax = 0.0;
+        // E = G - I; the series needs max|E| <= 1e-6 (a vote, not an FP64
+        // max-reduction; NaN entries are ignored as fmax would ignore them)
+        bool small = true;
         for (int e = lane; e < kk * kk; e += 32) {
             const int p = e / kk, q = e % kk;
-            if (q >= p) emax = fmax(emax, fabs(sh.G[p][q] - (p == q ? 1.0 : 0.0)));
+            if (q >= p && fabs(sh.G[p][q] - (p == q ? 1.0 : 0.0)) > 1e-6) small = false;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-        if (Shared<TX, K>::KS == K && emax <= 1e-6) {
+        small = __all_sync(0xffffffffu, small);
+        if (Shared<TX, K>::KS == K && small) {
             // S1 = triu(E) with the diagonal halved (FP64), S2 = the same of
             // -S1^T S1, R = S1 + S2, and (I + R)^-1 = I - S1 + [S1^2 - S2] +
             // O(|E|^3).  The bracket is second order (<= k^2 1e-12): its FP32
@@ -631,7 +653,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
                 const float second = sq + (q > p ? tt : 0.5f * tt);                      // S1^2 - S2
                 sh.Ri[p][q] = (p == q ? 1.0 : 0.0) - sh.T1[p][q] + (double)second;
             }
-        } else if (emax <= 1e-6) {
+        } else if (small) {
             // R1 = triu(E) with the diagonal halved; R2 from -R1^T R1 the same
             // way; R = R1 + R2; (I + R)^-1 = I - R + R^2 (error O(|E|^3))
             for (int e = lane; e < kk * kk; e += 32) {

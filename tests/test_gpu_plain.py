@@ -29,6 +29,19 @@ def test_c1_fp64_lockstep(P):
             U, _ = lockstep(s, X, U, cfg["alpha"])
 
 
+@pytest.mark.parametrize("k", [1, 6, 11])
+def test_fp64_plain_lockstep_widths(P, k):
+    """FP64 data at other basis widths: the pass is compiled per width for
+    k <= 8 and generic above (k = 11); N = 150 (ragged 16 x 16 blocks) in
+    R^24, lock-step with the oracle."""
+    X = W.moment_curve(150, 12, 21 + k, np.float64)
+    U = W.random_basis(24, k, 40 + k)
+    with P.Sap(X) as s:
+        s.set_path("plain")
+        for _ in range(6):
+            U, _ = lockstep(s, X, U, 0.01)
+
+
 def test_c1_fp64_free_run_history(P):
     """1000 iterations in captured graphs; the history must follow the
     oracle's exactly up to the first near-tie of the argmin."""

@@ -315,6 +315,30 @@ def test_softmin_ascent_step_stays_orthonormal():
     assert O.softmin(X, Un, 0.05, grad=False) > L
 
 
+def test_softmin_ascent_step_hand_cases(hand):
+    """Closed forms of one Grassmann ascent step on a single secant, where
+    dL/dU has a non-zero radial part U(U^T G): the result fails if the
+    tangent projection is dropped, if the step is normalised by ||G||
+    instead of ||G_R||, or if qf returns a negative diagonal of R."""
+    for case in hand["ascent_cases"]:
+        X = np.array(case["X"], dtype=np.float64)
+        U = np.array(case["U"], dtype=np.float64)
+        want = np.array([[_ev(e) for e in row] for row in case["U_new"]])
+        Un, L, nr = O.softmin_ascent_step(X, U, case["tau"], _ev(case["eta"]))
+        np.testing.assert_allclose(Un, want, rtol=0, atol=1e-15, err_msg=case["name"])
+        assert abs(L - _ev(case["L"])) <= 1e-15, case["name"]
+        assert abs(nr - _ev(case["norm_GR"])) <= 4e-15, case["name"]  # a few ulps
+
+
+def test_qf_hand_case():
+    """qf of the rows (3,4,0), (1,0,2): q1 = (3,4,0)/5; the second row minus
+    its projection 3/5 q1 is (16,-12,50)/25, of length 2 sqrt(29)/5, so
+    q2 = (8,-6,25)/(5 sqrt(29)); both R diagonal entries positive."""
+    Q = O.qf(np.array([[3.0, 4.0, 0.0], [1.0, 0.0, 2.0]]))
+    want = np.array([[0.6, 0.8, 0.0], np.array([8.0, -6.0, 25.0]) / (5 * math.sqrt(29))])
+    np.testing.assert_allclose(Q, want, rtol=0, atol=1e-15)
+
+
 # ---------------------------------------------------------------- secant PCA --
 # The PCA start of Algorithm 1 (Sec. IV): top-k left singular vectors of the
 # unit-secant matrix S.

@@ -46,9 +46,9 @@ sys.path.insert(0, ROOT)
 METRIC = "SAP iterations/s and secant evals/s, fused vs plain, at fixed min-ratio error"
 CFG_NAME = "c2"
 
-# DRAM traffic of one restructured-pass launch from an ncu capture of this
-# workload (profiles/restructured_pass_moment_curve_N8192.md), valid only
-# while the pass kernel's source is unchanged (hash below, kernel_source_sha).
+# DRAM traffic of one restructured-pass launch from the ncu capture of this
+# kernel on this workload, valid only while the pass kernel's source is
+# unchanged (hash below, kernel_source_sha).
 PASS_TRAFFIC_BYTES = 69096192   # 68.536 MB read + 0.560 MB written
 PASS_SOURCE_SHA = "e29efe2e5bc65299"
 

@@ -257,18 +257,21 @@ sap_status sap_project_df(sap_handle h, float *Yh_out, float *Yl_out, int out_is
 
 /*
  * The argmin step without any device allocation, for callers that cannot
- * allocate GPU memory: code running while a stream is captured into a CUDA
- * graph, code whose device memory belongs to another allocator's pool, or
- * loops that cannot afford an allocation's synchronisation or failure.  The
- * paper has no counterpart; it is a deployment variant of sap_min_secant in
- * the plain form, and returns the same pair and ratio.
+ * allocate GPU memory: code whose device memory belongs to another
+ * allocator's pool, or loops that cannot afford an allocation's implicit
+ * synchronisation or its failure.  The paper has no counterpart; it is a
+ * deployment variant of sap_min_secant in the plain form, and returns the
+ * same pair and ratio.
  *
  * X: device pointer, N x n row-major FP32; U: device pointer, n x k
- * column-major FP64 with orthonormal columns (not checked); eps: the Sec. VII
- * threshold (0 for none); cuda_stream: the stream to run on (NULL: the legacy
- * default stream); i, j, ratio: host outputs (nullable).  Synchronises the
- * stream.  Limits: 2 <= N <= 1024, 1 <= n <= 1024, 1 <= k <= min(n, 8);
- * anything larger returns SAP_E_ARG.
+ * column-major FP64 with orthonormal columns (not checked); eps: pairs with
+ * ||x_i - x_j|| < eps are excluded (0: none); cuda_stream: the stream to run
+ * on (NULL: the legacy default stream); i, j, ratio: host outputs
+ * (nullable).  Copies the result to the host and synchronises the stream
+ * before returning.  SAP_E_NO_SECANT if every pair is excluded,
+ * SAP_E_TIMEOUT if a device-side bounded wait gave up.  Limits:
+ * 2 <= N <= 1024, 1 <= n <= 1024, 1 <= k <= min(n, 8); anything larger
+ * returns SAP_E_ARG.
  *
  * Working memory is one fixed file-scope device array of about 4.2 MB that
  * every GPU loading the library holds until exit.  The first call on a

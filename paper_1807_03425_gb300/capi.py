@@ -349,10 +349,24 @@ def sap_project_df(h, out_hi, out_lo):
 
 def sap_min_secant_noalloc(X, U, eps=0.0, stream=None):
     """Allocation-free argmin for callers that must not allocate device
-    memory: X (N, n) float32 and U (k, n) float64 torch CUDA tensors; returns
-    (i, j, ratio).  Limits N <= 1024, n <= 1024, k <= 8; concurrent calls on
-    one device must be serialised (they share a fixed scratch array)."""
-    if stream is not None and hasattr(stream, "cuda_stream"):
+    memory: X (N, n) float32 and U (k, n) float64 contiguous torch CUDA
+    tensors on one device; returns (i, j, ratio).  Runs on `stream` (a
+    torch.cuda.Stream or a raw cudaStream_t), by default torch's current
+    stream on X's device, and synchronises it.  Limits N <= 1024, n <= 1024,
+    k <= 8; concurrent calls on one device must be serialised (they share a
+    fixed scratch array)."""
+    import torch
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32
+            and X.dim() == 2 and X.is_contiguous()):
+        raise TypeError("X must be a contiguous (N, n) float32 CUDA tensor")
+    if not (isinstance(U, torch.Tensor) and U.is_cuda and U.dtype == torch.float64
+            and U.dim() == 2 and U.is_contiguous()):
+        raise TypeError("U must be a contiguous (k, n) float64 CUDA tensor")
+    if U.device != X.device or U.shape[1] != X.shape[1]:
+        raise ValueError("X and U must share the device and the dimension n")
+    if stream is None:
+        stream = torch.cuda.current_stream(X.device)
+    if hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     i, j, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
     code = load_library().sap_min_secant_noalloc(

@@ -1,19 +1,19 @@
 // noalloc.cu -- sap_min_secant_noalloc: the argmin step of SAP for callers
 // that cannot allocate GPU memory.
 //
-// Some callers must not call cudaMalloc: code that runs while a stream is
-// being captured into a CUDA graph, code whose device memory is owned by
-// another allocator (a framework's pool) and must not be fragmented or grown
-// behind its back, and latency-critical loops that cannot afford an
-// allocation's implicit synchronisation or its failure at run time.  This
-// entry point serves them: it allocates nothing.  Its working memory is one
-// file-scope __device__ array of fixed size (about 4.2 MB), which every GPU
-// that loads the library holds until the process exits.
+// Some callers must not call cudaMalloc: code whose device memory is owned
+// by another allocator (a framework's pool) and must not be fragmented or
+// grown behind its back, and latency-critical loops that cannot afford an
+// allocation's implicit device-wide synchronisation or its failure at run
+// time.  This entry point serves them: it allocates nothing.  Its working
+// memory is one file-scope __device__ array of fixed size (about 4.2 MB),
+// which every GPU that loads the library holds until the process exits.
 //
 // It runs the same kernels as sap_min_secant on a handle in the plain form:
 // the FP32 all-pairs pass (secants formed on the fly, certified candidate
 // emission) followed by the FP64 recheck and argmin, so it returns the same
-// pair and ratio.
+// pair and ratio.  It copies the result to the host and synchronises the
+// caller's stream before returning.
 //
 // Limits: 2 <= N <= 1024 points, 1 <= n <= 1024, 1 <= k <= min(n, 8); larger
 // problems are rejected with SAP_E_ARG.  The scratch holds every pair of the
@@ -214,7 +214,8 @@ extern "C" sap_status sap_min_secant_noalloc(const float *X, int64_t N, int32_t 
     if (cudaMemcpyAsync(&st, &g->st, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SAP_E_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SAP_E_CUDA;
     if (st.status & ST_NO_SECANT) return SAP_E_NO_SECANT;
-    if (st.status & (ST_OVERFLOW | ST_TIMEOUT)) return SAP_E_UNSUPPORTED;
+    if (st.status & ST_TIMEOUT) return SAP_E_TIMEOUT;
+    if (st.status & ST_OVERFLOW) return SAP_E_UNSUPPORTED;
     if (i_out) *i_out = st.last_i;
     if (j_out) *j_out = st.last_j;
     if (ratio_out) *ratio_out = st.last_r;

@@ -207,6 +207,120 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sharded(args):
+    """The bench workload split over the torchrun ranks (one GPU each): rank
+    r stores and streams only its row band of pair tiles; per iteration each
+    rank's exact minimum (a 16-byte record) is all-gathered over NCCL and
+    every rank takes the same FP64 update.  Total work is fixed, so the
+    scaling is strong; `value` counts the job's iterations."""
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    import workloads as W
+    from paper_1807_03425_gb300 import ShardSap, capi
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    tdist.init_process_group("nccl")
+    cfg = W.CONFIGS[CFG_NAME]
+    N, n, k, alpha = cfg["N"], 2 * cfg["m"], cfg["k"], cfg["alpha"]
+    X = W.moment_curve(N, cfg["m"], cfg["data_seed"], np.float32)
+    U0 = W.random_basis(n, k, cfg["basis_seed"])
+    P = N * (N - 1) // 2
+    K, Wm = args.steps, max(args.warmup, 3)
+    _, _, my_pairs = capi.sap_shard_range(N, ws, rank)
+    stream = torch.cuda.Stream()
+    s = ShardSap(X, ws, rank)
+    s.set_stream(stream.cuda_stream)
+    s.set_tuning(pass_bound=4e-3, pass_stages=0, explicit_blocks_per_sm=1, update_blocks=0,
+                 plain_blocks_per_sm=2, programmatic_launch=0, refine_tier=0)
+    s.set_basis(U0)
+
+    def barrier():
+        torch.cuda.synchronize()
+        tdist.barrier()
+        torch.cuda.synchronize()
+
+    def maxed(x):
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
+    with torch.cuda.stream(stream):
+        for _ in range(Wm):
+            s.step(alpha)
+    s.set_basis(U0)
+    st0 = s.stats()["kernel_launches"]
+    clocks = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    tw0 = time.time()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(K):
+            s.step(alpha)
+        ev1.record(stream)
+    barrier()
+    tw1 = time.time()
+    ms = maxed(ev0.elapsed_time(ev1))
+    clk = clocks.stop(tw0, tw1)
+    launches = s.stats()["kernel_launches"] - st0
+    hist, _ = s.get_history(K)
+    value = K / (ms * 1e-3)
+    # this rank's pass, launched one by one with CUDA events around it
+    capi.sap_set_profiling(s.h, True)
+    s.set_basis(U0)
+    with torch.cuda.stream(stream):
+        for _ in range(min(K, 200)):
+            s.step(alpha)
+    torch.cuda.synchronize()
+    pms, pcnt = capi.sap_get_kernel_time(s.h, "restructured_pass")
+    capi.sap_set_profiling(s.h, False)
+    pass_ms = maxed(pms / max(pcnt, 1))
+    # end to end with host buffers (basis up, iteration, basis down)
+    Ke = min(K, 1000)
+    Uh = torch.from_numpy(U0.copy()).pin_memory().numpy()
+    Uo = torch.empty((k, n), dtype=torch.float64).pin_memory().numpy()
+    barrier()
+    te0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(Ke):
+            s.set_basis(Uh)
+            s.step(alpha)
+            s.get_basis(Uo)
+            Uh[:] = Uo
+    te = maxed(time.perf_counter() - te0)
+    hbm, _, peak_src = peaks()
+    alg_bytes = 2 * my_pairs
+    achieved = alg_bytes / (pass_ms * 1e-3) / 1e9
+    s.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": ws, "steps": K,
+        "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg["workload"], "N": N, "n": n, "k": k, "alpha": alpha,
+                   "path": "restructured, split over ranks",
+                   "parallelism": "sharded x%d: row bands of 128 x 128 pair tiles of equal pair count; "
+                                  "one 16-byte record per rank all-gathered (NCCL) per iteration" % ws,
+                   "l2": "not flushed between steps (each rank streams 1/%d of 68 MB)" % ws},
+        "secant_evals_per_s": value * P,
+        "final_min_ratio": float(hist[-1]),
+        "roofline": {"kernel": "restructured_pass (one rank's band)", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, per GPU)",
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": pass_ms},
+        "e2e": {"value": Ke / te, "unit": "iterations/s", "h2d_bytes_per_step": n * k * 8,
+                "d2h_bytes_per_step": n * k * 8},
+        "gpu_launches": launches,
+    }
+    if clk:
+        line["clocks"] = clk
+    print(json.dumps(line), flush=True)
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -215,10 +329,9 @@ def run_native(args):
     from paper_1807_03425_gb300 import Sap
 
     ws, rank, local = dist()
-    torch.cuda.set_device(local)
     if ws > 1:
-        import torch.distributed as tdist
-        tdist.init_process_group("nccl")
+        return run_sharded(args)
+    torch.cuda.set_device(local)
     cfg = W.CONFIGS[CFG_NAME]
     N, n, k, alpha = cfg["N"], 2 * cfg["m"], cfg["k"], cfg["alpha"]
     X = W.moment_curve(N, cfg["m"], cfg["data_seed"], np.float32)
@@ -394,9 +507,14 @@ def run_native(args):
         line["clocks"] = clk
     if ws == 1:
         line["cpu_baseline"] = cpu_baseline(X.astype(np.float64), U0, alpha)
-    print(json.dumps(line), flush=True)
     sap.close()
     splain.close()
+    if ws == 1:
+        # the other batched forms of the path, each a few timed iterations
+        # with its own roofline, clocks and oracle baseline
+        line["sweep"] = measure_sweep(args, 100, 8, local)
+        line["batch"] = measure_batch(args, 160, 16, local)
+    print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------ the other forms of the path
@@ -507,20 +625,28 @@ def run_sweep(args):
     """Dimension sweep k = 1..20 over N = 4096 blob images (n = 4096): every
     iteration advances all 20 bases (one tensor-core product for all of them,
     then 20 independent pass/recheck/update chains)."""
+    import workloads as W
+    _, rank, local = dist()
+    K = args.steps if args.steps else W.CONFIGS["c3"]["T"]
+    Wm = max(args.warmup if args.warmup is not None else 8, 3)
+    line = measure_sweep(args, K, Wm, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_sweep(args, K, Wm, local):
+    """The sweep workload's JSON line (K timed sweep iterations after Wm)."""
     import numpy as np
     import torch
 
     import workloads as W
     from paper_1807_03425_gb300 import Sap
-    _, rank, local = dist()
     torch.cuda.set_device(local)
     cfg = W.CONFIGS["c3"]
     N, n, kmax, alpha, thr = cfg["N"], cfg["n"], cfg["kmax"], cfg["alpha"], cfg["threshold"]
     X = W.blob_images(N, cfg["data_seed"])
     U0 = W.random_basis(n, kmax, cfg["basis_seed"])
     P = N * (N - 1) // 2
-    K = args.steps if args.steps else cfg["T"]
-    Wm = max(args.warmup if args.warmup is not None else 8, 3)
     stream = torch.cuda.Stream()
     s = Sap(X)
     s.set_stream(stream)
@@ -551,8 +677,6 @@ def run_sweep(args):
     if os.path.exists(pk):
         with open(pk) as f:
             bf16_peak = float(json.load(f)["bf16_tflops_sustained"])
-    if rank != 0:
-        return
     line = _common(args, cfg["workload"], it_s, "sweep iterations/s", ms / its, its, Wm, "f32",
                    {"N": N, "n": n, "k": "1..%d" % kmax, "alpha": alpha, "threshold": thr, "tuning": tuning,
                     "l2": "stored lengths 33.5 MB (L2-resident, shared by the 20 bases); X operands 67 MB"})
@@ -592,27 +716,34 @@ def run_sweep(args):
                             "kind": "oracle",
                             "sample": "one FP64 step of each k = 1..20 over the first %d images (%d pairs), "
                                       "scaled by %d/%d pairs" % (Ns, Ps, Ps, P)}
-    print(json.dumps(line), flush=True)
     s.close()
+    return line
 
 
 def run_batch(args):
     """32 uneven hyperspectral scenes advancing together (one captured graph
     per chunk of iterations, one branch per scene)."""
+    _, rank, local = dist()
+    K = args.steps if args.steps else 160
+    Wm = max(args.warmup if args.warmup is not None else 16, 3)
+    line = measure_batch(args, K, Wm, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_batch(args, K, Wm, local):
+    """The uneven-batch workload's JSON line (K timed batch iterations)."""
     import numpy as np
     import torch
 
     import workloads as W
     from paper_1807_03425_gb300 import BF16, SapBatch
-    _, rank, local = dist()
     torch.cuda.set_device(local)
     cfg = W.CONFIGS["c4"]
     B, n, k, alpha, eps = cfg["B"], cfg["n"], cfg["k"], cfg["alpha"], cfg["eps"]
     Xs, Ns = W.hyperspectral_batch(B, cfg["data_seed"])
     Us = [W.random_basis(n, k, cfg["basis_seed"] + b) for b in range(B)]
     Ptot = sum(N * (N - 1) // 2 for N in Ns)
-    K = args.steps if args.steps else 160
-    Wm = max(args.warmup if args.warmup is not None else 16, 3)
     stream = torch.cuda.Stream()
     sb = SapBatch([W.bf16_bits(X) for X in Xs], dtype=BF16)
     sb.set_stream(stream)
@@ -638,8 +769,6 @@ def run_batch(args):
     it_s = its / (ms * 1e-3)
     hbm = peaks()[0]
     alg = 2 * (Ptot - st1["n_excluded"] - st1["n_near"])  # BF16 w per stored pair
-    if rank != 0:
-        return
     line = _common(args, cfg["workload"], it_s, "batch iterations/s", ms / its, its, Wm, "f32",
                    {"datasets": B, "N_min": min(Ns), "N_max": max(Ns), "n": n, "k": k, "alpha": alpha,
                     "eps": eps, "input": "BF16 data, FP32 arithmetic",
@@ -670,8 +799,8 @@ def run_batch(args):
                             "kind": "oracle",
                             "sample": "one FP64 step of the smallest scene (N = %d, %d pairs), scaled by "
                                       "%d/%d pairs of the batch" % (Ns[b0], P0, P0, Ptot)}
-    print(json.dumps(line), flush=True)
     sb.close()
+    return line
 
 
 def run_softmin(args):
@@ -885,7 +1014,7 @@ def run_pca(args):
         "roofline": {"kernel": "Laplacian rows + Gram (FP64)", "bound": "fp64",
                      "achieved": fp64_flops / wall / 1e12, "unit": "TFLOP/s", "peak": None, "frac": None,
                      "traffic": None,
-                     "note": "whole start incl. cuSOLVER; FP64 rate of this part measured near 1.0 TFLOP/s"},
+                     "note": "whole start incl. the Jacobi eigensolver; FP64 rate of this part measured near 1.0 TFLOP/s"},
         "e2e": {"value": 1.0 / wall, "unit": "PCA starts/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": n * k * 8},
     })

@@ -162,8 +162,9 @@ sap_status sap_set_basis(sap_handle h, const double *U, int32_t k,
  * positive.  S S^T is formed in FP64 on the device as Xc^T L X (L the
  * 1/d^2-weighted graph Laplacian of the pairs, lengths from explicit FP64
  * differences), never storing S; the n x n symmetric eigenproblem is solved
- * by cuSOLVER (FP64), loaded at the first call (SAP_E_UNSUPPORTED if
- * libcusolver cannot be loaded).  U_out (nullable, host, n x k
+ * on the device by the cyclic Jacobi method in FP64 (round-robin parallel
+ * ordering, sweeps until the off-diagonal norm is below 4 n 2^-53 of the
+ * whole; SAP_E_CUDA if 40 sweeps do not get there).  U_out (nullable, host, n x k
  * column-major) receives the basis, sigma_out (nullable, k) the singular
  * values sqrt(lambda) in descending order.  1 <= k <= min(n, 32).  Resets
  * the iteration counter, like sap_set_basis.  Work memory: 8 B per pair
@@ -376,7 +377,12 @@ typedef struct {
     int32_t refine_tier;            /* second tier of the restructured form: 1 double-float Y
                                        (O(k) per pair), 0 explicit differences (O(n k) per pair),
                                        2 explicit differences fused into the FP64 recheck (one
-                                       launch fewer; n <= 256, else as 0), -1 chosen by n
+                                       launch fewer; n <= 256, else as 0), 3 explicit differences
+                                       in extended precision (hi + lo FP32, error-free products)
+                                       fused into the FP64 recheck (one launch fewer; k <= 8, else
+                                       as 0), 4 explicit differences in extended precision whose
+                                       list carries each pair's ratio, so the FP64 recheck takes
+                                       only the pairs within the final bound, -1 chosen by n
                                        (double-float above n = 256) */
     double us_per_iteration;        /* measured by sap_autotune; 0 when set by hand */
 } sap_tuning;
@@ -422,6 +428,79 @@ sap_status sap_create_subsamples(const void *X, int64_t N, int32_t n, sap_dtype 
                                  const int64_t *idx, int32_t R, int32_t m, sap_handle *out);
 sap_status sap_estimate_dim_b(sap_handle h, int32_t b, const double *U0, int32_t k_max, int32_t iters,
                               double alpha, double threshold, int32_t *k_out, double *ratios_out);
+
+/*
+ * Multi-GPU split of the argmin step (Algorithm 1, Sec. IV: the minimum over
+ * all pairs is the minimum of the minima over disjoint sets of pairs), one
+ * process per GPU.  The upper triangle of 128 x 128 pair tiles (I <= J), in
+ * row-major order over the tile grid, is cut into `world` contiguous ranges
+ * of nearly equal pair count; rank r owns range r.  Each rank holds the
+ * points and the basis in full and the lengths of its own tiles only.  One
+ * iteration:
+ *   1. sap_shard_min on every rank: its shard's exact minimum as a record;
+ *   2. an all-gather of the 16-byte records (the caller's collective, e.g.
+ *      NCCL through torch.distributed);
+ *   3. sap_shard_step on every rank with all records: the winning pair is
+ *      re-evaluated in FP64 and every rank takes the same update, so the
+ *      bases stay identical with no further exchange.
+ * A record is the FP64 squared ratio q = r^2 of the shard's best pair and
+ * the pair (i < j), or i = j = -1 when the shard has no candidate.
+ */
+typedef struct {
+    double q;
+    int32_t i, j;
+} sap_record;
+
+/* Tile range [t0, t1) and pair count of rank `rank` among `world` for N
+ * points (host only; 1 <= world <= 4096, 0 <= rank < world).  A range may be
+ * empty when world exceeds the number of tiles. */
+sap_status sap_shard_range(int64_t N, int32_t world, int32_t rank, int64_t *t0, int64_t *t1,
+                           int64_t *pairs);
+
+/* The lexicographic minimum (q, then i, then j) of `count` records into out
+ * (host only); records with i < 0 are skipped.  SAP_E_NO_SECANT if none. */
+sap_status sap_merge_records(const sap_record *recs, int32_t count, sap_record *out);
+
+/* Create a handle for rank `rank` of `world` on dataset X (as sap_create;
+ * FP32 or BF16 data, restructured form only).  The length preparation and
+ * the all-pairs pass cover only the rank's tiles.  SAP_E_ARG if the rank's
+ * range is empty.  On such a handle sap_step, sap_run, sap_min_secant,
+ * sap_estimate_dim, sap_autotune, sap_secant_pca, the soft-min calls and
+ * the plain path return SAP_E_STATE / SAP_E_UNSUPPORTED. */
+sap_status sap_create_shard(const void *X, int64_t N, int32_t n, sap_dtype dt, int x_is_device, int32_t world,
+                            int32_t rank, sap_handle *out);
+
+/* Step 1 of a sharded iteration: the exact minimum over the rank's pairs
+ * under the current basis, written as one record to rec_out (host, or
+ * device when out_is_device; then the call does not synchronise). */
+sap_status sap_shard_min(sap_handle h, sap_record *rec_out, int out_is_device);
+
+/* Step 3: the update toward the unit secant of the best of `count` records
+ * (all ranks' records, host or device as recs_is_device), with step alpha,
+ * recorded in the handle's history (sap_get_history).  The winning pair's
+ * ratio is re-evaluated in FP64 under the current basis, so every rank
+ * decides identically.  SAP_E_NO_SECANT if no record holds a pair (reported
+ * when the call synchronises: with a host `out` pair, or at the next call
+ * that reads the device status). */
+sap_status sap_shard_step(sap_handle h, double alpha, const sap_record *recs, int32_t count,
+                          int recs_is_device);
+
+/*
+ * Test hooks of the failure paths (no counterpart in the paper).
+ * sap_inject_fault: the next CUDA call this handle checks reports an error
+ * as if the runtime had returned it -- kind 1 an allocation failure
+ * (SAP_E_OOM; the handle stays usable), kind 2 a CUDA error (SAP_E_CUDA,
+ * sticky: every later call but sap_destroy returns SAP_E_CUDA).  Nothing is
+ * sent to the device.  NULL handle or another kind -> SAP_E_ARG.
+ * sap_selftest_wait: one kernel waits on an mbarrier that nothing arrives
+ * on, with the bounded wait every kernel of the library uses, for
+ * budget_cycles SM clocks (0 .. 4e9), then records that it gave up;
+ * returns SAP_E_TIMEOUT, and the context stays usable.  No copy is in
+ * flight during the wait.  Synchronises cuda_stream (NULL: the legacy
+ * default stream).
+ */
+sap_status sap_inject_fault(sap_handle h, int32_t kind);
+sap_status sap_selftest_wait(void *cuda_stream, int64_t budget_cycles);
 
 /* Read the handle's statistics. */
 sap_status sap_get_stats(sap_handle h, sap_stats *out);

@@ -7,6 +7,6 @@ mirrors the C entry points one-to-one (same names, argument marshalling only)
 and ``Sap`` wraps a handle.  There is no CPU fallback: if the shared library
 is missing or no GPU is present, calls raise.
 """
-from .capi import (SapError, Sap, SapBatch, load_library, library_path,  # noqa: F401
+from .capi import (SapError, Sap, SapBatch, ShardSap, load_library, library_path,  # noqa: F401
                    PLAIN, RESTRUCTURED, UPDATE_LITERAL, UPDATE_ANGLE,
                    SPLIT_FP16, SPLIT_BF16, F32, BF16, F64, KERNEL_CLASSES)

@@ -47,6 +47,12 @@ class Stats(ctypes.Structure):
                 ("y_error_unit", ctypes.c_double), ("ydf_error_unit", ctypes.c_double)]
 
 
+class Record(ctypes.Structure):
+    """One rank's minimum in the multi-GPU split: FP64 squared ratio q and
+    the pair (i, j); i = j = -1 when the rank has no candidate."""
+    _fields_ = [("q", ctypes.c_double), ("i", ctypes.c_int32), ("j", ctypes.c_int32)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("pass_bound", ctypes.c_double), ("pass_stages", ctypes.c_int32),
                 ("explicit_blocks_per_sm", ctypes.c_int32), ("update_blocks", ctypes.c_int32),
@@ -116,6 +122,13 @@ def load_library():
         "sap_autotune": ([vp, f64, i32, ctypes.POINTER(Tuning)], i32),
         "sap_get_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
         "sap_set_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
+        "sap_shard_range": ([i64, i32, i32, i64p, i64p, i64p], i32),
+        "sap_merge_records": ([ctypes.POINTER(Record), i32, ctypes.POINTER(Record)], i32),
+        "sap_create_shard": ([vp, i64, i32, i32, i32, i32, i32, ctypes.POINTER(vp)], i32),
+        "sap_shard_min": ([vp, vp, i32], i32),
+        "sap_shard_step": ([vp, f64, vp, i32, i32], i32),
+        "sap_inject_fault": ([vp, i32], i32),
+        "sap_selftest_wait": ([vp, i64], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -376,6 +389,83 @@ def sap_min_secant_noalloc(X, U, eps=0.0, stream=None):
     if code != 0:
         raise SapError(code, "sap_min_secant_noalloc")
     return i.value, j.value, r.value
+
+
+def sap_shard_range(N, world, rank):
+    """(t0, t1, pairs): the tile range [t0, t1) and pair count of `rank` among
+    `world` for N points (host only, no device needed)."""
+    t0, t1, pairs = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    code = load_library().sap_shard_range(N, world, rank, ctypes.byref(t0), ctypes.byref(t1), ctypes.byref(pairs))
+    if code != 0:
+        raise SapError(code, "sap_shard_range(N=%d, world=%d, rank=%d)" % (N, world, rank))
+    return t0.value, t1.value, pairs.value
+
+
+def sap_merge_records(recs):
+    """The winning record of a sequence of (q, i, j) (host only); None when no
+    record holds a pair."""
+    arr = (Record * len(recs))(*[Record(float(q), int(i), int(j)) for q, i, j in recs])
+    out = Record()
+    code = load_library().sap_merge_records(arr, len(recs), ctypes.byref(out))
+    if code == 4:
+        return None
+    if code != 0:
+        raise SapError(code, "sap_merge_records")
+    return out.q, out.i, out.j
+
+
+def sap_create_shard(X, world, rank, dtype=None):
+    """As sap_create, for rank `rank` of `world` (restructured form)."""
+    lib = load_library()
+    if dtype is None:
+        dtype = BF16 if ("bfloat16" in str(getattr(X, "dtype", "")) or "uint16" in str(getattr(X, "dtype", ""))) else F32
+    if not hasattr(X, "data_ptr"):
+        X = np.ascontiguousarray(X, dtype={F32: np.float32, BF16: np.uint16}[dtype])
+    elif not X.is_contiguous():
+        raise ValueError("X must be contiguous")
+    N, n = X.shape
+    p, dev = _ptr(X)
+    h = ctypes.c_void_p()
+    code = lib.sap_create_shard(p, N, n, dtype, dev, world, rank, ctypes.byref(h))
+    if code != 0:
+        raise SapError(code, "sap_create_shard(N=%d, n=%d, world=%d, rank=%d)" % (N, n, world, rank))
+    return h
+
+
+def sap_shard_min(h, out=None):
+    """This rank's minimum: into `out` (a 16-byte torch CUDA tensor, no
+    synchronisation) or, with out None, returned as (q, i, j)."""
+    lib = load_library()
+    if out is not None:
+        _check(h, lib.sap_shard_min(h, ctypes.c_void_p(out.data_ptr()), 1))
+        return out
+    r = Record()
+    _check(h, lib.sap_shard_min(h, ctypes.byref(r), 0))
+    return r.q, r.i, r.j
+
+
+def sap_shard_step(h, alpha, recs):
+    """The update from all ranks' records: a torch CUDA tensor of count x 16
+    bytes (no synchronisation) or a sequence of (q, i, j) tuples."""
+    lib = load_library()
+    if hasattr(recs, "data_ptr"):
+        count = recs.numel() * recs.element_size() // 16
+        _check(h, lib.sap_shard_step(h, float(alpha), ctypes.c_void_p(recs.data_ptr()), count, 1))
+        return
+    arr = (Record * len(recs))(*[Record(float(q), int(i), int(j)) for q, i, j in recs])
+    _check(h, lib.sap_shard_step(h, float(alpha), ctypes.cast(arr, ctypes.c_void_p), len(recs), 0))
+
+
+def sap_inject_fault(h, kind):
+    """Test hook: the next checked CUDA call of the handle fails (kind 1: an
+    allocation failure, 2: a sticky CUDA error).  Returns the status code."""
+    return load_library().sap_inject_fault(h, int(kind))
+
+
+def sap_selftest_wait(budget_cycles, stream=None):
+    """Test hook: a kernel whose bounded mbarrier wait runs out after
+    budget_cycles SM clocks.  Returns the status code (SAP_E_TIMEOUT)."""
+    return load_library().sap_selftest_wait(ctypes.c_void_p(stream) if stream else None, int(budget_cycles))
 
 
 def sap_get_stats(h):
@@ -703,3 +793,69 @@ class SapBatch:
 
     def stats(self):
         return sap_get_stats(self.h)
+
+
+class ShardSap:
+    """One rank's share of the all-pairs step in the multi-GPU split (one
+    process per GPU; see sap_create_shard).  `step` runs one SAP iteration:
+    the rank's exact minimum as a 16-byte record, an all-gather of the
+    records over `group` (torch.distributed: NCCL between GPUs), and the same
+    FP64 update on every rank.  The library runs on torch's current stream,
+    so the collective is ordered between the two calls."""
+
+    def __init__(self, X, world, rank, dtype=None):
+        import torch
+        self.world, self.rank = int(world), int(rank)
+        self.N, self.n = int(X.shape[0]), int(X.shape[1])
+        self.h = sap_create_shard(X, self.world, self.rank, dtype)
+        self.k = 0
+        self._rec = torch.empty(16, dtype=torch.uint8, device="cuda")
+        self._all = torch.empty(16 * self.world, dtype=torch.uint8, device="cuda")
+
+    def close(self):
+        if self.h:
+            sap_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        sap_set_stream(self.h, stream)
+
+    def set_basis(self, U):
+        sap_set_basis(self.h, U)
+        self.k = int(U.shape[0])
+
+    def get_basis(self, out=None):
+        return sap_get_basis(self.h, self.k, self.n, out)
+
+    def set_tuning(self, **params):
+        sap_set_tuning(self.h, **params)
+
+    def get_history(self, count):
+        return sap_get_history(self.h, count)
+
+    def stats(self):
+        return sap_get_stats(self.h)
+
+    def min_record(self, out=None):
+        return sap_shard_min(self.h, out)
+
+    def step_records(self, alpha, recs):
+        sap_shard_step(self.h, alpha, recs)
+
+    def step(self, alpha, group=None):
+        import torch.distributed as dist
+        sap_shard_min(self.h, self._rec)
+        dist.all_gather_into_tensor(self._all, self._rec, group=group)
+        sap_shard_step(self.h, alpha, self._all)

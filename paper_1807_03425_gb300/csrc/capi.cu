@@ -94,10 +94,20 @@ struct sap_ctx {
     std::vector<cudaEvent_t> kid_done;
     cudaEvent_t fork = nullptr;
 
+    cudaError_t inject = cudaSuccess;  // result forced on the next checked call (sap_inject_fault)
+
     long long launches = 0;
     std::vector<GraphEntry> graphs;
     long long graph_gen = 0;   // bumped whenever this handle's graphs are dropped
     long long kids_gen = -1;   // batch: sum of the datasets' graph_gen its graphs were made at
+
+    // multi-GPU split: this handle is rank shard_rank of shard_world and
+    // stores the tiles [shard_t0, shard_t1) of the row-major tile order
+    int shard_world = 1, shard_rank = 0;
+    long long shard_t0 = 0, shard_t1 = -1;
+    Partial *shard_rec = nullptr;   // this rank's minimum (sap_shard_min)
+    Partial *recs = nullptr;        // all ranks' records (sap_shard_step, host input)
+    int shard_steps = 0;
 
     TuneParams tune;          // launch parameters (tune.cu)
     TuneKey tune_key;         // shape the parameters were last applied for
@@ -121,9 +131,15 @@ sap_status fail(sap_handle h, sap_status s, const std::string &msg)
     return s;
 }
 
+// A checked CUDA call of the engine; an error injected by sap_inject_fault
+// replaces the next call's result.
 #define CK(call)                                                                   \
     do {                                                                           \
         cudaError_t e_ = (call);                                                   \
+        if (h->inject != cudaSuccess) {                                            \
+            e_ = h->inject;                                                        \
+            h->inject = cudaSuccess;                                               \
+        }                                                                          \
         if (e_ != cudaSuccess)                                                     \
             return fail(h, e_ == cudaErrorMemoryAllocation ? SAP_E_OOM : SAP_E_CUDA, \
                         std::string(#call) + ": " + cudaGetErrorString(e_));       \
@@ -226,7 +242,28 @@ struct Timed {
     }
 };
 
-sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only)
+// Arguments of the FP64 recheck + update over candidate list `list`
+// (count in st->cnt<which>), without the fused-tier fields.
+SelectUpdateArgs su_args(sap_handle h, double alpha, int eval_only, const int2 *list, int which)
+{
+    const bool f64 = h->dt == SAP_F64;
+    SelectUpdateArgs u;
+    u.X = f64 ? (const void *)h->X64 : (const void *)h->X32;
+    u.x_is_f64 = f64; u.N = (int)h->N; u.n = h->n;
+    u.U64 = h->U64; u.U32 = h->U32; u.U32lo = h->U32lo; u.KP = h->KP;
+    u.Uhi = h->rs.Uhi; u.Ulo = h->rs.Ulo; u.NP = h->rs.NP;
+    u.split_bf16 = h->split == SAP_SPLIT_BF16; u.split_scale = h->split == SAP_SPLIT_BF16 ? 256.f : 2048.f;
+    u.k = h->k; u.alpha = alpha; u.mode = (int)h->mode; u.eval_only = eval_only;
+    u.eps2 = h->eps2_f64; u.list = list; u.cap = (unsigned int)h->cap; u.which = which;
+    u.partials = h->partials;
+    u.grid = std::min(h->tune.su_blocks > 0 ? h->tune.su_blocks : h->sms, kRecheckBlocks);
+    u.work = h->work; u.st = h->st; u.hist = h->hist; u.argmin = h->am; u.seed_cert = cert_plain_f32(h->n, h->k);
+    u.pdl = h->tune.pdl;
+    u.fused = 0; u.near = nullptr; u.n_near = 0; u.cert2 = u.seed_cert;
+    return u;
+}
+
+sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only, Partial *shard_rec = nullptr)
 {
     cudaStream_t s = h->stream;
     const Cert c32 = cert_plain_f32(h->n, h->k);
@@ -260,24 +297,13 @@ sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only)
         list = h->cand2;
     }
     {
-        SelectUpdateArgs u;
-        u.X = f64 ? (const void *)h->X64 : (const void *)h->X32;
-        u.x_is_f64 = f64; u.N = (int)h->N; u.n = h->n;
-        u.U64 = h->U64; u.U32 = h->U32; u.U32lo = h->U32lo; u.KP = h->KP;
-        u.Uhi = h->rs.Uhi; u.Ulo = h->rs.Ulo; u.NP = h->rs.NP;
-        u.split_bf16 = h->split == SAP_SPLIT_BF16; u.split_scale = h->split == SAP_SPLIT_BF16 ? 256.f : 2048.f;
-        u.k = h->k; u.alpha = alpha; u.mode = (int)h->mode; u.eval_only = eval_only;
-        u.eps2 = h->eps2_f64; u.list = list; u.cap = (unsigned int)h->cap; u.which = which;
-        u.partials = h->partials;
-        u.grid = std::min(h->tune.su_blocks > 0 ? h->tune.su_blocks : h->sms, kRecheckBlocks);
-        u.work = h->work; u.st = h->st; u.hist = h->hist; u.argmin = h->am; u.seed_cert = c32;
-        u.pdl = h->tune.pdl;
-        if (h->path == SAP_PLAIN) {
-            u.fused = 0; u.near = nullptr; u.n_near = 0; u.cert2 = c32;
-        } else {
+        SelectUpdateArgs u = su_args(h, alpha, eval_only, list, which);
+        u.shard_rec = shard_rec;
+        if (h->path != SAP_PLAIN) {
             BasisView bv;
             bv.k = h->k;
             bv.cand1 = h->cand1;
+            bv.cand2 = h->cand2;
             restructured_fuse_args(h, bv, u);
         }
         Timed t(h, K_UPDATE);
@@ -414,6 +440,11 @@ TuneKey handle_tune_key(sap_handle h)
     return t;
 }
 bool &handle_tuning_flag(sap_handle h) { return h->tuning; }
+void handle_shard(sap_handle h, long long *t0, long long *t1)
+{
+    *t0 = h->shard_world > 1 ? h->shard_t0 : 0;
+    *t1 = h->shard_world > 1 ? h->shard_t1 : -1;
+}
 TuneKey &handle_applied_key(sap_handle h) { return h->tune_key; }
 void handle_drop_graphs(sap_handle h) { drop_graphs(h); }
 bool handle_path_restructured(sap_handle h) { return h->path == SAP_RESTRUCTURED && h->dt != SAP_F64; }
@@ -436,7 +467,57 @@ void handle_add_launches(sap_handle h, long long delta) { h->launches += delta; 
 
 extern "C" {
 
-const char *sap_version(void) { return "libsap 0.1 (sm_103a)"; }
+const char *sap_version(void) { return "libsap 0.2 (sm_103a)"; }
+
+sap_status sap_inject_fault(sap_handle h, int32_t kind)
+{
+    if (!h || (kind != 1 && kind != 2)) return SAP_E_ARG;
+    h->inject = kind == 1 ? cudaErrorMemoryAllocation : cudaErrorLaunchFailure;
+    return SAP_OK;
+}
+
+namespace {
+// Waits on an mbarrier that nothing arrives on, with the library's bounded
+// wait; records whether the wait gave up.
+__global__ void selftest_wait_kernel(long long budget, int *status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const long long t0 = clock64();
+    bool done = false;
+    while (!done) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+                     " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(a) : "memory");
+        if (ok) done = true;
+        else if (clock64() - t0 > budget) break;
+    }
+    *status = done ? 0 : ST_TIMEOUT;
+}
+} // namespace
+
+sap_status sap_selftest_wait(void *cuda_stream, int64_t budget_cycles)
+{
+    if (budget_cycles < 0 || budget_cycles > 4000000000ll) return SAP_E_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return SAP_E_NO_DEVICE;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int *d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return SAP_E_OOM;
+    int status = -1;
+    selftest_wait_kernel<<<1, 1, 0, s>>>((long long)budget_cycles, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return SAP_E_CUDA;
+    return status == 0 ? SAP_OK : SAP_E_TIMEOUT;
+}
 
 const char *sap_status_str(sap_status s)
 {
@@ -474,6 +555,7 @@ sap_status sap_destroy(sap_handle h)
     softmin_free(h);
     sweep_free(h->sw);
     dfree(h->X32); dfree(h->X64); dfree(h->U64); dfree(h->U32); dfree(h->U32lo);
+    dfree(h->shard_rec); dfree(h->recs);
     dfree(h->tiles); dfree(h->cand1); dfree(h->cand2); dfree(h->partials);
     dfree(h->work); dfree(h->st); dfree(h->hist); dfree(h->am);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -481,13 +563,21 @@ sap_status sap_destroy(sap_handle h)
     return SAP_OK;
 }
 
-sap_status sap_create(const void *X, int64_t N, int32_t n, sap_dtype dt, int x_is_device,
-                      sap_handle *out)
+static sap_status create_impl(const void *X, int64_t N, int32_t n, sap_dtype dt, int x_is_device, int32_t world,
+                              int32_t rank, sap_handle *out)
 {
     if (!out) return SAP_E_ARG;
     *out = nullptr;
     if (!X || N < 2 || N > 92681 || n < 1 || n > 16384) return SAP_E_ARG;
     if (dt != SAP_F32 && dt != SAP_BF16 && dt != SAP_F64) return SAP_E_ARG;
+    long long t0 = 0, t1 = -1;
+    if (world > 1) {
+        if (dt == SAP_F64) return SAP_E_UNSUPPORTED;  // the split covers the restructured form
+        int64_t a = 0, b = 0, pairs = 0;
+        if (sap_shard_range(N, world, rank, &a, &b, &pairs) != SAP_OK || b <= a) return SAP_E_ARG;
+        t0 = a;
+        t1 = b;
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
         cudaGetLastError();
@@ -495,6 +585,12 @@ sap_status sap_create(const void *X, int64_t N, int32_t n, sap_dtype dt, int x_i
     }
     sap_handle h = new sap_ctx();
     h->N = N; h->n = n; h->dt = dt;
+    if (world > 1) {
+        h->shard_world = world;
+        h->shard_rank = rank;
+        h->shard_t0 = t0;
+        h->shard_t1 = t1;
+    }
     CK(cudaGetDevice(&h->device));
     CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
     if (x_is_device) {
@@ -553,9 +649,26 @@ sap_status sap_create(const void *X, int64_t N, int32_t n, sap_dtype dt, int x_i
         sap_status rs = restructured_prepare(h);
         if (rs != SAP_OK) return cleanup_fail(rs);
     }
+    if (world > 1) {
+        chk(dalloc(&h->shard_rec, 1));
+        chk(dalloc(&h->recs, 4096));
+        if (st != SAP_OK) return cleanup_fail(st);
+    }
     if (reset_state(h) != SAP_OK) return cleanup_fail(SAP_E_CUDA);
     *out = h;
     return SAP_OK;
+}
+
+sap_status sap_create(const void *X, int64_t N, int32_t n, sap_dtype dt, int x_is_device, sap_handle *out)
+{
+    return create_impl(X, N, n, dt, x_is_device, 1, 0, out);
+}
+
+sap_status sap_create_shard(const void *X, int64_t N, int32_t n, sap_dtype dt, int x_is_device, int32_t world,
+                            int32_t rank, sap_handle *out)
+{
+    if (world < 1 || world > 4096 || rank < 0 || rank >= world) return SAP_E_ARG;
+    return create_impl(X, N, n, dt, x_is_device, world, rank, out);
 }
 
 // Batch handles forward the dataset-wide settings to every dataset; calls
@@ -573,6 +686,12 @@ sap_status sap_create(const void *X, int64_t N, int32_t n, sap_dtype dt, int x_i
             }                                                         \
             return SAP_OK;                                            \
         }                                                             \
+    } while (0)
+
+#define NOT_SHARD(h)                                                                 \
+    do {                                                                             \
+        if ((h)->shard_world > 1)                                                    \
+            return fail(h, SAP_E_STATE, "shard handle: use sap_shard_min / sap_shard_step"); \
     } while (0)
 
 #define NOT_BATCH(h)                                                                 \
@@ -601,6 +720,8 @@ sap_status sap_set_path(sap_handle h, sap_path p)
     CHECK_HANDLE(h);
     FORWARD_BATCH(h, sap_set_path(kid, p));
     if (p != SAP_PLAIN && p != SAP_RESTRUCTURED) return fail(h, SAP_E_ARG, "unknown path");
+    if (p == SAP_PLAIN && h->shard_world > 1)
+        return fail(h, SAP_E_UNSUPPORTED, "the split covers the restructured form only");
     if (p == SAP_RESTRUCTURED && h->dt == SAP_F64)
         return fail(h, SAP_E_UNSUPPORTED, "the restructured form needs FP32 or BF16 data");
     if (p == SAP_PLAIN && h->dt != SAP_F64 && h->k > 8)
@@ -661,6 +782,7 @@ sap_status sap_secant_pca(sap_handle h, int32_t k, double *U_out, double *sigma_
 {
     CHECK_HANDLE(h);
     NOT_BATCH(h);
+    NOT_SHARD(h);
     std::vector<double> U((size_t)h->n * std::max(k, 1));
     sap_status s = secant_pca(h, k, U.data(), sigma_out);
     if (s != SAP_OK) return s;
@@ -713,7 +835,7 @@ sap_status sap_set_tuning(sap_handle h, const sap_tuning *in)
         in->explicit_blocks_per_sm < 1 || in->explicit_blocks_per_sm > 8 || in->update_blocks < 0 ||
         in->update_blocks > kRecheckBlocks || in->plain_blocks_per_sm < 1 || in->plain_blocks_per_sm > 8 ||
         (in->programmatic_launch != 0 && in->programmatic_launch != 1) || in->refine_tier < -1 ||
-        in->refine_tier > 2)
+        in->refine_tier > 4)
         return fail(h, SAP_E_ARG, "tuning parameter out of range");
     CK(cudaStreamSynchronize(h->stream));
     TuneParams p;
@@ -731,6 +853,7 @@ sap_status sap_set_tuning(sap_handle h, const sap_tuning *in)
 sap_status sap_autotune(sap_handle h, double alpha, int32_t iters, sap_tuning *out)
 {
     CHECK_HANDLE(h);
+    NOT_SHARD(h);
     if (h->is_batch) {
         for (size_t b = 0; b < h->kids.size(); ++b) {
             sap_status st = sap_autotune(h->kids[b], alpha, iters, nullptr);
@@ -802,6 +925,7 @@ sap_status sap_set_basis(sap_handle h, const double *U, int32_t k, int u_is_devi
     }
     sap_status s = tune_lookup(h);
     if (s != SAP_OK) return s;
+    h->shard_steps = 0;
     return reset_state(h);
 }
 
@@ -833,6 +957,7 @@ sap_status sap_min_secant(sap_handle h, int64_t *i, int64_t *j, double *ratio)
 {
     CHECK_HANDLE(h);
     NOT_BATCH(h);
+    NOT_SHARD(h);
     if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
     sap_status s = enqueue_iteration(h, 0.0, 1);
     if (s != SAP_OK) return s;
@@ -843,11 +968,92 @@ sap_status sap_step(sap_handle h, double alpha, int64_t *i, int64_t *j, double *
 {
     CHECK_HANDLE(h);
     NOT_BATCH(h);
+    NOT_SHARD(h);
     if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
     if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(h, SAP_E_ARG, "alpha must be in [0, 1]");
     sap_status s = enqueue_iteration(h, alpha, 0);
     if (s != SAP_OK) return s;
     if (i || j || ratio) return read_last(h, i, j, ratio);
+    return SAP_OK;
+}
+
+// ---------------------------------------------------------------- shards --
+
+static_assert(sizeof(sap_record) == sizeof(Partial), "a record is the recheck's (q, i, j)");
+
+// The ranks' records to the candidate list of the FP64 recheck (its count in
+// st->cnt1); records without a pair are skipped.
+__global__ void records_to_list_kernel(const Partial *recs, int count, int2 *list, ProbState *st)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int c = 0;
+        for (int e = 0; e < count; ++e)
+            if (recs[e].i >= 0) list[c++] = make_int2(recs[e].i, recs[e].j);
+        st->cnt1 = c;
+    }
+}
+
+sap_status sap_shard_min(sap_handle h, sap_record *rec_out, int out_is_device)
+{
+    CHECK_HANDLE(h);
+    NOT_BATCH(h);
+    if (h->shard_world <= 1) return fail(h, SAP_E_STATE, "not a shard handle (sap_create_shard)");
+    if (!rec_out) return fail(h, SAP_E_ARG, "rec_out is NULL");
+    if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
+    sap_status s = enqueue_iteration(h, 0.0, 1, h->shard_rec);
+    if (s != SAP_OK) return s;
+    if (out_is_device) {
+        CK(cudaMemcpyAsync(rec_out, h->shard_rec, sizeof(sap_record), cudaMemcpyDeviceToDevice, h->stream));
+        return SAP_OK;
+    }
+    CK(cudaMemcpyAsync(rec_out, h->shard_rec, sizeof(sap_record), cudaMemcpyDeviceToHost, h->stream));
+    return sync_and_status(h);
+}
+
+sap_status sap_shard_step(sap_handle h, double alpha, const sap_record *recs, int32_t count, int recs_is_device)
+{
+    CHECK_HANDLE(h);
+    NOT_BATCH(h);
+    if (h->shard_world <= 1) return fail(h, SAP_E_STATE, "not a shard handle (sap_create_shard)");
+    if (!recs || count < 1 || count > 4096 || count > h->cap) return fail(h, SAP_E_ARG, "1 <= count <= 4096 records");
+    if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(h, SAP_E_ARG, "alpha must be in [0, 1]");
+    // the history grows by one entry per step, keeping what it holds
+    if (h->shard_steps + 1 > h->hist_cap) {
+        const int cap = 2 * h->hist_cap;
+        double *nh = nullptr;
+        int2 *na = nullptr;
+        CK(dalloc(&nh, cap));
+        CK(dalloc(&na, cap));
+        CK(cudaMemcpyAsync(nh, h->hist, (size_t)h->hist_cap * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(na, h->am, (size_t)h->hist_cap * sizeof(int2), cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(&h->st->hist_cap, &cap, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        drop_graphs(h);
+        dfree(h->hist);
+        dfree(h->am);
+        h->hist = nh;
+        h->am = na;
+        h->hist_cap = cap;
+    }
+    const Partial *src = reinterpret_cast<const Partial *>(recs);
+    if (!recs_is_device) {
+        CK(cudaMemcpyAsync(h->recs, recs, (size_t)count * sizeof(sap_record), cudaMemcpyHostToDevice, h->stream));
+        src = h->recs;
+    }
+    records_to_list_kernel<<<1, 32, 0, h->stream>>>(src, count, h->cand1, h->st);
+    CK(cudaGetLastError());
+    h->launches++;
+    SelectUpdateArgs u = su_args(h, alpha, 0, h->cand1, 1);
+    u.grid = 1;  // a few pairs: one block rechecks them and updates
+    u.pdl = 0;
+    {
+        Timed t(h, K_UPDATE);
+        CK(launch_select_update(u, h->stream));
+    }
+    h->shard_steps++;
+    h->last_iters = h->shard_steps - 1;
+    if (!recs_is_device) return sync_and_status(h);
     return SAP_OK;
 }
 
@@ -888,6 +1094,7 @@ sap_status sap_run(sap_handle h, double alpha, int32_t iters, double *hist, int6
 {
     CHECK_HANDLE(h);
     NOT_BATCH(h);
+    NOT_SHARD(h);
     if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");
     if (iters < 0) return fail(h, SAP_E_ARG, "iters must be >= 0");
     if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(h, SAP_E_ARG, "alpha must be in [0, 1]");
@@ -1051,6 +1258,7 @@ sap_status sap_softmin_forward(sap_handle h, double tau, double *L_out)
 {
     CHECK_HANDLE(h);
     NOT_BATCH(h);
+    NOT_SHARD(h);
     if (!L_out) return fail(h, SAP_E_ARG, "null output");
     return softmin_forward(h, tau, L_out);
 }
@@ -1059,6 +1267,7 @@ sap_status sap_softmin_backward(sap_handle h, double tau, double L, double *G_ou
 {
     CHECK_HANDLE(h);
     NOT_BATCH(h);
+    NOT_SHARD(h);
     return softmin_backward(h, tau, L, G_out, out_is_device);
 }
 
@@ -1066,6 +1275,7 @@ sap_status sap_softmin_ascent(sap_handle h, double tau, double eta, int32_t step
 {
     CHECK_HANDLE(h);
     NOT_BATCH(h);
+    NOT_SHARD(h);
     return softmin_ascent(h, tau, eta, steps, hist);
 }
 
@@ -1074,6 +1284,7 @@ sap_status sap_estimate_dim(sap_handle h, const double *U0, int32_t k_max, int32
 {
     CHECK_HANDLE(h);
     NOT_BATCH(h);
+    NOT_SHARD(h);
     if (!k_out && !ratios_out) return fail(h, SAP_E_ARG, "no output");
     const sap_status s = sweep_run(h, U0, k_max, iters, alpha, threshold, k_out, ratios_out);
     if (s != SAP_OK) return s;

@@ -12,15 +12,21 @@
 // triangle, 64 x 64 tiles, 0 for excluded pairs: d = 0, Sec. II, or d < eps,
 // Sec. VII); the rows R_i (every block owns one block of rows and walks all
 // column blocks, reading the stored upper triangle transposed where needed,
-// so no atomics and a fixed summation order); and C = Xc^T R.  The n x n
-// symmetric eigenproblem goes to cuSOLVER's FP64 divide-and-conquer solver
-// (the paper's own choice of library for this step, Sec. V), loaded at the
-// first call so that the library does not depend on it otherwise.
+// so no atomics and a fixed summation order); and C = Xc^T R.
+//
+// The n x n symmetric eigenproblem (the paper calls cuSolver's SVD for this
+// step, Sec. V) is solved here by the cyclic Jacobi method in FP64 (Golub
+// and Van Loan, Matrix Computations, Sec. 8.5): sweeps of plane rotations,
+// each zeroing one off-diagonal entry (p, q) with the rotation of the 2 x 2
+// symmetric Schur decomposition, in the round-robin ("tournament") order of
+// the parallel variant: n' - 1 rounds of n'/2 disjoint pairs per sweep (n'
+// = n rounded up to even; an odd n's extra index pairs with nobody), so
+// one round is one independent rotation per pair, applied to A from both
+// sides and to the accumulated vectors V.  Sweeps stop when the
+// off-diagonal Frobenius norm is below 4 n 2^-53 of the whole (quadratic
+// convergence: typically 6 to 10 sweeps), or after 40.
 #include "sap_internal.cuh"
 #include "../../include/sap.h"
-
-#include <cusolverDn.h>
-#include <dlfcn.h>
 
 #include <algorithm>
 #include <cmath>
@@ -197,47 +203,105 @@ __global__ void symmetrize_kernel(double *C, int n)
     }
 }
 
-// ---- cuSOLVER, loaded on first use
-struct Solver {
-    bool tried = false, ok = false;
-    cusolverStatus_t (*create)(cusolverDnHandle_t *) = nullptr;
-    cusolverStatus_t (*destroy)(cusolverDnHandle_t) = nullptr;
-    cusolverStatus_t (*set_stream)(cusolverDnHandle_t, cudaStream_t) = nullptr;
-    cusolverStatus_t (*bufsize)(cusolverDnHandle_t, cusolverEigMode_t, cublasFillMode_t, int, const double *, int,
-                                const double *, int *) = nullptr;
-    cusolverStatus_t (*syevd)(cusolverDnHandle_t, cusolverEigMode_t, cublasFillMode_t, int, double *, int, double *,
-                              double *, int, int *) = nullptr;
-};
+// ---- cyclic Jacobi eigensolver (FP64)
 
-Solver &solver()
+// Round r (0 <= r < m - 1) of the round-robin pairing of m (even) indices:
+// index m - 1 meets r, and every other x meets (2r - x) mod (m - 1).
+__device__ __forceinline__ int rr_partner(int x, int r, int m)
 {
-    static Solver s;
-    if (s.tried) return s;
-    s.tried = true;
-    std::vector<std::string> names = {"libcusolver.so.12", "libcusolver.so"};
-    const char *home = std::getenv("CUDA_HOME");
-    names.push_back(std::string(home ? home : "/usr/local/cuda") + "/lib64/libcusolver.so.12");
-    void *lib = nullptr;
-    for (const auto &nm : names)
-        if ((lib = dlopen(nm.c_str(), RTLD_NOW | RTLD_LOCAL))) break;
-    if (!lib) return s;
-    s.create = (decltype(s.create))dlsym(lib, "cusolverDnCreate");
-    s.destroy = (decltype(s.destroy))dlsym(lib, "cusolverDnDestroy");
-    s.set_stream = (decltype(s.set_stream))dlsym(lib, "cusolverDnSetStream");
-    s.bufsize = (decltype(s.bufsize))dlsym(lib, "cusolverDnDsyevd_bufferSize");
-    s.syevd = (decltype(s.syevd))dlsym(lib, "cusolverDnDsyevd");
-    s.ok = s.create && s.destroy && s.set_stream && s.bufsize && s.syevd;
-    return s;
+    if (x == m - 1) return r;
+    if (x == r) return m - 1;
+    int y = (2 * r - x) % (m - 1);
+    return y < 0 ? y + (m - 1) : y;
+}
+
+// The rotation of every pair of round r: for pair (p, q), p < q, with
+// a_pq != 0, tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| +
+// sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c; J = [[c, s], [-s, c]] in
+// the (p, q) plane makes (J^T A J)_pq = 0.  Each index x stores the column
+// combination col'_x = f_x col_x + g_x col_partner: (c, -s) for p, (s, c)
+// read as (c, s) for q.  Unpaired indices (the extra one of an odd n, or
+// a pair with a_pq = 0) keep f = 1, g = 0.
+__global__ void jacobi_angles_kernel(const double *A, int n, int m, int r, double2 *fg, int *partner)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const int y = rr_partner(x, r, m);
+    double f = 1.0, g = 0.0;
+    int pt = x;
+    if (y < n) {
+        const int p = x < y ? x : y, q = x < y ? y : x;
+        const double apq = A[(size_t)p * n + q];
+        if (apq != 0.0) {
+            const double tau = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+            f = c;
+            g = x == p ? -sn : sn;
+            pt = y;
+        }
+    }
+    fg[x] = make_double2(f, g);
+    partner[x] = pt;
+}
+
+// A' = J^T A J entry by entry (each entry reads at most four of A) and
+// V' = V J (each entry reads two of V); one thread per entry.
+__global__ void jacobi_apply_kernel(const double *A, const double *V, int n, const double2 *fg, const int *partner,
+                                    double *A2, double *V2)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * n) return;
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    const double2 ci = fg[i], cj = fg[j];
+    const int pi = partner[i], pj = partner[j];
+    const double a = A[(size_t)i * n + j], b = A[(size_t)i * n + pj];
+    const double c = A[(size_t)pi * n + j], d = A[(size_t)pi * n + pj];
+    // rows combine with (f_i, g_i), columns with (f_j, g_j)
+    A2[(size_t)i * n + j] = ci.x * (cj.x * a + cj.y * b) + ci.y * (cj.x * c + cj.y * d);
+    V2[(size_t)i * n + j] = cj.x * V[(size_t)i * n + j] + cj.y * V[(size_t)i * n + pj];
+}
+
+__global__ void jacobi_init_kernel(double *V, int n)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx < (long long)n * n) V[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+}
+
+// off = sum of squared off-diagonal entries, all = sum of all squares (one
+// block; fixed summation order).
+__global__ void jacobi_norms_kernel(const double *A, int n, double *out)
+{
+    __shared__ double so[32], sa[32];
+    double off = 0.0, all = 0.0;
+    for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
+        const double v = A[idx];
+        all = fma(v, v, all);
+        if (idx / n != idx % n) off = fma(v, v, off);
+    }
+    off = warp_sum(off);
+    all = warp_sum(all);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { so[w] = off; sa[w] = all; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double o = 0.0, a = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { o += so[q]; a += sa[q]; }
+        out[0] = o;
+        out[1] = a;
+    }
 }
 
 struct Scratch {
-    double *w = nullptr, *R = nullptr, *mean = nullptr, *C = nullptr, *lam = nullptr, *work = nullptr;
+    double *w = nullptr, *R = nullptr, *mean = nullptr, *C = nullptr, *C2 = nullptr, *V = nullptr, *V2 = nullptr,
+           *norms = nullptr;
+    double2 *fg = nullptr;
     int2 *tiles = nullptr;
-    int *info = nullptr;
+    int *partner = nullptr;
     ~Scratch()
     {
-        for (void *p : {(void *)w, (void *)R, (void *)mean, (void *)C, (void *)lam, (void *)work, (void *)tiles,
-                        (void *)info})
+        for (void *p : {(void *)w, (void *)R, (void *)mean, (void *)C, (void *)C2, (void *)V, (void *)V2,
+                        (void *)norms, (void *)fg, (void *)tiles, (void *)partner})
             if (p) cudaFree(p);
     }
 };
@@ -248,8 +312,6 @@ sap_status secant_pca(sap_handle h, int k, double *U_out, double *sigma_out)
 {
     const int N = (int)handle_n_points(h), n = handle_n_dim(h);
     if (k < 1 || k > n || k > kMaxK) return handle_fail(h, SAP_E_ARG, "need 1 <= k <= min(n, 32)");
-    Solver &sv = solver();
-    if (!sv.ok) return handle_fail(h, SAP_E_UNSUPPORTED, "cuSOLVER (libcusolver.so.12) could not be loaded");
     cudaStream_t s = handle_stream(h);
     const float *X32 = handle_x32(h);
     const double *X64 = handle_x64(h);
@@ -273,8 +335,12 @@ sap_status secant_pca(sap_handle h, int k, double *U_out, double *sigma_out)
     PCK(cudaMalloc(&sc.R, (size_t)N * n * sizeof(double)));
     PCK(cudaMalloc(&sc.mean, (size_t)n * sizeof(double)));
     PCK(cudaMalloc(&sc.C, (size_t)n * n * sizeof(double)));
-    PCK(cudaMalloc(&sc.lam, (size_t)n * sizeof(double)));
-    PCK(cudaMalloc(&sc.info, sizeof(int)));
+    PCK(cudaMalloc(&sc.C2, (size_t)n * n * sizeof(double)));
+    PCK(cudaMalloc(&sc.V, (size_t)n * n * sizeof(double)));
+    PCK(cudaMalloc(&sc.V2, (size_t)n * n * sizeof(double)));
+    PCK(cudaMalloc(&sc.norms, 2 * sizeof(double)));
+    PCK(cudaMalloc(&sc.fg, (size_t)n * sizeof(double2)));
+    PCK(cudaMalloc(&sc.partner, (size_t)n * sizeof(int)));
     const double eps2 = handle_eps2(h);
     const dim3 lgrid(nb, (n + PC - 1) / PC), ggrid((n + 15) / 16, (n + 15) / 16);
     if (X64) {
@@ -291,40 +357,49 @@ sap_status secant_pca(sap_handle h, int k, double *U_out, double *sigma_out)
     PCK(cudaGetLastError());
     symmetrize_kernel<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, s>>>(sc.C, n);
     PCK(cudaGetLastError());
-    // eigenvalues ascending, eigenvectors in the columns of C (column-major:
-    // C is symmetric, so its row-major storage is the same matrix)
-    cusolverDnHandle_t dn = nullptr;
-    if (sv.create(&dn) != CUSOLVER_STATUS_SUCCESS) return handle_fail(h, SAP_E_CUDA, "cusolverDnCreate failed");
-    int lwork = 0;
-    cusolverStatus_t cs = sv.set_stream(dn, s);
-    if (cs == CUSOLVER_STATUS_SUCCESS)
-        cs = sv.bufsize(dn, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, sc.C, n, sc.lam, &lwork);
-    if (cs == CUSOLVER_STATUS_SUCCESS && cudaMalloc(&sc.work, (size_t)std::max(lwork, 1) * sizeof(double)) != cudaSuccess)
-        cs = CUSOLVER_STATUS_ALLOC_FAILED;
-    if (cs == CUSOLVER_STATUS_SUCCESS)
-        cs = sv.syevd(dn, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n, sc.C, n, sc.lam, sc.work, lwork,
-                      sc.info);
-    int info = 0;
-    if (cs == CUSOLVER_STATUS_SUCCESS &&
-        (cudaMemcpyAsync(&info, sc.info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         cudaStreamSynchronize(s) != cudaSuccess))
-        cs = CUSOLVER_STATUS_EXECUTION_FAILED;
-    sv.destroy(dn);
-    if (cs != CUSOLVER_STATUS_SUCCESS || info != 0)
-        return handle_fail(h, SAP_E_CUDA, "symmetric eigensolver failed");
-    // the k largest: the last k columns, largest first; each signed so that
-    // its entry of largest magnitude is positive
-    std::vector<double> V((size_t)n * k), lam(n);
-    PCK(cudaMemcpy(V.data(), sc.C + (size_t)(n - k) * n, V.size() * sizeof(double), cudaMemcpyDeviceToHost));
-    PCK(cudaMemcpy(lam.data(), sc.lam, n * sizeof(double), cudaMemcpyDeviceToHost));
+    // cyclic Jacobi sweeps: A (= C) towards diag(lambda), V accumulating the
+    // rotations (its columns become the eigenvectors)
+    const unsigned nn_blocks = (unsigned)(((long long)n * n + 255) / 256);
+    jacobi_init_kernel<<<nn_blocks, 256, 0, s>>>(sc.V, n);
+    PCK(cudaGetLastError());
+    const int m = n + (n & 1);
+    double *A = sc.C, *A2 = sc.C2, *V = sc.V, *V2 = sc.V2;
+    const double u = std::ldexp(1.0, -53);
+    bool converged = n == 1;
+    for (int sweep = 0; sweep < 40 && !converged; ++sweep) {
+        for (int r = 0; r < m - 1; ++r) {
+            jacobi_angles_kernel<<<(n + 127) / 128, 128, 0, s>>>(A, n, m, r, sc.fg, sc.partner);
+            jacobi_apply_kernel<<<nn_blocks, 256, 0, s>>>(A, V, n, sc.fg, sc.partner, A2, V2);
+            std::swap(A, A2);
+            std::swap(V, V2);
+        }
+        PCK(cudaGetLastError());
+        jacobi_norms_kernel<<<1, 1024, 0, s>>>(A, n, sc.norms);
+        double nrm[2] = {0.0, 0.0};
+        PCK(cudaMemcpyAsync(nrm, sc.norms, sizeof(nrm), cudaMemcpyDeviceToHost, s));
+        PCK(cudaStreamSynchronize(s));
+        const double tol = 4.0 * n * u;
+        converged = !(nrm[0] > tol * tol * nrm[1]);
+    }
+    if (!converged) return handle_fail(h, SAP_E_CUDA, "Jacobi eigensolver did not converge in 40 sweeps");
+    // the k largest eigenvalues (diagonal of A) and their columns of V,
+    // largest first; each vector signed so that its entry of largest
+    // magnitude is positive
+    std::vector<double> Ah((size_t)n * n), Vh((size_t)n * n);
+    PCK(cudaMemcpy(Ah.data(), A, Ah.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    PCK(cudaMemcpy(Vh.data(), V, Vh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<int> order(n);
+    for (int c = 0; c < n; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return Ah[(size_t)a * n + a] > Ah[(size_t)b * n + b]; });
     for (int c = 0; c < k; ++c) {
-        const double *src = V.data() + (size_t)(k - 1 - c) * n;
+        const int col = order[c];
         int am = 0;
         for (int l = 1; l < n; ++l)
-            if (std::fabs(src[l]) > std::fabs(src[am])) am = l;
-        const double sg = src[am] < 0 ? -1.0 : 1.0;
-        for (int l = 0; l < n; ++l) U_out[(size_t)c * n + l] = sg * src[l];
-        if (sigma_out) sigma_out[c] = std::sqrt(std::max(lam[n - 1 - c], 0.0));
+            if (std::fabs(Vh[(size_t)l * n + col]) > std::fabs(Vh[(size_t)am * n + col])) am = l;
+        const double sg = Vh[(size_t)am * n + col] < 0 ? -1.0 : 1.0;
+        for (int l = 0; l < n; ++l) U_out[(size_t)c * n + l] = sg * Vh[(size_t)l * n + col];
+        if (sigma_out) sigma_out[c] = std::sqrt(std::max(Ah[(size_t)col * n + col], 0.0));
     }
     return SAP_OK;
 #undef PCK

@@ -642,6 +642,7 @@ struct ExplArgs {
     int2 *cand2;
     long long cap2;
     int pdl;
+    int pack;          // extended-precision kernel: write cand2 as packed (i, j, ratio) entries
 };
 
 constexpr int EPW = 4;  // entries per warp per round
@@ -781,23 +782,7 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
     }
 }
 
-// ---- extended-precision explicit recheck (large n)
-__device__ __forceinline__ void xs_two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-// (hi, lo) += x * (yh + yl), the product x * yh error-free
-__device__ __forceinline__ void xs_fma(float &hi, float &lo, float x, float yh, float yl)
-{
-    const float p = __fmul_rn(x, yh);
-    const float pe = fmaf(x, yh, -p);
-    float s, e;
-    xs_two_sum(hi, p, s, e);
-    hi = s;
-    lo = __fadd_rn(lo, __fadd_rn(e, fmaf(x, yl, pe)));
-}
+// ---- extended-precision explicit recheck (large n; helpers in sap_internal.cuh)
 
 // The same tier for large n, where the FP32 dot products' certified error
 // (gamma_{n+3}) would pass too many pairs on: D = fl(x_i - x_j) in FP32, then
@@ -809,10 +794,9 @@ __device__ __forceinline__ void xs_fma(float &hi, float &lo, float x, float yh, 
 template <int K>
 __global__ void __launch_bounds__(256) explicit_df_kernel(ExplArgs a)
 {
-    __shared__ float red[32];
-    __shared__ int scan[33];
-    __shared__ int base_sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // pairs per warp and round: as many as the reduce-scatter holds
+    constexpr int E = (K + 1) <= 8 ? 4 : (K + 1) <= 16 ? 2 : 1;
     // near list first (while the pass may still run), then the pass's candidates
     const float seed = load_pos_float(&a.st->seed_ub);
     for (int seg = 0; seg < (a.pdl ? 2 : 1); ++seg) {
@@ -825,63 +809,84 @@ __global__ void __launch_bounds__(256) explicit_df_kernel(ExplArgs a)
         nn = a.pdl ? 0 : a.n_near;
         total = nn + c1;
     }
-    for (long long base = (long long)blockIdx.x * 8; base < total; base += (long long)gridDim.x * 8) {
-        const long long idx = base + warp;
-        const bool valid = idx < total;
-        const int2 pr = valid ? (idx < nn ? __ldcg(a.near + idx) : __ldcg(a.cand1 + (idx - nn))) : make_int2(0, 0);
-        float zh[K + 1], zl[K + 1];
+    for (long long base = ((long long)blockIdx.x * 8 + warp) * E; base < total; base += (long long)gridDim.x * 8 * E) {
+        int2 pr[E];
+        bool valid[E];
 #pragma unroll
-        for (int q = 0; q <= K; ++q) zh[q] = zl[q] = 0.f;
-        if (valid) {
+        for (int e = 0; e < E; ++e) {
+            const long long idx = base + e;
+            valid[e] = idx < total;
+            pr[e] = valid[e] ? (idx < nn ? __ldcg(a.near + idx) : __ldcg(a.cand1 + (idx - nn))) : make_int2(0, 0);
+        }
+        // any earlier value of the running bound is a valid (looser) bound
+        const float ub2 = load_pos_float(&a.st->run_ub2);
+        float rr;
+        int code;
+        if constexpr ((K + 1) * E <= 32) {
+            df_eval<K, E>(a.X, a.n, a.U32, a.U32lo, a.KP, pr, valid, lane, rr, code);
+        } else {
+            // k = 32: K + 1 sums per pair, one pair per warp, butterfly sums
+            float zh[K + 1], zl[K + 1];
+#pragma unroll
+            for (int q = 0; q <= K; ++q) zh[q] = zl[q] = 0.f;
+            if (valid[0]) {
 #pragma unroll 2
-            for (int l = lane; l < a.n; l += 32) {
-                const float D = a.X[(size_t)pr.x * a.n + l] - a.X[(size_t)pr.y * a.n + l];
-                xs_fma(zh[K], zl[K], D, D, 0.f);
-                const float *uh = a.U32 + (size_t)l * a.KP, *ul = a.U32lo + (size_t)l * a.KP;
+                for (int l = lane; l < a.n; l += 32) {
+                    const float D = a.X[(size_t)pr[0].x * a.n + l] - a.X[(size_t)pr[0].y * a.n + l];
+                    xs_fma(zh[K], zl[K], D, D, 0.f);
+                    const float *uh = a.U32 + (size_t)l * a.KP, *ul = a.U32lo + (size_t)l * a.KP;
 #pragma unroll
-                for (int c = 0; c < K; ++c) xs_fma(zh[c], zl[c], D, __ldcg(uh + c), __ldcg(ul + c));
+                    for (int c = 0; c < K; ++c) xs_fma(zh[c], zl[c], D, __ldcg(uh + c), __ldcg(ul + c));
+                }
             }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
+            for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-            for (int q = 0; q <= K; ++q) {
-                const float h2 = __shfl_xor_sync(0xffffffffu, zh[q], o);
-                const float l2 = __shfl_xor_sync(0xffffffffu, zl[q], o);
-                float s, e;
-                xs_two_sum(zh[q], h2, s, e);
-                zh[q] = s;
-                zl[q] = __fadd_rn(zl[q], __fadd_rn(l2, e));
+                for (int q = 0; q <= K; ++q) {
+                    const float h2 = __shfl_xor_sync(0xffffffffu, zh[q], o);
+                    const float l2 = __shfl_xor_sync(0xffffffffu, zl[q], o);
+                    float s, e;
+                    xs_two_sum(zh[q], h2, s, e);
+                    zh[q] = s;
+                    zl[q] = __fadd_rn(zl[q], __fadd_rn(l2, e));
+                }
+            const float dd = zh[K] + zl[K];
+            float zz = 0.f;
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                const float z = zh[c] + zl[c];
+                zz = fmaf(z, z, zz);
             }
-        const float dd = zh[K] + zl[K];
-        float zz = 0.f;
-#pragma unroll
-        for (int c = 0; c < K; ++c) {
-            const float z = zh[c] + zl[c];
-            zz = fmaf(z, z, zz);
+            code = (lane != 0 || !valid[0]) ? 0 : (dd < 1e-30f ? 2 : 1);  // 2: too short for FP32
+            rr = code == 1 ? sqrtf(zz / dd) : INFINITY;
         }
-        const int code = !valid ? 0 : (dd < 1e-30f ? 2 : 1);  // 2: too short for FP32
-        const float rr = code == 1 ? sqrtf(zz / dd) : INFINITY;
-        const float bmin = block_min(rr, red);
-        float U = fminf(seed, load_pos_float(&a.st->run_ub2));
-        if (bmin < INFINITY) {
-            const float ub = cert_upper(bmin, a.cert);
-            if (threadIdx.x == 0) atomic_min_pos_float(&a.st->run_ub2, ub);
+        const float wmin = warp_min(rr);
+        float U = fminf(seed, ub2);
+        if (wmin < INFINITY) {
+            const float ub = cert_upper(wmin, a.cert);
+            if (lane == 0 && ub < ub2) atomic_min_pos_float(&a.st->run_ub2, ub);
             U = fminf(U, ub);
         }
         const float th = cert_emit_threshold(U, a.cert);
-        const int cnt = (lane == 0 && (code == 2 || (code == 1 && rr <= th))) ? 1 : 0;
-        int tot;
-        const int off = block_exclusive_scan(cnt, scan, &tot);
-        if (tot == 0) continue;
-        if (threadIdx.x == 0) base_sh = (int)atomicAdd((unsigned int *)&a.st->cnt2, (unsigned int)tot);
-        __syncthreads();
-        if (cnt) {
-            const long long pos = (long long)(unsigned int)base_sh + off;
-            if (pos < a.cap2) a.cand2[pos] = pr;
-            else atomicOr(&a.st->status, ST_OVERFLOW);
+        const bool emit = code == 2 || (code == 1 && rr <= th);
+        const unsigned int m = __ballot_sync(0xffffffffu, emit);
+        if (!m) continue;
+        unsigned int b0 = 0;
+        if (lane == 0) b0 = atomicAdd((unsigned int *)&a.st->cnt2, (unsigned int)__popc(m));
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        int2 mp = pr[0];
+#pragma unroll
+        for (int e = 1; e < E; ++e)
+            if (lane == e) mp = pr[e];
+        if (emit) {
+            const long long pos = (long long)b0 + __popc(m & ((1u << lane) - 1u));
+            if (pos < a.cap2) {
+                if (a.pack) reinterpret_cast<unsigned long long *>(a.cand2)[pos] = pack_cand(mp.x, mp.y, rr, code == 2);
+                else a.cand2[pos] = mp;
+            } else {
+                atomicOr(&a.st->status, ST_OVERFLOW);
+            }
         }
-        __syncthreads();
     }
     }
 }
@@ -1056,6 +1061,7 @@ struct RefineArgs {
     int Npad;
     const float *w;          // stored 1/d^2, tile-major upper triangle
     int nb;                  // point blocks per side (Npad / 128)
+    long long tile0;         // global index of the first stored tile
     const float *xn;         // ||x_i||, rounded up
     float beta;              // sqrt(k) (eps_df + 2^-46), rounded up
     const int2 *cand1;
@@ -1108,7 +1114,7 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs a)
                 } else {
                     pr = __ldcg(a.cand1 + (idx - nn));
                     const int I = pr.x >> 7, J = pr.y >> 7;
-                    const long long t = (long long)I * a.nb - (long long)I * (I - 1) / 2 + (J - I);
+                    const long long t = (long long)I * a.nb - (long long)I * (I - 1) / 2 + (J - I) - a.tile0;
                     wv = __ldg(a.w + t * (T * T) + (pr.x & (T - 1)) * T + (pr.y & (T - 1)));
                 }
                 if (!(wv < INFINITY)) {
@@ -1283,15 +1289,6 @@ Cert cert_pass(int n, int k, double b_cap)
 // orthonormal), n^1.5 2^-46 from the hi + lo accumulation; relative: the
 // rounding of d, the FP32 squares and sum of the k components, the division
 // and the square root.
-Cert cert_explicit_df(int n, int k)
-{
-    const double u = std::ldexp(1.0, -24);
-    auto g = [&](double m) { return m * u / (1.0 - m * u); };
-    Cert c;
-    c.A = (float)((u + std::pow((double)n, 1.5) * std::ldexp(1.0, -46)) * 1.1);
-    c.rho = (float)((g(k + 2) + 6 * u) * 1.1);
-    return c;
-}
 
 // Explicit tier in extended precision for large n (the FP32 tier's
 // gamma_{n+3} bound grows with n).
@@ -1428,9 +1425,14 @@ sap_status restructured_prepare(sap_handle h)
         RCK(cudaMalloc(&r.Xlo, (size_t)r.Npad * r.NP * 2));
         RCK(cudaMalloc(&r.counters, 8 * sizeof(unsigned int)));
         const int nb = r.Npad / T;
+        long long t0 = 0, t1 = -1;  // a shard stores the tiles [t0, t1) of the row-major order only
+        handle_shard(h, &t0, &t1);
         std::vector<int2> t;
+        long long g = 0;
         for (int I = 0; I < nb; ++I)
-            for (int J = I; J < nb; ++J) t.push_back(make_int2(I, J));
+            for (int J = I; J < nb; ++J, ++g)
+                if (g >= t0 && (t1 < 0 || g < t1)) t.push_back(make_int2(I, J));
+        r.tile0 = t0;
         r.nwtiles = (int)t.size();
         RCK(cudaMalloc(&r.wtiles, t.size() * sizeof(int2)));
         RCK(cudaMemcpy(r.wtiles, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice));
@@ -1603,10 +1605,10 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         if (eb) cudaEventRecord(eb, s);
         handle_push_timing(h, 1, ea, eb);
     }
-    const int tier = restructured_tier(h);
-    if (tier == 2) {
+    const int tier = restructured_tier_for(h, b.k);
+    if (tier == 2 || tier == 3) {
         // the explicit tier runs inside the FP64 recheck (restructured_fuse_args)
-    } else if (tier == 0) {
+    } else if (tier == 0 || tier == 4) {
         ExplArgs x;
         x.X = handle_x32(h);
         x.N = (int)handle_n_points(h);
@@ -1619,8 +1621,9 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         x.cap1 = (unsigned int)b.cap;
         x.near = r.near;
         x.n_near = r.n_near;
-        const bool df = explicit_uses_df(n);
+        const bool df = tier == 4 || explicit_uses_df(n);
         x.cert = df ? cert_explicit_df(n, b.k) : cert_explicit(n, b.k);
+        x.pack = tier == 4;
         x.st = b.st;
         x.cand2 = b.cand2;
         x.cap2 = b.cap;
@@ -1649,6 +1652,7 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         x.Npad = r.Npad;
         x.w = r.w;
         x.nb = r.Npad / T;
+        x.tile0 = r.tile0;
         x.xn = r.xn;
         x.beta = (float)(std::sqrt((double)b.k) * (df_error_unit(n) + std::ldexp(1.0, -46)) * 1.02);
         x.cand1 = b.cand1;
@@ -1810,13 +1814,17 @@ sap_status restructured_project_df(sap_handle h, float *Yh_out, float *Yl_out, i
     return SAP_OK;
 }
 
-int restructured_tier(sap_handle h)
+int restructured_tier_for(sap_handle h, int k)
 {
     const int t = handle_tune(h).refine;
     const int n = handle_n_dim(h);
+    if (t == 4) return 4;
+    if (t == 3) return k <= 8 ? 3 : 0;
     if (t == 2) return explicit_uses_df(n) ? 0 : 2;
     return (t < 0 ? n > 256 : t != 0) ? 1 : 0;
 }
+
+int restructured_tier(sap_handle h) { return restructured_tier_for(h, handle_k(h)); }
 
 bool restructured_uses_refine(sap_handle h) { return restructured_tier(h) == 1; }
 
@@ -1826,13 +1834,26 @@ void restructured_fuse_args(sap_handle h, const BasisView &b, SelectUpdateArgs &
     u.near = nullptr;
     u.n_near = 0;
     u.cert2 = cert_explicit(handle_n_dim(h), b.k);
-    if (restructured_tier(h) != 2) return;
+    const int tier = restructured_tier_for(h, b.k);
+    if (tier == 4) {
+        // the extended tier's packed list, filtered by the final bound
+        u.fused = 4;
+        u.list = b.cand2;
+        u.which = 2;
+        u.cert2 = cert_explicit_df(handle_n_dim(h), b.k);
+        return;
+    }
+    if (tier != 2 && tier != 3) return;
     RestrState &r = restr_state(h);
-    u.fused = 1;
+    u.fused = tier;
     u.near = r.near;
     u.n_near = r.n_near;
     u.list = b.cand1;
     u.which = 1;
+    if (tier == 3) {
+        u.cert2 = cert_explicit_df(handle_n_dim(h), b.k);
+        u.grid = std::min(std::max(1, handle_tune(h).expl_per_sm) * handle_sms(h), kRecheckBlocks);
+    }
 }
 
 int restructured_kernels_per_iteration(sap_handle h)
@@ -1840,7 +1861,7 @@ int restructured_kernels_per_iteration(sap_handle h)
     // product (+ slice sum), pass, and the explicit tier, or the double-float
     // product + refine tier, or nothing (fused into the FP64 recheck)
     const int tier = restructured_tier(h);
-    return 2 + (tier == 1 ? 2 : tier == 0 ? 1 : 0) + (restr_state(h).ksplit > 1 ? 1 : 0);
+    return 2 + (tier == 1 ? 2 : (tier == 0 || tier == 4) ? 1 : 0) + (restr_state(h).ksplit > 1 ? 1 : 0);  // 2, 3: fused
 }
 
 void restructured_free(sap_handle h)

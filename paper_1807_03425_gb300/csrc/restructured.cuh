@@ -25,6 +25,7 @@ struct RestrState {
     uint16_t *wb = nullptr;
     int2 *wtiles = nullptr;   // (I, J) per tile, I <= J
     int nwtiles = 0;
+    long long tile0 = 0;      // global index of the first stored tile (a shard's range starts there)
     int2 *near = nullptr;     // pairs the pass skips, evaluated by the refine tier
     float *near_w = nullptr;  // their 1/d^2 (FP32; +inf when too short for FP32)
     unsigned int near_cap = 0;
@@ -70,6 +71,7 @@ void handle_count_launch(sap_handle h, int cls, cudaEvent_t *a, cudaEvent_t *b);
 void handle_push_timing(sap_handle h, int cls, cudaEvent_t a, cudaEvent_t b);
 sap_status handle_fail(sap_handle h, sap_status s, const char *msg);
 TuneParams &handle_tune(sap_handle h);
+void handle_shard(sap_handle h, long long *t0, long long *t1);  // stored tile range (all tiles: 0, -1)
 
 // One basis of the restructured form: the handle's own, or one of the bases
 // of a dimension sweep that share the handle's dataset, lengths and near list.
@@ -99,11 +101,17 @@ int restructured_kernels_per_iteration(sap_handle h);
 // Second tier of the restructured form: 0 explicit differences (own
 // launch), 1 double-float Y + refine, 2 explicit differences fused into the
 // FP64 recheck (tuning value 2; only where the plain FP32 explicit tier
-// applies, n <= 256, else 0).
+// applies, n <= 256, else 0), 3 explicit differences in extended precision
+// fused into the FP64 recheck on the tier's grid (tuning value 3; k <= 8,
+// else 0), 4 explicit differences in extended precision in their own
+// launch, whose list carries each pair's ratio so that the FP64 recheck
+// evaluates only the pairs within the final bound (tuning value 4).
 int restructured_tier(sap_handle h);
+int restructured_tier_for(sap_handle h, int k);
 bool restructured_uses_refine(sap_handle h);
 // Fills the fused-tier fields of the FP64 recheck of basis b (fused = 0
-// unless the tier is 2; then list/which name the pass's candidates).
+// unless the tier is 2 or 3; then list/which name the pass's candidates,
+// and for tier 3 the grid is the tier's).
 void restructured_fuse_args(sap_handle h, const BasisView &b, SelectUpdateArgs &u);
 void restructured_free(sap_handle h);
 void restructured_stats(sap_handle h, sap_stats *out);

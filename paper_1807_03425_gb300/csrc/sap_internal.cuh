@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace sap {
 
 // Programmatic dependent launch.  A kernel launched with launch_pdl may start
@@ -89,7 +91,9 @@ struct TuneParams {
     int su_blocks = 0;       // FP64 recheck + update: blocks (0: one per SM)
     int plain_per_sm = 2;    // plain pass: blocks per SM (FP64 data: twice as many)
     int pdl = 0;             // programmatic dependent launch between the kernels of an iteration
-    int refine = -1;         // second tier: 1 double-float refine, 0 explicit differences, -1 by n (> 256: refine)
+    int refine = -1;         // second tier: 1 double-float refine, 0 explicit differences, 2 / 3 explicit
+                             // (FP32 / extended precision) fused into the FP64 recheck, 4 extended precision
+                             // with ratios for a final filter, -1 by n (> 256: refine)
     double us_per_iter = 0;  // measured by the tuner (0: not tuned)
 };
 
@@ -115,17 +119,44 @@ struct ProbState {
     alignas(128) unsigned int tile_next;
 };
 
+// Certified error model of one tier (see the header comment).
+struct Cert {
+    float A;
+    float rho;
+};
+
 // Best pair of one recheck block (FP64).
 struct Partial {
     double r;
     int i, j;
 };
 
-// Certified error model of one tier (see the header comment).
-struct Cert {
-    float A;
-    float rho;
-};
+
+// Error model of the explicit-difference tier in extended precision: D =
+// fl(x_i - x_j) moves U^T D and d by at most 2^-24 d (U orthonormal), so
+// |r~ - r| <= 2^-24 (+ n^1.5 2^-46 for the hi + lo accumulation) absolute,
+// plus the final FP32 roundings of the k + 2 terms relative.
+__host__ __device__ inline Cert cert_explicit_df(int n, int k)
+{
+    const double u = 5.9604644775390625e-8;  // 2^-24
+    const double g = (k + 2) * u / (1.0 - (k + 2) * u);
+    Cert c;
+    c.A = (float)((u + (double)n * sqrt((double)n) * 1.4210854715202004e-14) * 1.1);  // 2^-46
+    c.rho = (float)((g + 6 * u) * 1.1);
+    return c;
+}
+
+// The same model evaluated in FP32 on the device (the 1.1 margin covers
+// the rounding of this arithmetic; FP64 scalar operations are slow here).
+__device__ __forceinline__ Cert cert_explicit_df_dev(int n, int k)
+{
+    const float u = 5.9604644775390625e-8f;
+    const float g = (k + 2) * u / (1.0f - (k + 2) * u);
+    Cert c;
+    c.A = (u + (float)n * sqrtf((float)n) * 1.4210854715202004e-14f) * 1.1f;
+    c.rho = (g + 6 * u) * 1.1f;
+    return c;
+}
 
 __device__ __forceinline__ float cert_upper(float rt, Cert c)
 {
@@ -256,6 +287,140 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *scratch, int *to
     return (w > 0 ? scratch[w - 1] : 0) + x - v;
 }
 
+// Extended-precision FP32 arithmetic for the explicit-difference tiers:
+// s + e = a + b exactly (Knuth's two-sum; the _rn intrinsics keep the
+// compiler from contracting the steps into FMAs).
+__device__ __forceinline__ void xs_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) += x * (yh + yl), the product x * yh error-free
+__device__ __forceinline__ void xs_fma(float &hi, float &lo, float x, float yh, float yl)
+{
+    const float p = __fmul_rn(x, yh);
+    const float pe = fmaf(x, yh, -p);
+    float s, e;
+    xs_two_sum(hi, p, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, fmaf(x, yl, pe)));
+}
+
+// Reduce-scatter of the extended-precision sums of E pairs, then lane e < E
+// forms pair e's ratio (rr, code as in df_eval below).
+template <int K, int E>
+__device__ __forceinline__ void df_finish(float (&zh)[E][K + 1], float (&zl)[E][K + 1], const bool (&valid)[E],
+                                          int lane, float &rr, int &code)
+{
+    // Reduce-scatter of the E (K + 1) double-float sums (halving exchanges,
+    // each addition an exact two-sum of the high parts with the low parts
+    // added), then lane e < E gathers its pair's K + 1 totals.
+    constexpr int M = E * (K + 1);
+    static_assert(M <= 32, "pairs per warp times components");
+    constexpr int S = M <= 8 ? 8 : M <= 16 ? 16 : 32;
+    constexpr int dup = 32 / S;
+    float h[S], lo[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        h[q] = q < M ? zh[q < M ? q / (K + 1) : 0][q < M ? q % (K + 1) : 0] : 0.f;
+        lo[q] = q < M ? zl[q < M ? q / (K + 1) : 0][q < M ? q % (K + 1) : 0] : 0.f;
+    }
+#pragma unroll
+    for (int lvl = 0; (S >> lvl) > 1; ++lvl) {
+        const int half = (S >> lvl) / 2, o = 16 >> lvl;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float sh_ = up ? h[i] : h[i + half], sl = up ? lo[i] : lo[i + half];
+            const float kh = up ? h[i + half] : h[i], kl = up ? lo[i + half] : lo[i];
+            const float rh = __shfl_xor_sync(0xffffffffu, sh_, o), rl = __shfl_xor_sync(0xffffffffu, sl, o);
+            float sum, er;
+            xs_two_sum(kh, rh, sum, er);
+            h[i] = sum;
+            lo[i] = __fadd_rn(kl, __fadd_rn(rl, er));
+        }
+    }
+#pragma unroll
+    for (int o = 16 / S; o > 0; o >>= 1) {
+        const float rh = __shfl_xor_sync(0xffffffffu, h[0], o), rl = __shfl_xor_sync(0xffffffffu, lo[0], o);
+        float sum, er;
+        xs_two_sum(h[0], rh, sum, er);
+        h[0] = sum;
+        lo[0] = __fadd_rn(lo[0], __fadd_rn(rl, er));
+    }
+    const float tot = h[0] + lo[0];
+    const int me = lane < E ? lane : 0;
+    float z[K + 1];
+#pragma unroll
+    for (int q = 0; q <= K; ++q) z[q] = __shfl_sync(0xffffffffu, tot, (me * (K + 1) + q) * dup);
+    const float dd = z[K];
+    float zz = 0.f;
+#pragma unroll
+    for (int c = 0; c < K; ++c) zz = fmaf(z[c], z[c], zz);
+    bool v = false;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (lane == e) v = valid[e];
+    code = (lane >= E || !v) ? 0 : (dd < 1e-30f ? 2 : 1);
+    rr = code == 1 ? sqrtf(zz / dd) : INFINITY;
+}
+
+// Extended-precision explicit evaluation of E pairs by one warp (the
+// extended-precision second tiers): D = fl(x_i - x_j) in FP32, then |D|^2 and U^T D as
+// hi + lo FP32 sums with error-free products against the hi + lo FP32 basis.
+// Since U is orthonormal, the rounding of D moves U^T D and d by at most
+// 2^-24 d, so the ratio's error is 2^-24 absolute plus small relative terms
+// (the error model of the explicit extended-precision tier).  On return lane
+// e < E holds pair e's ratio in rr with code 1, or code 2 when |D|^2 is too
+// small for FP32 (decided in FP64 downstream); other lanes get code 0.
+template <int K, int E>
+__device__ __forceinline__ void df_eval(const float *X, int n, const float *U32, const float *U32lo, int KP,
+                                        const int2 (&pr)[E], const bool (&valid)[E], int lane, float &rr,
+                                        int &code)
+{
+    float zh[E][K + 1], zl[E][K + 1];
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int q = 0; q <= K; ++q) zh[e][q] = zl[e][q] = 0.f;
+#pragma unroll 2
+    for (int l = lane; l < n; l += 32) {
+        float uh[K], ul[K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            uh[c] = __ldcg(U32 + (size_t)l * KP + c);
+            ul[c] = __ldcg(U32lo + (size_t)l * KP + c);
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float D = X[(size_t)pr[e].x * n + l] - X[(size_t)pr[e].y * n + l];
+            xs_fma(zh[e][K], zl[e][K], D, D, 0.f);
+#pragma unroll
+            for (int c = 0; c < K; ++c) xs_fma(zh[e][c], zl[e][c], D, uh[c], ul[c]);
+        }
+    }
+    df_finish<K, E>(zh, zl, valid, lane, rr, code);
+}
+
+// A candidate with its extended-precision ratio packed in 64 bits: i and j
+// take 17 bits each (N <= 92681), the ratio's FP32 bits without the lowest
+// (truncation rounds down, so a filter on it keeps a superset); a pair too
+// short for FP32 carries ratio 0 (always kept).
+__device__ __forceinline__ unsigned long long pack_cand(int i, int j, float r, bool short_pair)
+{
+    const unsigned long long rb = short_pair ? 0ull : (unsigned long long)(__float_as_uint(r) >> 1);
+    return ((unsigned long long)i << 47) | ((unsigned long long)j << 30) | rb;
+}
+__device__ __forceinline__ float packed_ratio(unsigned long long v)
+{
+    return __uint_as_float((unsigned int)(v & 0x3fffffffull) << 1);
+}
+__device__ __forceinline__ int2 packed_pair(unsigned long long v)
+{
+    return make_int2((int)(v >> 47), (int)((v >> 30) & 0x1ffffull));
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launchers (implemented in the .cu files, called by the engine).
 
@@ -323,14 +488,23 @@ struct SelectUpdateArgs {
     int2 *argmin;          // hist_cap entries
     Cert seed_cert;        // error model of the seed evaluation
     int pdl;               // launch with programmatic stream serialization
-    // fused second tier (restructured form): phase 1 takes the near pairs and
-    // the pass's candidates (list, count in st->cnt1), filters each by
-    // explicit FP32 differences under cert2 and evaluates the survivors in
-    // FP64 at once (FP32 data only)
+    // fused second tier (restructured form, FP32 data only):
+    //  fused == 2: phase 1 takes the near pairs and the pass's candidates
+    //    (list, count in st->cnt1), filters each by explicit FP32
+    //    differences under cert2 and evaluates the survivors in FP64 at once;
+    //  fused == 3: the same pairs from explicit differences in extended
+    //    precision (cert2), each survivor evaluated in FP64 at once by the
+    //    same warp (k <= 8; the grid is the tier's);
+    //  fused == 4: the list (count in st->cnt2) holds the extended-precision
+    //    tier's packed (i, j, ratio) entries; those within the final bound
+    //    (cert2) are evaluated in FP64
     int fused;
     const int2 *near;
     int n_near;
     Cert cert2;
+    // shard evaluation (eval_only): the best pair (q = r^2, i, j; i = -1 if
+    // none) goes here instead of the history, and no status bit is set
+    Partial *shard_rec = nullptr;
 };
 cudaError_t launch_select_update(const SelectUpdateArgs &a, cudaStream_t s);
 

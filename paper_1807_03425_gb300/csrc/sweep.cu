@@ -186,6 +186,7 @@ SelectUpdateArgs update_args(sap_handle h, SweepState &sw, SweepBasis &b, double
     BasisView v;
     v.k = b.k;
     v.cand1 = b.cand1;
+    v.cand2 = b.cand2;
     restructured_fuse_args(h, v, u);
     return u;
 }

@@ -99,3 +99,15 @@ def test_tuning_calls_validate_without_device(lib):
     assert lib.sap_get_tuning(None, ctypes.byref(t)) == 1
     assert lib.sap_set_tuning(None, ctypes.byref(t)) == 1
     assert lib.sap_set_pass_bound(None, 1e-3) == 1
+
+
+def test_failure_hooks_validate_arguments(lib):
+    """The test hooks refuse bad arguments on the host; without a device the
+    wait reports SAP_E_NO_DEVICE (on a GPU machine it is exercised by the GPU
+    tests)."""
+    assert capi.sap_status_str(lib.sap_inject_fault(None, 1)) == "SAP_E_ARG"
+    assert capi.sap_status_str(lib.sap_selftest_wait(None, -1)) == "SAP_E_ARG"
+    assert capi.sap_status_str(lib.sap_selftest_wait(None, 5_000_000_000)) == "SAP_E_ARG"
+    import torch
+    if not torch.cuda.is_available():
+        assert capi.sap_status_str(lib.sap_selftest_wait(None, 1000)) == "SAP_E_NO_DEVICE"

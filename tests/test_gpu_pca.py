@@ -1,6 +1,6 @@
 """The PCA start of Algorithm 1 (sap_secant_pca): the top k left singular
 vectors of the unit-secant matrix, formed on the device in FP64 as
-Xc^T L X and diagonalised by cuSOLVER, against the FP64 oracle (which sums
+Xc^T L X and diagonalised by the library's FP64 Jacobi solver, against the FP64 oracle (which sums
 s s^T pair by pair and diagonalises with numpy)."""
 import numpy as np
 import pytest
@@ -33,9 +33,11 @@ def compare(Ug, svg, Uo, svo):
     assert np.abs(Ug @ Ug.T - np.eye(Ug.shape[0])).max() < 1e-12
 
 
-@pytest.mark.parametrize("N,n,k", [(300, 7, 1), (517, 40, 3), (700, 100, 5), (65, 12, 12)])
+@pytest.mark.parametrize("N,n,k", [(300, 7, 1), (517, 40, 3), (700, 100, 5), (65, 12, 12), (130, 1, 1),
+                                   (300, 33, 4)])
 def test_secant_pca_matches_oracle(P, N, n, k):
-    """Ragged point counts around the 64-point blocks, k up to n."""
+    """Ragged point counts around the 64-point blocks, k up to n; odd n (the
+    Jacobi round-robin has an unpaired index) and n = 1."""
     X = scaled(N, n, N + n)
     with P.Sap(X) as s:
         Ug, svg = s.secant_pca(k)

@@ -48,6 +48,12 @@ EXTREMES = [
          programmatic_launch=1, refine_tier=2),
     dict(pass_bound=8e-3, pass_stages=0, explicit_blocks_per_sm=1, update_blocks=38, plain_blocks_per_sm=2,
          programmatic_launch=0, refine_tier=2),
+    dict(pass_bound=4e-3, pass_stages=0, explicit_blocks_per_sm=1, update_blocks=76, plain_blocks_per_sm=2,
+         programmatic_launch=1, refine_tier=3),
+    dict(pass_bound=5e-4, pass_stages=3, explicit_blocks_per_sm=4, update_blocks=0, plain_blocks_per_sm=2,
+         programmatic_launch=0, refine_tier=3),
+    dict(pass_bound=4e-3, pass_stages=0, explicit_blocks_per_sm=2, update_blocks=152, plain_blocks_per_sm=2,
+         programmatic_launch=1, refine_tier=4),
 ]
 
 

@@ -144,9 +144,15 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
                 if (a.ksplit == 1) {
                     // block-major: the KY components of each 128-row block are contiguous
                     float *yb = a.Y + (size_t)(row >> 7) * ((size_t)a.KY * 128) + (row & 127);
+                    float *yd = a.Yd ? a.Yd + (size_t)(row >> 7) * ((size_t)a.KY * 256) + yd_offset(row & 127)
+                                     : nullptr;
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
-                        if (c0 + q < a.KY) yb[(size_t)(c0 + q) * 128] = fmaf(d2[q], a.lo_scale, d1[q]) * a.out_scale;
+                        if (c0 + q < a.KY) {
+                            const float y = fmaf(d2[q], a.lo_scale, d1[q]) * a.out_scale;
+                            yb[(size_t)(c0 + q) * 128] = y;
+                            if (yd) *reinterpret_cast<float2 *>(yd + (size_t)(c0 + q) * 256) = make_float2(y, y);
+                        }
                 } else {
                     float *dst = a.Ypart + (size_t)blockIdx.y * a.KY * a.Npad;
 #pragma unroll
@@ -164,15 +170,20 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
 }
 
 // Y = (sum of the K slices, in slice order) * out_scale; the slices are
-// component-major (c * Npad + row), Y block-major like the product's output.
-__global__ void ksum_kernel(const float *Ypart, int ksplit, int KY, int Npad, float out_scale, float *Y)
+// component-major (c * Npad + row), Y (and Yd) block-major like the
+// product's output.
+__global__ void ksum_kernel(const float *Ypart, int ksplit, int KY, int Npad, float out_scale, float *Y, float *Yd)
 {
     const size_t count = (size_t)KY * Npad;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
         float s = Ypart[e];
         for (int q = 1; q < ksplit; ++q) s += Ypart[(size_t)q * count + e];
         const size_t c = e / Npad, row = e % Npad;
-        Y[(row >> 7) * ((size_t)KY * 128) + c * 128 + (row & 127)] = s * out_scale;
+        const float y = s * out_scale;
+        Y[(row >> 7) * ((size_t)KY * 128) + c * 128 + (row & 127)] = y;
+        if (Yd)
+            *reinterpret_cast<float2 *>(Yd + (row >> 7) * ((size_t)KY * 256) + c * 256 + yd_offset((int)(row & 127))) =
+                make_float2(y, y);
     }
 }
 
@@ -207,7 +218,7 @@ cudaError_t launch_gemm_y(const GemmArgs &a, cudaStream_t s)
     if (e != cudaSuccess || ksplit == 1) return e;
     const size_t count = (size_t)a.KY * a.Npad;
     ksum_kernel<<<(unsigned)std::min<size_t>((count + 255) / 256, 2048), 256, 0, s>>>(a.Ypart, ksplit, a.KY, a.Npad,
-                                                                                    a.out_scale, a.Y);
+                                                                                    a.out_scale, a.Y, a.Yd);
     return cudaGetLastError();
 }
 

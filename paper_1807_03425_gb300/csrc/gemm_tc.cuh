@@ -10,6 +10,10 @@ struct GemmArgs {
     CUtensorMap ta_hi, ta_lo;   // X split parts: Npad x NP, 16-bit, box 64 x 128
     CUtensorMap tb_hi, tb_lo;   // U split parts: KPG x NP, 16-bit, box 64 x KPG
     float *Y;                   // FP32, block-major: [Npad/128][KY][128]
+    // optional second copy for the row side of the all-pairs pass: per
+    // block and component 256 floats, row a = 16 r + g at g * 16 + (r / 2) * 4
+    // + (r % 2) * 2, written twice ({y, y} pairs)
+    float *Yd;
     int KY;                     // components written (multiple of 4, <= KPG)
     int Npad;                   // rows (multiple of 128)
     int nkb;                    // K blocks of 64

@@ -382,6 +382,7 @@ sap_status secant_pca(sap_handle h, int k, double *U_out, double *sigma_out)
         converged = !(nrm[0] > tol * tol * nrm[1]);
     }
     if (!converged) return handle_fail(h, SAP_E_CUDA, "Jacobi eigensolver did not converge in 40 sweeps");
+    PCK(cudaStreamSynchronize(s));  // the copies below run on the legacy stream
     // the k largest eigenvalues (diagonal of A) and their columns of V,
     // largest first; each vector signed so that its entry of largest
     // magnitude is positive

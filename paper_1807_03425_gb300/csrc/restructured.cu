@@ -270,6 +270,7 @@ struct PassArgs {
     const int2 *wtiles;
     int ntiles;
     const float *Y;   // this basis's first component in block 0 of the block-major Y
+    const float *Yd;  // the same in the doubled row-side copy (block stride Ykt * 256 floats)
     int KY;           // components of this basis
     int Ykt;          // components per block of the Y buffer (block stride / 128)
     int Npad;
@@ -283,12 +284,16 @@ struct PassArgs {
     int pdl;
 };
 
-// One ring stage: the BF16 1/d^2 tile (32 KB), then for each side the basis's
-// components of the point block (block-major Y: one copy), then the 128 point
-// norms nu of each side.
-__host__ __device__ inline uint32_t pass_stage_bytes(int KY)
+// One ring stage: the BF16 1/d^2 tile (32 KB), then the row side's point
+// block -- for k <= 8 the k used components of the doubled copy ({y, y}
+// pairs, 1 KB each), else the KY components of Y -- and the column side's
+// (k, else KY, components of Y; one copy each, block-major), then the 128
+// point norms nu of each side.
+__host__ __device__ inline uint32_t pass_row_bytes(int k, int KY) { return k <= 8 ? (uint32_t)k * T * 8 : (uint32_t)T * KY * 4; }
+__host__ __device__ inline uint32_t pass_col_bytes(int k, int KY) { return k <= 8 ? (uint32_t)k * T * 4 : (uint32_t)T * KY * 4; }
+__host__ __device__ inline uint32_t pass_stage_bytes(int k, int KY)
 {
-    return (uint32_t)T * T * 2 + 2u * T * KY * 4 + 2u * T * 4;
+    return (uint32_t)T * T * 2 + pass_row_bytes(k, KY) + pass_col_bytes(k, KY) + 2u * T * 4;
 }
 
 // Certified error of one stored pair's ratio from the tensor-core Y:
@@ -350,7 +355,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int KY = a.KY, S = a.stages;
-    const uint32_t wbytes = T * T * 2, ybytes = T * KY * 4, sbytes = wbytes + 2 * ybytes + 2 * T * 4;
+    constexpr bool DBL = CPT == 4;  // row side from the doubled copy (k = K <= 8)
+    const uint32_t wbytes = T * T * 2, ibytes = pass_row_bytes(DBL ? K : 9, KY),
+                   jbytes = pass_col_bytes(DBL ? K : 9, KY), sbytes = wbytes + ibytes + jbytes + 2 * T * 4;
     // tiles below gridDim.x * S are static (it < S); the rest are dynamic
     const int nall = blockIdx.x < (unsigned)a.ntiles ? (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     const int nstatic = nall < S ? nall : S;
@@ -379,16 +386,17 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 unsigned char *base = sm + (size_t)it * sbytes;
                 tc::mbar_expect_tx(&full[it], sbytes);
                 tc::bulk_g2s(base, a.wb + (size_t)t * T * T, wbytes, &full[it]);
-                tc::bulk_g2s(base + wbytes + 2 * ybytes, a.nu + (size_t)IJ.x * T, T * 4, &full[it]);
-                tc::bulk_g2s(base + wbytes + 2 * ybytes + T * 4, a.nu + (size_t)IJ.y * T, T * 4, &full[it]);
+                tc::bulk_g2s(base + wbytes + ibytes + jbytes, a.nu + (size_t)IJ.x * T, T * 4, &full[it]);
+                tc::bulk_g2s(base + wbytes + ibytes + jbytes + T * 4, a.nu + (size_t)IJ.y * T, T * 4, &full[it]);
             }
             grid_dep_wait();
             grid_dep_launch();
             for (int it = 0; it < pre; ++it) {
                 const int2 IJ = sIJ[it];
                 unsigned char *base = sm + (size_t)it * sbytes;
-                tc::bulk_g2s(base + wbytes, a.Y + (size_t)IJ.x * a.Ykt * T, ybytes, &full[it]);
-                tc::bulk_g2s(base + wbytes + ybytes, a.Y + (size_t)IJ.y * a.Ykt * T, ybytes, &full[it]);
+                if (DBL) tc::bulk_g2s(base + wbytes, a.Yd + (size_t)IJ.x * a.Ykt * 2 * T, ibytes, &full[it]);
+                else tc::bulk_g2s(base + wbytes, a.Y + (size_t)IJ.x * a.Ykt * T, ibytes, &full[it]);
+                tc::bulk_g2s(base + wbytes + ibytes, a.Y + (size_t)IJ.y * a.Ykt * T, jbytes, &full[it]);
             }
             int issued = pre;
             bool marked = false;
@@ -427,10 +435,11 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 tc::mbar_expect_tx(&full[s], sbytes);
                 tc::bulk_g2s(base, a.wb + (size_t)t * T * T, wbytes, &full[s]);
                 // one copy per side: the basis's components of the point block
-                tc::bulk_g2s(base + wbytes, a.Y + (size_t)IJ.x * a.Ykt * T, ybytes, &full[s]);
-                tc::bulk_g2s(base + wbytes + ybytes, a.Y + (size_t)IJ.y * a.Ykt * T, ybytes, &full[s]);
-                tc::bulk_g2s(base + wbytes + 2 * ybytes, a.nu + (size_t)IJ.x * T, T * 4, &full[s]);
-                tc::bulk_g2s(base + wbytes + 2 * ybytes + T * 4, a.nu + (size_t)IJ.y * T, T * 4, &full[s]);
+                if (DBL) tc::bulk_g2s(base + wbytes, a.Yd + (size_t)IJ.x * a.Ykt * 2 * T, ibytes, &full[s]);
+                else tc::bulk_g2s(base + wbytes, a.Y + (size_t)IJ.x * a.Ykt * T, ibytes, &full[s]);
+                tc::bulk_g2s(base + wbytes + ibytes, a.Y + (size_t)IJ.y * a.Ykt * T, jbytes, &full[s]);
+                tc::bulk_g2s(base + wbytes + ibytes + jbytes, a.nu + (size_t)IJ.x * T, T * 4, &full[s]);
+                tc::bulk_g2s(base + wbytes + ibytes + jbytes + T * 4, a.nu + (size_t)IJ.y * T, T * 4, &full[s]);
                 ++issued;
             }
             // no copy of ours may still be in flight when the block exits
@@ -464,8 +473,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
         if (IJ.x < 0) break;  // the producer has no more tiles
         const float gnow = load_pos_float(&a.st->run_ub1);  // consumed after the tile
         const uint16_t *hs = reinterpret_cast<const uint16_t *>(sm + (size_t)s * sbytes);
-        const float *yI = reinterpret_cast<const float *>(sm + (size_t)s * sbytes + wbytes);  // yI[c * T + a]
-        const float *yJ = yI + T * KY;
+        // row side: yI[c * T + a], or (DBL) the doubled copy yI[c * 2T + yd_offset(a)]
+        const float *yI = reinterpret_cast<const float *>(sm + (size_t)s * sbytes + wbytes);
+        const float *yJ = reinterpret_cast<const float *>(sm + (size_t)s * sbytes + wbytes + ibytes);  // yJ[c * T + b]
 
         float v[RPW][CPT];
         float mymin = INFINITY;
@@ -491,9 +501,18 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                     for (int p = 0; p < NPR; ++p) s2[h][p] = 0ull;
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
-                    const float yca = yI[c * T + row0 + r0 * RSTEP];        // broadcast
-                    const float ycb = yI[c * T + row0 + (r0 + 1) * RSTEP];  // broadcast
-                    const uint64_t yya = tc::pk2(yca, yca), yyb = tc::pk2(ycb, ycb);
+                    // rows row0 + r0 RSTEP and the next, each as a {y, y} pair (broadcast)
+                    uint64_t yya, yyb;
+                    if constexpr (DBL) {
+                        const ulonglong2 yy = *reinterpret_cast<const ulonglong2 *>(yI + c * 2 * T + row0 * 16 + (r0 >> 1) * 4);
+                        yya = yy.x;
+                        yyb = yy.y;
+                    } else {
+                        const float yca = yI[c * T + row0 + r0 * RSTEP];
+                        const float ycb = yI[c * T + row0 + (r0 + 1) * RSTEP];
+                        yya = tc::pk2(yca, yca);
+                        yyb = tc::pk2(ycb, ycb);
+                    }
 #pragma unroll
                     for (int p = 0; p < NPR; ++p) {
                         const uint64_t ea = tc::sub2(yya, yj2[p][c]);
@@ -553,7 +572,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
             if (lane == 0) tc::mbar_arrive(&empty[s]);
             continue;
         }
-        const float *nuI = yJ + T * KY;
+        const float *nuI = reinterpret_cast<const float *>(sm + (size_t)s * sbytes + wbytes + ibytes + jbytes);
         const float *nuJ = nuI + T;
         if (refine) {
             // the bound of the tile's minimum from that pair's own error
@@ -1354,12 +1373,12 @@ sap_status classify(sap_handle h, int k)
     return SAP_OK;
 }
 
-size_t pass_smem_bytes(int KY, int stages) { return (size_t)stages * pass_stage_bytes(KY); }
+size_t pass_smem_bytes(int k, int KY, int stages) { return (size_t)stages * pass_stage_bytes(k, KY); }
 
-int pass_pick_stages(int KY)
+int pass_pick_stages(int k, int KY)
 {
     int s = kPassStagesMax;
-    while (s > 2 && pass_smem_bytes(KY, s) > 222 * 1024) --s;
+    while (s > 2 && pass_smem_bytes(k, KY, s) > 222 * 1024) --s;
     return s;
 }
 
@@ -1367,7 +1386,7 @@ template <int K, int CPT>
 cudaError_t launch_pass_k(const PassArgs &a, int grid, cudaStream_t s)
 {
     return launch_pdl(a.pdl != 0, restr_pass_kernel<K, CPT>, dim3(grid), dim3(kPassThreads),
-                      pass_smem_bytes(a.KY, a.stages), s, a);
+                      pass_smem_bytes(CPT == 4 ? K : 9, a.KY, a.stages), s, a);
 }
 
 template <int K, int CPT>
@@ -1499,6 +1518,7 @@ sap_status restructured_basis_alloc(sap_handle h)
     dfree(r.Uhi);
     dfree(r.Ulo);
     dfree(r.Y);
+    dfree(r.Yd);
     dfree(r.Ypart);
     r.KPG = (k + 15) / 16 * 16;
     r.KY = padded_stride(k);   // <= KPG; columns >= k are zero
@@ -1506,6 +1526,8 @@ sap_status restructured_basis_alloc(sap_handle h)
     RCK(cudaMalloc(&r.Ulo, (size_t)r.KPG * r.NP * 2));
     RCK(cudaMalloc(&r.Y, (size_t)r.Npad * r.KY * sizeof(float)));
     RCK(cudaMemset(r.Y, 0, (size_t)r.Npad * r.KY * sizeof(float)));
+    RCK(cudaMalloc(&r.Yd, (size_t)r.Npad * r.KY * 2 * sizeof(float)));
+    RCK(cudaMemset(r.Yd, 0, (size_t)r.Npad * r.KY * 2 * sizeof(float)));
     dfree(r.Ydh);
     dfree(r.Ydl);
     RCK(cudaMalloc(&r.Ydh, (size_t)r.Npad * r.KY * sizeof(float)));
@@ -1544,6 +1566,7 @@ sap_status restructured_set_bound(sap_handle h, double b_cap)
 GemmArgs product_args(sap_handle h, const RestrState &r)
 {
     GemmArgs g = r.gemm;
+    g.Yd = nullptr;
     g.Npad = r.Npad;
     g.nkb = r.NP / 64;
     g.ab_bf16 = handle_split_bf16(h);
@@ -1555,13 +1578,14 @@ GemmArgs product_args(sap_handle h, const RestrState &r)
 }
 
 sap_status restructured_enqueue_product(sap_handle h, const CUtensorMap *mhi, const CUtensorMap *mlo, int KPG,
-                                        float *Y, int KY, float *Ypart, ProbState *st, cudaStream_t s)
+                                        float *Y, float *Yd, int KY, float *Ypart, ProbState *st, cudaStream_t s)
 {
     RestrState &r = restr_state(h);
     GemmArgs g = product_args(h, r);
     g.tb_hi = *mhi;
     g.tb_lo = *mlo;
     g.Y = Y;
+    g.Yd = Yd;
     g.KY = KY;
     g.KPG = KPG;
     g.stages = gemm_pick_stages(KPG, g.nkb);
@@ -1587,12 +1611,13 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         p.wtiles = r.wtiles;
         p.ntiles = r.nwtiles;
         p.Y = b.Y;
+        p.Yd = b.Yd;
         p.KY = b.KY;
         p.Ykt = b.Ykt;
         p.Npad = r.Npad;
         p.nu = r.nu;
         p.beta = (float)(std::sqrt((double)b.k) * r.y_eps * 1.02);
-        p.stages = pass_pick_stages(b.KY);
+        p.stages = pass_pick_stages(b.k, b.KY);
         if (handle_tune(h).pass_stages >= 2) p.stages = std::min(p.stages, handle_tune(h).pass_stages);
         p.cert = cert_pass(n, b.k, r.b_cap);
         p.st = b.st;
@@ -1685,7 +1710,7 @@ sap_status restructured_enqueue(sap_handle h, double alpha)
     (void)alpha;
     RestrState &r = restr_state(h);
     cudaStream_t s = handle_stream(h);
-    sap_status st = restructured_enqueue_product(h, &r.gemm.tb_hi, &r.gemm.tb_lo, r.KPG, r.Y, r.KY, r.Ypart,
+    sap_status st = restructured_enqueue_product(h, &r.gemm.tb_hi, &r.gemm.tb_lo, r.KPG, r.Y, r.Yd, r.KY, r.Ypart,
                                                  handle_state(h), s);
     if (st != SAP_OK) return st;
     BasisView b;
@@ -1695,6 +1720,7 @@ sap_status restructured_enqueue(sap_handle h, double alpha)
     b.U32 = handle_u32(h);
     b.U32lo = handle_u32lo(h);
     b.Y = r.Y;
+    b.Yd = r.Yd;
     b.Ykt = r.KY;
     b.Ydh = r.Ydh;
     b.Ydl = r.Ydl;
@@ -1868,7 +1894,7 @@ void restructured_free(sap_handle h)
 {
     RestrState &r = restr_state(h);
     dfree(r.Xhi); dfree(r.Xlo); dfree(r.center); dfree(r.nu); dfree(r.w); dfree(r.wtiles);
-    dfree(r.near); dfree(r.counters); dfree(r.Uhi); dfree(r.Ulo); dfree(r.Y); dfree(r.Ypart);
+    dfree(r.near); dfree(r.counters); dfree(r.Uhi); dfree(r.Ulo); dfree(r.Y); dfree(r.Yd); dfree(r.Ypart);
     dfree(r.near_w); dfree(r.xn); dfree(r.Ydh); dfree(r.Ydl); dfree(r.wb);
 }
 

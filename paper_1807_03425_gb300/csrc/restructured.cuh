@@ -40,6 +40,7 @@ struct RestrState {
     void *Uhi = nullptr, *Ulo = nullptr;  // KPG x NP 16-bit
     int KPG = 0;              // k rounded up to the MMA N granule (16)
     float *Y = nullptr;       // block-major [Npad/128][KY][128]
+    float *Yd = nullptr;      // doubled row-side copy of Y for the pass: [Npad/128][KY][256]
     float *Ydh = nullptr, *Ydl = nullptr;  // double-float Y of the refine tier, KY x Npad each
     int KY = 0;               // k rounded up to 4
     int ksplit = 1;           // K slices of the product (shorter accumulation chains)
@@ -79,6 +80,7 @@ struct BasisView {
     int k, KP, KY;            // width, FP32 basis stride, Y stride (components)
     const float *U32, *U32lo; // n x KP FP32 basis and its low part
     float *Y;                 // this basis's first component in block 0 of a block-major Y
+    float *Yd;                // the same in the doubled row-side copy (block stride Ykt * 256)
     int Ykt;                  // components per 128-point block of that Y buffer
     float *Ydh, *Ydl;         // double-float Y (refine tier), KY x Npad each
     ProbState *st;
@@ -88,7 +90,7 @@ struct BasisView {
 
 // Restructured-form entry points (restructured.cu).
 sap_status restructured_enqueue_product(sap_handle h, const CUtensorMap *mhi, const CUtensorMap *mlo, int KPG,
-                                        float *Y, int KY, float *Ypart, ProbState *st, cudaStream_t s);
+                                        float *Y, float *Yd, int KY, float *Ypart, ProbState *st, cudaStream_t s);
 sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStream_t s); // pass + explicit tier
 bool restructured_u_maps(sap_handle h, void *Uhi, void *Ulo, int KPG, CUtensorMap *mhi, CUtensorMap *mlo);
 void restructured_split_host(sap_handle h, const double *U, int k, uint16_t *hi, uint16_t *lo); // k rows of NP

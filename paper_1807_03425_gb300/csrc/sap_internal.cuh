@@ -421,6 +421,16 @@ __device__ __forceinline__ int2 packed_pair(unsigned long long v)
     return make_int2((int)(v >> 47), (int)((v >> 30) & 0x1ffffull));
 }
 
+// Offset of row a (0..127) of a block in the doubled row-side copy of Y
+// (per component 256 floats): the all-pairs pass's consumer warp g (0..15)
+// takes rows g, g + 16, ..., g + 112, two at a time, so row a = 16 r + g
+// sits at g * 16 + (r / 2) * 4 + (r % 2) * 2 as the pair {y_a, y_a}.
+__host__ __device__ __forceinline__ int yd_offset(int a)
+{
+    const int g = a & 15, r = a >> 4;
+    return g * 16 + (r >> 1) * 4 + (r & 1) * 2;
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launchers (implemented in the .cu files, called by the engine).
 

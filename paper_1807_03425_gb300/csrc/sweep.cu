@@ -80,6 +80,7 @@ sap_status alloc_impl(sap_handle h, SweepState *&swp, int kmax, int hist_need)
     WCK(cudaMalloc(&sw.Uhi, (size_t)sw.KPG * r.NP * 2));
     WCK(cudaMalloc(&sw.Ulo, (size_t)sw.KPG * r.NP * 2));
     WCK(cudaMalloc(&sw.Y, (size_t)sw.KY * r.Npad * sizeof(float)));
+    WCK(cudaMalloc(&sw.Yd, (size_t)sw.KY * r.Npad * 2 * sizeof(float)));
     if (sw.ksplit > 1) WCK(cudaMalloc(&sw.Ypart, (size_t)sw.ksplit * sw.KY * r.Npad * sizeof(float)));
     WCK(cudaMalloc(&sw.gst, sizeof(ProbState)));
     WCK(cudaMemset(sw.gst, 0, sizeof(ProbState)));
@@ -145,6 +146,7 @@ sap_status upload(sap_handle h, SweepState &sw, const double *U0)
     WCK(cudaMemcpy(sw.Uhi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice));
     WCK(cudaMemcpy(sw.Ulo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice));
     WCK(cudaMemset(sw.Y, 0, (size_t)sw.KY * r.Npad * sizeof(float)));
+    WCK(cudaMemset(sw.Yd, 0, (size_t)sw.KY * r.Npad * 2 * sizeof(float)));
     return SAP_OK;
 }
 
@@ -196,7 +198,7 @@ sap_status enqueue_iteration(sap_handle h, SweepState &sw, double alpha, int eva
 {
     RestrState &r = restr_state(h);
     cudaStream_t s0 = handle_stream(h);
-    sap_status st = restructured_enqueue_product(h, &sw.mhi, &sw.mlo, sw.KPG, sw.Y, sw.KY, sw.Ypart, sw.gst, s0);
+    sap_status st = restructured_enqueue_product(h, &sw.mhi, &sw.mlo, sw.KPG, sw.Y, sw.Yd, sw.KY, sw.Ypart, sw.gst, s0);
     if (st != SAP_OK) return st;
     WCK(cudaEventRecord(sw.fork, s0));
     for (SweepBasis &b : sw.b) {
@@ -208,6 +210,7 @@ sap_status enqueue_iteration(sap_handle h, SweepState &sw, double alpha, int eva
         v.U32 = b.U32;
         v.U32lo = b.U32lo;
         v.Y = sw.Y + (size_t)b.off * 128;  // block-major: the basis's components within each block
+        v.Yd = sw.Yd + (size_t)b.off * 256;
         v.Ykt = sw.KY;
         v.Ydh = b.Ydh;
         v.Ydl = b.Ydl;
@@ -384,7 +387,7 @@ void sweep_free(SweepState *&s)
         if (b.stream) cudaStreamDestroy(b.stream);
         if (b.done) cudaEventDestroy(b.done);
     }
-    wfree(s->Uhi); wfree(s->Ulo); wfree(s->Y); wfree(s->Ypart); wfree(s->gst);
+    wfree(s->Uhi); wfree(s->Ulo); wfree(s->Y); wfree(s->Yd); wfree(s->Ypart); wfree(s->gst);
     if (s->fork) cudaEventDestroy(s->fork);
     delete s;
     s = nullptr;

@@ -35,6 +35,7 @@ struct SweepState {
     int KPG = 0;
     CUtensorMap mhi, mlo;
     float *Y = nullptr;                   // KY x Npad, all bases' components
+    float *Yd = nullptr;                  // doubled row-side copy for the pass (2 KY x Npad)
     int KY = 0;
     float *Ypart = nullptr;
     int ksplit = 1;

@@ -234,7 +234,7 @@ def run_sharded(args):
     s = ShardSap(X, ws, rank)
     s.set_stream(stream.cuda_stream)
     s.set_tuning(pass_bound=4e-3, pass_stages=0, explicit_blocks_per_sm=1, update_blocks=0,
-                 plain_blocks_per_sm=2, programmatic_launch=0, refine_tier=0)
+                 plain_blocks_per_sm=2, programmatic_launch=0, refine_tier=-1)
     s.set_basis(U0)
 
     def barrier():

@@ -382,8 +382,12 @@ typedef struct {
                                        fused into the FP64 recheck (one launch fewer; k <= 8, else
                                        as 0), 4 explicit differences in extended precision whose
                                        list carries each pair's ratio, so the FP64 recheck takes
-                                       only the pairs within the final bound, -1 chosen by n
-                                       (double-float above n = 256) */
+                                       only the pairs within the final bound, 5 explicit
+                                       differences inside the all-pairs pass: each emitted pair,
+                                       and each near pair, is rechecked at once by the warp that
+                                       found it (two launches fewer; n <= 256 and k <= 16, else
+                                       as 0), -1 chosen by n and k (double-float above n = 256,
+                                       else 5 for k <= 16, else 0) */
     double us_per_iteration;        /* measured by sap_autotune; 0 when set by hand */
 } sap_tuning;
 

@@ -300,6 +300,7 @@ sap_status enqueue_iteration(sap_handle h, double alpha, int eval_only, Partial 
         SelectUpdateArgs u = su_args(h, alpha, eval_only, list, which);
         u.shard_rec = shard_rec;
         if (h->path != SAP_PLAIN) {
+            u.seeds_in_product = 1;  // the next iteration's product evaluates them
             BasisView bv;
             bv.k = h->k;
             bv.cand1 = h->cand1;
@@ -835,7 +836,7 @@ sap_status sap_set_tuning(sap_handle h, const sap_tuning *in)
         in->explicit_blocks_per_sm < 1 || in->explicit_blocks_per_sm > 8 || in->update_blocks < 0 ||
         in->update_blocks > kRecheckBlocks || in->plain_blocks_per_sm < 1 || in->plain_blocks_per_sm > 8 ||
         (in->programmatic_launch != 0 && in->programmatic_launch != 1) || in->refine_tier < -1 ||
-        in->refine_tier > 4)
+        in->refine_tier > 5)
         return fail(h, SAP_E_ARG, "tuning parameter out of range");
     CK(cudaStreamSynchronize(h->stream));
     TuneParams p;
@@ -1047,6 +1048,7 @@ sap_status sap_shard_step(sap_handle h, double alpha, const sap_record *recs, in
     SelectUpdateArgs u = su_args(h, alpha, 0, h->cand1, 1);
     u.grid = 1;  // a few pairs: one block rechecks them and updates
     u.pdl = 0;
+    u.seeds_in_product = 1;  // a split handle is restructured: its product evaluates them
     {
         Timed t(h, K_UPDATE);
         CK(launch_select_update(u, h->stream));

@@ -37,7 +37,74 @@ __host__ __device__ inline uint32_t tmem_cols_for(int n)
     return c;
 }
 
-__global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ GemmArgs a)
+// Butterfly sums of M hi + lo FP32 pairs over the warp, interleaved (each
+// addition an exact two-sum of the high parts, the low parts added): entries
+// below `live`, and the last one if `last`.  Every lane ends with a total
+// (the lanes may differ in the last bits: the low parts add in lane order).
+template <int M>
+__device__ __forceinline__ void warp_df_totals(float (&h)[M], float (&l)[M], int live, bool last)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            if (!(c < live || (last && c == M - 1))) continue;
+            const float h2 = __shfl_xor_sync(0xffffffffu, h[c], o), l2 = __shfl_xor_sync(0xffffffffu, l[c], o);
+            float s, e;
+            xs_two_sum(h[c], h2, s, e);
+            h[c] = s;
+            l[c] = __fadd_rn(l[c], __fadd_rn(l2, e));
+        }
+    }
+}
+
+// The seed bound of the next pass (see GemmArgs): one warp evaluates watch
+// pairs q0, q0 + step, ... in extended precision (explicit FP32
+// differences, error-free products with the hi + lo FP32 basis; the error
+// model of the explicit extended-precision tier) and returns the smallest
+// certified upper bound (lane 0's value is the one used).
+__device__ float product_seeds(const GemmArgs &a, int q0, int step, int lane)
+{
+    const ProbState *st = a.seed_st;
+    const int n = a.seed_n, k = a.seed_k, KP = a.seed_KP;
+    const int nw = st->watch_n;
+    const Cert cert = cert_explicit_df_dev(n, k);
+    float best = INFINITY;
+    for (int q = q0; q < nw; q += step) {
+        const int2 pr = st->watch[q];
+        const float *xi = a.seed_X + (size_t)pr.x * n, *xj = a.seed_X + (size_t)pr.y * n;
+        float dd = 0.f, zz = 0.f;
+        // components c0 .. c0 + 7, and (first chunk) |x_i - x_j|^2 in slot 8
+        for (int c0 = 0; c0 < k; c0 += 8) {
+            float zh[9], zl[9];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) zh[c] = zl[c] = 0.f;
+            const int live = k - c0 < 8 ? k - c0 : 8;
+            for (int l = lane; l < n; l += 32) {
+                const float D = xi[l] - xj[l];
+                if (c0 == 0) xs_fma(zh[8], zl[8], D, D, 0.f);
+                const float *uh = a.seed_U + (size_t)l * KP + c0, *ul = a.seed_Ulo + (size_t)l * KP + c0;
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c < live) xs_fma(zh[c], zl[c], D, uh[c], ul[c]);
+            }
+            warp_df_totals<9>(zh, zl, live, c0 == 0);
+            if (c0 == 0) dd = zh[8] + zl[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < live) {
+                    const float z = zh[c] + zl[c];
+                    zz = fmaf(z, z, zz);
+                }
+        }
+        if (dd > 1e-30f) best = fminf(best, cert_upper(sqrtf(zz / dd), cert));
+    }
+    return best;
+}
+
+// 128 threads (TMA producer, MMA issuer, four epilogue warps over the TMEM
+// lane quadrants), or 192 where warps 4 and 5 evaluate the seeds meanwhile.
+__global__ void __launch_bounds__(192, 1) gemm_y_kernel(const __grid_constant__ GemmArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -73,6 +140,16 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
     grid_dep_launch();
     grid_dep_wait();
     const int m0 = blockIdx.x * GM;
+    // the next pass's seed bound, by warps 4 and 5 of every CTA (beside the
+    // product): a pair per warp, merged by an atomic minimum
+    if (a.seed_st && warp >= 4) {
+        const int sw = 2 * (blockIdx.y * gridDim.x + blockIdx.x) + warp - 4;
+        const int nsw = 2 * gridDim.x * gridDim.y;
+        if (sw < a.seed_st->watch_n) {
+            const float sb = product_seeds(a, sw, nsw, lane);
+            if (lane == 0 && sb < INFINITY) atomicMin(&a.seed_st->seed_ub, __float_as_uint(sb));
+        }
+    }
     // this CTA's K slice
     const int kb0 = (int)(((long long)blockIdx.y * a.nkb) / a.ksplit);
     const int nkb = (int)(((long long)(blockIdx.y + 1) * a.nkb) / a.ksplit) - kb0;
@@ -132,7 +209,7 @@ __global__ void __launch_bounds__(128, 1) gemm_y_kernel(const __grid_constant__ 
     tc::tc_fence_after();
     // the TMEM loads below are warp-collective: decide for the whole block
     const int good = __syncthreads_and(ok ? 1 : 0) && !abort_sh;
-    if (good) {
+    if (good && warp < 4) {
         const int row = m0 + warp * 32 + lane;
         const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
         for (int c0 = 0; c0 < a.KY; c0 += 8) {
@@ -214,7 +291,8 @@ cudaError_t launch_gemm_y(const GemmArgs &a, cudaStream_t s)
     if (ksplit > a.nkb) return cudaErrorInvalidValue;
     GemmArgs b = a;
     b.ksplit = ksplit;
-    cudaError_t e = launch_pdl(a.pdl != 0, gemm_y_kernel, dim3(a.Npad / GM, ksplit), dim3(128), shm, s, b);
+    cudaError_t e = launch_pdl(a.pdl != 0, gemm_y_kernel, dim3(a.Npad / GM, ksplit), dim3(a.seed_st ? 192 : 128), shm,
+                               s, b);
     if (e != cudaSuccess || ksplit == 1) return e;
     const size_t count = (size_t)a.KY * a.Npad;
     ksum_kernel<<<(unsigned)std::min<size_t>((count + 255) / 256, 2048), 256, 0, s>>>(a.Ypart, ksplit, a.KY, a.Npad,

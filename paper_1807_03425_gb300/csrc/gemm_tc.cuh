@@ -26,6 +26,17 @@ struct GemmArgs {
     int ksplit;                 // K slices (grid.y); > 1: raw slices go to Ypart
     float *Ypart;               // ksplit x KY x Npad FP32 (ksplit > 1)
     int pdl;                    // programmatic launch (see sap_internal.cuh)
+    // Seeds of the next all-pairs pass, computed by idle warps of every CTA
+    // (single-basis handles; null seed_st: none): the recent argmin pairs'
+    // ratios under the basis this product uses, in extended precision from
+    // explicit differences, as certified upper bounds merged into
+    // seed_st->seed_ub by an atomic minimum (the update that changed the
+    // basis reset it to +inf; an unchanged basis keeps its valid bound).
+    const float *seed_X = nullptr;   // N x n row-major FP32 points
+    const float *seed_U = nullptr;   // the basis, FP32 n x KP row-major ...
+    const float *seed_Ulo = nullptr; // ... and its FP32 residual
+    ProbState *seed_st = nullptr;
+    int seed_n = 0, seed_k = 0, seed_KP = 0;
 };
 
 size_t gemm_smem_bytes(int KPG, int stages);

@@ -282,6 +282,20 @@ struct PassArgs {
     int2 *cand;
     long long cap;
     int pdl;
+    // second tier inside the pass (non-null X; n <= 256, k <= 16): every
+    // emitted pair, and every near pair, is evaluated at once from explicit
+    // FP32 differences (the explicit tier's arithmetic and error model,
+    // cert2); the pairs that can still be the argmin go to cand2 (count in
+    // st->cnt2), and cand1 is not written (st->cnt1 still counts)
+    const float *X = nullptr;  // N x n FP32 points
+    int n = 0;
+    const float *U32 = nullptr;  // n x KP FP32 basis (pad columns zero)
+    int KP = 0;
+    const int2 *near = nullptr;
+    int n_near = 0;
+    int2 *cand2 = nullptr;
+    long long cap2 = 0;
+    Cert cert2;
 };
 
 // One ring stage: the BF16 1/d^2 tile (32 KB), then the row side's point
@@ -339,7 +353,72 @@ __device__ __forceinline__ float bf16_at(const uint16_t *p) { return __uint_as_f
 constexpr int kConsumerWarps = 16;
 constexpr int kPassThreads = (kConsumerWarps + 1) * 32;
 
-template <int K, int CPT>
+// Explicit FP32 differences of E pairs by one warp (lanes over the
+// coordinates, the E (K + 1) sums reduced together), as in the explicit
+// tier: lane e < E receives pair e's ratio rr and code (1: rr valid, 2:
+// |x_i - x_j|^2 too small for FP32, the FP64 tier decides; 0: none).
+template <int K, int E>
+__device__ __forceinline__ void expl32_eval(const float *X, int n, const float *U32, int KP, const int2 (&pr)[E],
+                                            const bool (&valid)[E], int lane, float &rr, int &code)
+{
+    constexpr int KU = (K + 3) / 4 * 4;
+    constexpr int M = E * (K + 1);
+    float acc[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) acc[q] = 0.f;
+#pragma unroll 2
+    for (int l = lane; l < n; l += 32) {
+        float u[KU];
+#pragma unroll
+        for (int c = 0; c < KU; c += 4) {
+            const float4 t = __ldcg(reinterpret_cast<const float4 *>(U32 + (size_t)l * KP + c));
+            u[c] = t.x; u[c + 1] = t.y; u[c + 2] = t.z; u[c + 3] = t.w;
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float D = X[(size_t)pr[e].x * n + l] - X[(size_t)pr[e].y * n + l];
+            acc[e * (K + 1) + K] = fmaf(D, D, acc[e * (K + 1) + K]);
+#pragma unroll
+            for (int c = 0; c < K; ++c) acc[e * (K + 1) + c] = fmaf(u[c], D, acc[e * (K + 1) + c]);
+        }
+    }
+    float z[K + 1];
+    if constexpr (M <= 32) {
+        constexpr int S = M <= 8 ? 8 : M <= 16 ? 16 : 32;
+        constexpr int dup = 32 / S;
+        float r[S];
+#pragma unroll
+        for (int q = 0; q < S; ++q) r[q] = q < M ? acc[q < M ? q : 0] : 0.f;
+        const float t = warp_reduce_scatter<S>(r, lane);
+        const int e = lane < E ? lane : 0;
+#pragma unroll
+        for (int c = 0; c <= K; ++c) z[c] = __shfl_sync(0xffffffffu, t, (e * (K + 1) + c) * dup);
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < M; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+#pragma unroll
+        for (int c = 0; c <= K; ++c) z[c] = acc[c];
+#pragma unroll
+        for (int e = 1; e < E; ++e)
+            if (lane == e)
+#pragma unroll
+                for (int c = 0; c <= K; ++c) z[c] = acc[e * (K + 1) + c];
+    }
+    bool myvalid = valid[0];
+#pragma unroll
+    for (int e = 1; e < E; ++e)
+        if (lane == e) myvalid = valid[e];
+    const float dd = z[K];
+    float zz = 0.f;
+#pragma unroll
+    for (int c = 0; c < K; ++c) zz = fmaf(z[c], z[c], zz);
+    code = (lane >= E || !myvalid) ? 0 : (dd < 1e-30f ? 2 : 1);
+    rr = code == 1 ? sqrtf(zz / dd) : INFINITY;
+}
+
+template <int K, int CPT, bool EXPL>
 __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
 {
     constexpr int SR = 4 / CPT;                  // warps sharing one row
@@ -461,6 +540,54 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     const int col0 = seg * 32 * CPT + lane * CPT;
     const float seed = load_pos_float(&a.st->seed_ub);
     float uwarp = INFINITY;  // best upper bound this warp has produced
+    // second tier inside the pass: EX pairs per warp and round
+    constexpr int EX = (K + 1) * 2 <= 32 ? 2 : 1;
+    auto expl_round = [&](const int2 (&pr)[EX], const bool (&valid)[EX]) {
+        float rr;
+        int code;
+        expl32_eval<K, EX>(a.X, a.n, a.U32, a.KP, pr, valid, lane, rr, code);
+        const float wmin = warp_min(rr);
+        // any earlier value of the running bound is a valid (looser) bound
+        float U2 = fminf(fminf(seed, uwarp), load_pos_float(&a.st->run_ub2));
+        if (wmin < INFINITY) {
+            const float ub = cert_upper(wmin, a.cert2);
+            if (lane == 0 && ub < U2) {
+                atomic_min_pos_float(&a.st->run_ub2, ub);
+                atomic_min_pos_float(&a.st->run_ub1, ub);  // bounds the pass's own emission too
+            }
+            U2 = fminf(U2, ub);
+            uwarp = fminf(uwarp, ub);
+        }
+        const float th = cert_emit_threshold(U2, a.cert2);
+        const unsigned int m = __ballot_sync(0xffffffffu, code == 2 || (code == 1 && rr <= th));
+        if (!m) return;
+        unsigned int b0 = 0;
+        if (lane == 0) b0 = atomicAdd((unsigned int *)&a.st->cnt2, (unsigned int)__popc(m));
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        int2 mp = pr[0];
+#pragma unroll
+        for (int e = 1; e < EX; ++e)
+            if (lane == e) mp = pr[e];
+        if (m >> lane & 1u) {
+            const long long pos = (long long)b0 + __popc(m & ((1u << lane) - 1u));
+            if (pos < a.cap2) a.cand2[pos] = mp;
+            else atomicOr(&a.st->status, ST_OVERFLOW);
+        }
+    };
+    if constexpr (EXPL) {
+        // the near pairs, while the first stages' copies land
+        const long long G = (long long)gridDim.x * kConsumerWarps * EX;
+        for (long long base = ((long long)blockIdx.x * kConsumerWarps + warp) * EX; base < a.n_near; base += G) {
+            int2 pr[EX];
+            bool valid[EX];
+#pragma unroll
+            for (int e = 0; e < EX; ++e) {
+                valid[e] = base + e < a.n_near;
+                pr[e] = valid[e] ? __ldcg(a.near + base + e) : make_int2(0, 0);
+            }
+            expl_round(pr, valid);
+        }
+    }
     // ring position and barrier phase, advanced without integer division
     int s = 0;
     uint32_t phase = 0;
@@ -616,6 +743,35 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
         // the warp's reads of stage s are done
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&empty[s]);
+        if constexpr (EXPL) {
+            const int total = __reduce_add_sync(0xffffffffu, cnt);
+            if (total == 0) continue;
+            if (lane == 0) atomicAdd((unsigned int *)&a.st->cnt1, (unsigned int)total);
+            // the emitted pairs, EX per round: each round takes the lowest
+            // pending pair of each of the first EX lanes that have one
+            const int i0 = IJ.x * T, j0 = IJ.y * T;
+            uint32_t rem = emit;
+            for (;;) {
+                unsigned int has = __ballot_sync(0xffffffffu, rem != 0u);
+                if (!has) break;
+                const int bit = rem ? __ffs(rem) - 1 : 0;
+                const int pi = i0 + row0 + (bit / CPT) * RSTEP, pj = j0 + col0 + bit % CPT;
+                int2 pr[EX];
+                bool valid[EX];
+#pragma unroll
+                for (int e = 0; e < EX; ++e) {
+                    const int src = has ? __ffs(has) - 1 : 0;
+                    valid[e] = has != 0u;
+                    pr[e].x = __shfl_sync(0xffffffffu, pi, src);
+                    pr[e].y = __shfl_sync(0xffffffffu, pj, src);
+                    if (!valid[e]) pr[e] = make_int2(0, 0);
+                    if (has && lane == src) rem &= rem - 1u;
+                    has &= has - 1u;
+                }
+                expl_round(pr, valid);
+            }
+            continue;
+        }
         if (__any_sync(0xffffffffu, cnt > 0)) {
             int incl = cnt;
 #pragma unroll
@@ -1382,18 +1538,29 @@ int pass_pick_stages(int k, int KY)
     return s;
 }
 
+// the form with the second tier inside exists for k <= 16
 template <int K, int CPT>
 cudaError_t launch_pass_k(const PassArgs &a, int grid, cudaStream_t s)
 {
-    return launch_pdl(a.pdl != 0, restr_pass_kernel<K, CPT>, dim3(grid), dim3(kPassThreads),
-                      pass_smem_bytes(CPT == 4 ? K : 9, a.KY, a.stages), s, a);
+    const size_t shm = pass_smem_bytes(CPT == 4 ? K : 9, a.KY, a.stages);
+    if constexpr (K <= 16) {
+        if (a.X) return launch_pdl(a.pdl != 0, restr_pass_kernel<K, CPT, true>, dim3(grid), dim3(kPassThreads), shm, s, a);
+    } else {
+        if (a.X) return cudaErrorNotSupported;
+    }
+    return launch_pdl(a.pdl != 0, restr_pass_kernel<K, CPT, false>, dim3(grid), dim3(kPassThreads), shm, s, a);
 }
 
 template <int K, int CPT>
 cudaError_t config_pass_k()
 {
-    return cudaFuncSetAttribute(restr_pass_kernel<K, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                224 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(restr_pass_kernel<K, CPT, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
+    if constexpr (K <= 16)
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(restr_pass_kernel<K, CPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     224 * 1024);
+    return e;
 }
 
 cudaError_t configure_pass_kernels()
@@ -1567,6 +1734,7 @@ GemmArgs product_args(sap_handle h, const RestrState &r)
 {
     GemmArgs g = r.gemm;
     g.Yd = nullptr;
+    g.seed_st = nullptr;
     g.Npad = r.Npad;
     g.nkb = r.NP / 64;
     g.ab_bf16 = handle_split_bf16(h);
@@ -1578,10 +1746,20 @@ GemmArgs product_args(sap_handle h, const RestrState &r)
 }
 
 sap_status restructured_enqueue_product(sap_handle h, const CUtensorMap *mhi, const CUtensorMap *mlo, int KPG,
-                                        float *Y, float *Yd, int KY, float *Ypart, ProbState *st, cudaStream_t s)
+                                        float *Y, float *Yd, int KY, float *Ypart, ProbState *st, cudaStream_t s,
+                                        bool seeds)
 {
     RestrState &r = restr_state(h);
     GemmArgs g = product_args(h, r);
+    if (seeds) {
+        g.seed_X = handle_x32(h);
+        g.seed_U = handle_u32(h);
+        g.seed_Ulo = handle_u32lo(h);
+        g.seed_st = st;
+        g.seed_n = handle_n_dim(h);
+        g.seed_k = handle_k(h);
+        g.seed_KP = handle_kp(h);
+    }
     g.tb_hi = *mhi;
     g.tb_lo = *mlo;
     g.Y = Y;
@@ -1605,6 +1783,7 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
     RestrState &r = restr_state(h);
     const int n = handle_n_dim(h);
     cudaEvent_t ea, eb;
+    const int tier = restructured_tier_for(h, b.k);
     {
         PassArgs p;
         p.wb = r.wb;
@@ -1624,15 +1803,26 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         p.cand = b.cand1;
         p.cap = b.cap;
         p.pdl = handle_tune(h).pdl;
+        if (tier == 5) {
+            p.X = handle_x32(h);
+            p.n = n;
+            p.U32 = b.U32;
+            p.KP = b.KP;
+            p.near = r.near;
+            p.n_near = r.n_near;
+            p.cand2 = b.cand2;
+            p.cap2 = b.cap;
+            p.cert2 = cert_explicit(n, b.k);
+        }
         handle_count_launch(h, 1, &ea, &eb);
         if (ea) cudaEventRecord(ea, s);
         RCK(launch_pass(p, b.k, std::min(r.nwtiles, handle_sms(h)), s));
         if (eb) cudaEventRecord(eb, s);
         handle_push_timing(h, 1, ea, eb);
     }
-    const int tier = restructured_tier_for(h, b.k);
-    if (tier == 2 || tier == 3) {
+    if (tier == 2 || tier == 3 || tier == 5) {
         // the explicit tier runs inside the FP64 recheck (restructured_fuse_args)
+        // or (5) inside the pass
     } else if (tier == 0 || tier == 4) {
         ExplArgs x;
         x.X = handle_x32(h);
@@ -1711,7 +1901,7 @@ sap_status restructured_enqueue(sap_handle h, double alpha)
     RestrState &r = restr_state(h);
     cudaStream_t s = handle_stream(h);
     sap_status st = restructured_enqueue_product(h, &r.gemm.tb_hi, &r.gemm.tb_lo, r.KPG, r.Y, r.Yd, r.KY, r.Ypart,
-                                                 handle_state(h), s);
+                                                 handle_state(h), s, true);
     if (st != SAP_OK) return st;
     BasisView b;
     b.k = handle_k(h);
@@ -1844,10 +2034,12 @@ int restructured_tier_for(sap_handle h, int k)
 {
     const int t = handle_tune(h).refine;
     const int n = handle_n_dim(h);
+    if (t == 5) return explicit_uses_df(n) || k > 16 ? 0 : 5;
     if (t == 4) return 4;
     if (t == 3) return k <= 8 ? 3 : 0;
     if (t == 2) return explicit_uses_df(n) ? 0 : 2;
-    return (t < 0 ? n > 256 : t != 0) ? 1 : 0;
+    if (t < 0) return n > 256 ? 1 : (k <= 16 ? 5 : 0);
+    return t != 0 ? 1 : 0;
 }
 
 int restructured_tier(sap_handle h) { return restructured_tier_for(h, handle_k(h)); }
@@ -1885,7 +2077,8 @@ void restructured_fuse_args(sap_handle h, const BasisView &b, SelectUpdateArgs &
 int restructured_kernels_per_iteration(sap_handle h)
 {
     // product (+ slice sum), pass, and the explicit tier, or the double-float
-    // product + refine tier, or nothing (fused into the FP64 recheck)
+    // product + refine tier, or nothing (fused into the FP64 recheck or, 5,
+    // into the pass)
     const int tier = restructured_tier(h);
     return 2 + (tier == 1 ? 2 : (tier == 0 || tier == 4) ? 1 : 0) + (restr_state(h).ksplit > 1 ? 1 : 0);  // 2, 3: fused
 }

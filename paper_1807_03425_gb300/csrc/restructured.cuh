@@ -89,8 +89,11 @@ struct BasisView {
 };
 
 // Restructured-form entry points (restructured.cu).
+// seeds: the product also evaluates the next pass's seed bound (one basis
+// per handle; the update then leaves the seeds to it)
 sap_status restructured_enqueue_product(sap_handle h, const CUtensorMap *mhi, const CUtensorMap *mlo, int KPG,
-                                        float *Y, float *Yd, int KY, float *Ypart, ProbState *st, cudaStream_t s);
+                                        float *Y, float *Yd, int KY, float *Ypart, ProbState *st, cudaStream_t s,
+                                        bool seeds = false);
 sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStream_t s); // pass + explicit tier
 bool restructured_u_maps(sap_handle h, void *Uhi, void *Ulo, int KPG, CUtensorMap *mhi, CUtensorMap *mlo);
 void restructured_split_host(sap_handle h, const double *U, int k, uint16_t *hi, uint16_t *lo); // k rows of NP

@@ -93,7 +93,8 @@ struct TuneParams {
     int pdl = 0;             // programmatic dependent launch between the kernels of an iteration
     int refine = -1;         // second tier: 1 double-float refine, 0 explicit differences, 2 / 3 explicit
                              // (FP32 / extended precision) fused into the FP64 recheck, 4 extended precision
-                             // with ratios for a final filter, -1 by n (> 256: refine)
+                             // with ratios for a final filter, 5 explicit FP32 inside the pass, -1 by n
+                             // and k (n > 256: refine, else k <= 16: 5, else 0)
     double us_per_iter = 0;  // measured by the tuner (0: not tuned)
 };
 
@@ -515,6 +516,10 @@ struct SelectUpdateArgs {
     // shard evaluation (eval_only): the best pair (q = r^2, i, j; i = -1 if
     // none) goes here instead of the history, and no status bit is set
     Partial *shard_rec = nullptr;
+    // 1: the next iteration's product evaluates the seeds (FP32 and BF16
+    // data); an update that changes the basis then only resets the seed
+    // bound to +inf
+    int seeds_in_product = 0;
 };
 cudaError_t launch_select_update(const SelectUpdateArgs &a, cudaStream_t s);
 

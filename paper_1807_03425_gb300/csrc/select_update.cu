@@ -958,7 +958,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             // warp 4 records the result meanwhile; warps 4-7 then fetch the
             // coordinates of the seed pairs (two per warp)
             if (w == kQW && lane == 0) record(b);
-            if (go && sizeof(TX) == 4) {
+            if (go && sizeof(TX) == 4 && !a.seeds_in_product) {
                 seed_bar();
                 const int nw = sh.watch_n;
 #pragma unroll
@@ -974,7 +974,9 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
                 }
             }
         }
-        if (!go) return;
+        // with the seeds in the next product, the bound it merges into starts at +inf
+        if (go && a.seeds_in_product && tid == 0) st->seed_ub = 0x7f800000u;
+        if (!go || a.seeds_in_product) return;
         __syncthreads();  // the new basis is written
         // seeds: the recent argmin pairs under the new basis, two per warp of
         // warps 4-7; FP32 data in extended precision from the basis's hi +
@@ -1044,7 +1046,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
     const int nwatch = sh.watch_n;
     const bool prefetch = n <= 32 * kSeedRegs;
     float wxi[kSeedRegs], wxj[kSeedRegs];
-    if (prefetch && w < nwatch) {
+    if (prefetch && w < nwatch && !a.seeds_in_product) {
         const int2 pr = sh.watch[w];
 #pragma unroll
         for (int q = 0; q < kSeedRegs; ++q) {
@@ -1259,6 +1261,11 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
             write_row<TX, K>(a, sh, kk, l, row, Uf);
         }
         __syncthreads();
+    }
+
+    if (a.seeds_in_product) {
+        if (tid == 0) st->seed_ub = 0x7f800000u;  // the next product merges its seeds into +inf
+        return;
     }
 
     // seeds: the recent argmin pairs under the new basis

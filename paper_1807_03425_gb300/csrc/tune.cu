@@ -70,7 +70,7 @@ void load_locked()
         if (std::sscanf(line, "sap-tune %d %lld %d %d %d %d %d %llx %lf %d %d %d %d %d %d %lf", &ver, &k.N, &k.n,
                         &k.k, &k.dt, &k.path, &k.split, &k.eps_bits, &p.b_cap, &p.pass_stages, &p.expl_per_sm,
                         &p.su_blocks, &p.plain_per_sm, &p.pdl, &p.refine, &p.us_per_iter) == 16 &&
-            ver == 3 && p.refine >= -1 && p.refine <= 4 && p.b_cap >= 1e-6 && p.b_cap <= 0.25 && p.expl_per_sm >= 1 && p.expl_per_sm <= 8 &&
+            ver == 3 && p.refine >= -1 && p.refine <= 5 && p.b_cap >= 1e-6 && p.b_cap <= 0.25 && p.expl_per_sm >= 1 && p.expl_per_sm <= 8 &&
             p.plain_per_sm >= 1 && p.plain_per_sm <= 8 && p.su_blocks >= 0 && p.su_blocks <= kRecheckBlocks &&
             p.pass_stages >= 0 && p.pass_stages <= 5 && (p.pdl == 0 || p.pdl == 1))
             g_cache[k] = p;
@@ -188,7 +188,7 @@ sap_status tune_handle(sap_handle h, double alpha, int iters)
     };
     const bool restr = handle_path_restructured(h);
     if (restr) {
-        for (int rf : {0, 1, 2, 3, 4}) {
+        for (int rf : {0, 1, 2, 3, 4, 5}) {
             TuneParams c = best;
             c.refine = rf;
             consider(c);

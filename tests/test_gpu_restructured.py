@@ -154,16 +154,17 @@ def test_c2_restructured_full_size(P):
     assert st["n_near"] > 0 and st["last_tier2"] >= 1
 
 
-@pytest.mark.parametrize("tier", [0, 1, 2, 3, 4])
-@pytest.mark.parametrize("N,n,k", [(600, 300, 3), (450, 40, 1), (700, 100, 5)])
+@pytest.mark.parametrize("tier", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("N,n,k", [(600, 300, 3), (450, 40, 1), (700, 100, 5), (800, 60, 12)])
 def test_second_tiers_lockstep(P, tier, N, n, k):
     """Every second tier (explicit differences, double-float refine,
     explicit differences fused into the FP64 recheck in FP32 or in extended
-    precision, extended precision with a final filter) gives the oracle's argmin, ratio and update in lock-step, for
-    n on both sides of the 256 switch (above it the fused FP32 tier falls
-    back to the separate one), n = 100 (the one-warp update of n <= 128
-    with a ragged last row group) and k = 1 (where ties in the ratio are
-    dense)."""
+    precision, extended precision with a final filter, explicit differences
+    inside the all-pairs pass) gives the oracle's argmin, ratio and update in
+    lock-step, for n on both sides of the 256 switch (above it the FP32
+    fused tiers fall back to the separate one), n = 100 (the one-warp update
+    of n <= 128 with a ragged last row group), k = 1 (where ties in the
+    ratio are dense) and k = 12 (the padded compute width)."""
     g = np.random.default_rng(N + n)
     t = g.random(N) * 2 * np.pi
     # a curve on a 2-torus linearly embedded in R^n (short secants abound)

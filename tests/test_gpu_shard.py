@@ -35,7 +35,7 @@ def unsplit(P, X, U0, alpha, T, tier):
         return hist, am, s.get_basis()
 
 
-@pytest.mark.parametrize("world,tier", [(2, 0), (3, 3), (5, 1)])
+@pytest.mark.parametrize("world,tier", [(2, 0), (3, 3), (5, 1), (2, 5)])
 def test_split_equals_unsplit_bitwise(P, world, tier):
     """Moment curve N = 1500 in R^40 (12 point blocks, 78 tiles, ragged last
     block), k = 5: world ranks, host records."""

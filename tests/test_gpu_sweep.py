@@ -105,18 +105,21 @@ def test_sweep_equals_single_basis_runs_and_oracle(P, N, side, kmax, T):
         check_final(X64, Uf[k], hg, amg)
 
 
-def test_sweep_fused_extended_tier_equals_single_runs(P):
-    """The dimension sweep with the extended-precision second tier fused
-    into the FP64 recheck (every basis on its own stream, k <= 8) gives the
-    same trajectories, bit for bit, as single-basis runs with the default
-    tiers: the tiers only select candidates, the FP64 tier decides."""
+@pytest.mark.parametrize("tier", [3, 5])
+def test_sweep_fused_tiers_equal_single_runs(P, tier):
+    """The dimension sweep with the second tier fused into another kernel
+    (3: extended precision inside the FP64 recheck, k <= 8; 5: explicit
+    FP32 differences inside the all-pairs pass), every basis on its own
+    stream, gives the same trajectories, bit for bit, as single-basis runs
+    with the default tiers: the tiers only select candidates, the FP64 tier
+    decides."""
     alpha, T, kmax = 0.01, 20, 6
     X = images(200, 10, 5)
     n = X.shape[1]
     U0 = W.random_basis(n, kmax, 6)
     with P.Sap(X) as s:
         s.set_tuning(pass_bound=2e-3, pass_stages=0, explicit_blocks_per_sm=1, update_blocks=0,
-                     plain_blocks_per_sm=2, programmatic_launch=1, refine_tier=3)
+                     plain_blocks_per_sm=2, programmatic_launch=1, refine_tier=tier)
         s.estimate_dim(U0, T, alpha, 0.1)
         hist = {k: s.sweep_history(k, T + 1) for k in range(1, kmax + 1)}
     ref = single_runs(P, X, U0, range(1, kmax + 1), alpha, T)

@@ -54,6 +54,10 @@ EXTREMES = [
          programmatic_launch=0, refine_tier=3),
     dict(pass_bound=4e-3, pass_stages=0, explicit_blocks_per_sm=2, update_blocks=152, plain_blocks_per_sm=2,
          programmatic_launch=1, refine_tier=4),
+    dict(pass_bound=2e-3, pass_stages=0, explicit_blocks_per_sm=1, update_blocks=76, plain_blocks_per_sm=2,
+         programmatic_launch=1, refine_tier=5),
+    dict(pass_bound=1.6e-2, pass_stages=2, explicit_blocks_per_sm=2, update_blocks=0, plain_blocks_per_sm=2,
+         programmatic_launch=0, refine_tier=5),
 ]
 
 

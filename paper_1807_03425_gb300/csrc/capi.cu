@@ -421,6 +421,7 @@ void handle_push_timing(sap_handle h, int cls, cudaEvent_t a, cudaEvent_t b)
 sap_status handle_fail(sap_handle h, sap_status s, const char *msg) { return fail(h, s, msg); }
 SoftState &soft_state(sap_handle h) { return h->ss; }
 double *handle_u64(sap_handle h) { return h->U64; }
+Partial *handle_partials(sap_handle h) { return h->partials; }
 float *handle_u32_mut(sap_handle h) { return h->U32; }
 sap_status handle_reset_state(sap_handle h) { return reset_state(h); }
 int handle_profiling(sap_handle h) { return h->profiling ? 1 : 0; }

@@ -282,20 +282,27 @@ struct PassArgs {
     int2 *cand;
     long long cap;
     int pdl;
-    // second tier inside the pass (non-null X; n <= 256, k <= 16): every
-    // emitted pair, and every near pair, is evaluated at once from explicit
-    // FP32 differences (the explicit tier's arithmetic and error model,
-    // cert2); the pairs that can still be the argmin go to cand2 (count in
-    // st->cnt2), and cand1 is not written (st->cnt1 still counts)
+    // second and third tiers inside the pass (non-null X; k <= 16): the
+    // near pairs (before the tiles) and every emitted pair are evaluated at
+    // once by the warp that holds them, from explicit FP32 differences (the
+    // explicit tier's arithmetic and error model, cert32), which tightens
+    // the bounds; the survivors wait in the warp's list and, once its tiles
+    // are done, those that can still be the argmin under the bound as it is
+    // then are evaluated in FP64 (the FP64 recheck's arithmetic).  Every
+    // block leaves its best (q = r^2, i, j) in partials[blockIdx.x] for the
+    // update.  No list is written; st->cnt1 counts the emitted pairs,
+    // st->cnt2 the FP64 evaluations.
     const float *X = nullptr;  // N x n FP32 points
     int n = 0;
     const float *U32 = nullptr;  // n x KP FP32 basis (pad columns zero)
     int KP = 0;
+    const double *U64 = nullptr;  // n x k FP64 basis, column-major
+    int k = 0;
+    double eps2 = 0.0;            // squared minimum secant length
     const int2 *near = nullptr;
     int n_near = 0;
-    int2 *cand2 = nullptr;
-    long long cap2 = 0;
-    Cert cert2;
+    Partial *partials = nullptr;
+    Cert cert32;
 };
 
 // One ring stage: the BF16 1/d^2 tile (32 KB), then the row side's point
@@ -353,59 +360,38 @@ __device__ __forceinline__ float bf16_at(const uint16_t *p) { return __uint_as_f
 constexpr int kConsumerWarps = 16;
 constexpr int kPassThreads = (kConsumerWarps + 1) * 32;
 
+// A second-tier survivor of the pass waiting for the FP64 tier (r: its FP32
+// explicit ratio, -1 when too short for FP32).
+struct DeferredPair {
+    int i, j;
+    float r;
+};
+constexpr int kDefer = 32;  // deferred survivors per consumer warp
+// dynamic shared memory of the pass: the 227 KB a block may hold, less the
+// static part (barriers, tile coordinates, the deferred survivors)
+constexpr int kPassDynSmem = 216 * 1024;
+
 // Explicit FP32 differences of E pairs by one warp (lanes over the
 // coordinates, the E (K + 1) sums reduced together), as in the explicit
 // tier: lane e < E receives pair e's ratio rr and code (1: rr valid, 2:
-// |x_i - x_j|^2 too small for FP32, the FP64 tier decides; 0: none).
+// |x_i - x_j|^2 too small for FP32, a later tier decides; 0: none).
+// expl32_finish reduces the per-lane sums acc[e (K + 1) + c].
 template <int K, int E>
-__device__ __forceinline__ void expl32_eval(const float *X, int n, const float *U32, int KP, const int2 (&pr)[E],
-                                            const bool (&valid)[E], int lane, float &rr, int &code)
+__device__ __forceinline__ void expl32_finish(float (&acc)[E * (K + 1)], const bool (&valid)[E], int lane, float &rr,
+                                              int &code)
 {
-    constexpr int KU = (K + 3) / 4 * 4;
     constexpr int M = E * (K + 1);
-    float acc[M];
+    static_assert(M <= 32, "pairs per warp times components");
+    constexpr int S = M <= 8 ? 8 : M <= 16 ? 16 : 32;
+    constexpr int dup = 32 / S;
+    float r[S];
 #pragma unroll
-    for (int q = 0; q < M; ++q) acc[q] = 0.f;
-#pragma unroll 2
-    for (int l = lane; l < n; l += 32) {
-        float u[KU];
-#pragma unroll
-        for (int c = 0; c < KU; c += 4) {
-            const float4 t = __ldcg(reinterpret_cast<const float4 *>(U32 + (size_t)l * KP + c));
-            u[c] = t.x; u[c + 1] = t.y; u[c + 2] = t.z; u[c + 3] = t.w;
-        }
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const float D = X[(size_t)pr[e].x * n + l] - X[(size_t)pr[e].y * n + l];
-            acc[e * (K + 1) + K] = fmaf(D, D, acc[e * (K + 1) + K]);
-#pragma unroll
-            for (int c = 0; c < K; ++c) acc[e * (K + 1) + c] = fmaf(u[c], D, acc[e * (K + 1) + c]);
-        }
-    }
+    for (int q = 0; q < S; ++q) r[q] = q < M ? acc[q < M ? q : 0] : 0.f;
+    const float t = warp_reduce_scatter<S>(r, lane);
+    const int me = lane < E ? lane : 0;
     float z[K + 1];
-    if constexpr (M <= 32) {
-        constexpr int S = M <= 8 ? 8 : M <= 16 ? 16 : 32;
-        constexpr int dup = 32 / S;
-        float r[S];
 #pragma unroll
-        for (int q = 0; q < S; ++q) r[q] = q < M ? acc[q < M ? q : 0] : 0.f;
-        const float t = warp_reduce_scatter<S>(r, lane);
-        const int e = lane < E ? lane : 0;
-#pragma unroll
-        for (int c = 0; c <= K; ++c) z[c] = __shfl_sync(0xffffffffu, t, (e * (K + 1) + c) * dup);
-    } else {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int q = 0; q < M; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-#pragma unroll
-        for (int c = 0; c <= K; ++c) z[c] = acc[c];
-#pragma unroll
-        for (int e = 1; e < E; ++e)
-            if (lane == e)
-#pragma unroll
-                for (int c = 0; c <= K; ++c) z[c] = acc[e * (K + 1) + c];
-    }
+    for (int c = 0; c <= K; ++c) z[c] = __shfl_sync(0xffffffffu, t, (me * (K + 1) + c) * dup);
     bool myvalid = valid[0];
 #pragma unroll
     for (int e = 1; e < E; ++e)
@@ -416,6 +402,43 @@ __device__ __forceinline__ void expl32_eval(const float *X, int n, const float *
     for (int c = 0; c < K; ++c) zz = fmaf(z[c], z[c], zz);
     code = (lane >= E || !myvalid) ? 0 : (dd < 1e-30f ? 2 : 1);
     rr = code == 1 ? sqrtf(zz / dd) : INFINITY;
+}
+
+// One coordinate l of the sums: |D|^2 and U^T D for each pair's D[e]
+template <int K, int E>
+__device__ __forceinline__ void expl32_step(float (&acc)[E * (K + 1)], const float *U32, int KP, int l,
+                                            const float (&D)[E])
+{
+    constexpr int KU = (K + 3) / 4 * 4;
+    float u[KU];
+#pragma unroll
+    for (int c = 0; c < KU; c += 4) {
+        const float4 t = __ldcg(reinterpret_cast<const float4 *>(U32 + (size_t)l * KP + c));
+        u[c] = t.x; u[c + 1] = t.y; u[c + 2] = t.z; u[c + 3] = t.w;
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        acc[e * (K + 1) + K] = fmaf(D[e], D[e], acc[e * (K + 1) + K]);
+#pragma unroll
+        for (int c = 0; c < K; ++c) acc[e * (K + 1) + c] = fmaf(u[c], D[e], acc[e * (K + 1) + c]);
+    }
+}
+
+template <int K, int E>
+__device__ __forceinline__ void expl32_eval(const float *X, int n, const float *U32, int KP, const int2 (&pr)[E],
+                                            const bool (&valid)[E], int lane, float &rr, int &code)
+{
+    float acc[E * (K + 1)];
+#pragma unroll
+    for (int q = 0; q < E * (K + 1); ++q) acc[q] = 0.f;
+#pragma unroll 2
+    for (int l = lane; l < n; l += 32) {
+        float D[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) D[e] = X[(size_t)pr[e].x * n + l] - X[(size_t)pr[e].y * n + l];
+        expl32_step<K, E>(acc, U32, KP, l, D);
+    }
+    expl32_finish<K, E>(acc, valid, lane, rr, code);
 }
 
 template <int K, int CPT, bool EXPL>
@@ -430,6 +453,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) uint64_t full[kPassStagesMax], empty[kPassStagesMax];
     __shared__ int2 sIJ[kPassStagesMax];
+    __shared__ Partial pbest[kConsumerWarps];  // tiers inside: the warps' best pairs
+    __shared__ unsigned int pdone;             // consumer warps finished
+    __shared__ DeferredPair defer[EXPL ? kConsumerWarps : 1][EXPL ? kDefer : 1];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -443,6 +469,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     const long long budget = 4000000000ll;
 
     if (tid == 0) {
+        pdone = 0;
         for (int s = 0; s < S; ++s) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], kConsumerWarps);
@@ -540,42 +567,76 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     const int col0 = seg * 32 * CPT + lane * CPT;
     const float seed = load_pos_float(&a.st->seed_ub);
     float uwarp = INFINITY;  // best upper bound this warp has produced
-    // second tier inside the pass: EX pairs per warp and round
+    // second tier inside the pass: EX pairs per warp and round; the pairs
+    // that survive it are evaluated in FP64 later (this warp's best)
     constexpr int EX = (K + 1) * 2 <= 32 ? 2 : 1;
-    auto expl_round = [&](const int2 (&pr)[EX], const bool (&valid)[EX]) {
-        float rr;
-        int code;
-        expl32_eval<K, EX>(a.X, a.n, a.U32, a.KP, pr, valid, lane, rr, code);
-        const float wmin = warp_min(rr);
-        // any earlier value of the running bound is a valid (looser) bound
-        float U2 = fminf(fminf(seed, uwarp), load_pos_float(&a.st->run_ub2));
-        if (wmin < INFINITY) {
-            const float ub = cert_upper(wmin, a.cert2);
-            if (lane == 0 && ub < U2) {
-                atomic_min_pos_float(&a.st->run_ub2, ub);
-                atomic_min_pos_float(&a.st->run_ub1, ub);  // bounds the pass's own emission too
-            }
-            U2 = fminf(U2, ub);
-            uwarp = fminf(uwarp, ub);
-        }
-        const float th = cert_emit_threshold(U2, a.cert2);
-        const unsigned int m = __ballot_sync(0xffffffffu, code == 2 || (code == 1 && rr <= th));
-        if (!m) return;
-        unsigned int b0 = 0;
-        if (lane == 0) b0 = atomicAdd((unsigned int *)&a.st->cnt2, (unsigned int)__popc(m));
-        b0 = __shfl_sync(0xffffffffu, b0, 0);
-        int2 mp = pr[0];
+    Partial best = {INFINITY, 0x7fffffff, 0x7fffffff};
+    int nd = 0;  // deferred survivors of this warp (warp-uniform)
+    auto fp64_pair = [&](int2 ij) {
+        if constexpr (EXPL) {
+            if (lane == 0) atomicAdd((unsigned int *)&a.st->cnt2, 1u);
+            // FP64: |D|^2 and U^T D with D = x_i - x_j (the FP64 recheck's sums)
+            double v[K + 1];
 #pragma unroll
-        for (int e = 1; e < EX; ++e)
-            if (lane == e) mp = pr[e];
-        if (m >> lane & 1u) {
-            const long long pos = (long long)b0 + __popc(m & ((1u << lane) - 1u));
-            if (pos < a.cap2) a.cand2[pos] = mp;
-            else atomicOr(&a.st->status, ST_OVERFLOW);
+            for (int q = 0; q <= K; ++q) v[q] = 0.0;
+#pragma unroll 4
+            for (int l = lane; l < a.n; l += 32) {
+                const double D = (double)a.X[(size_t)ij.x * a.n + l] - (double)a.X[(size_t)ij.y * a.n + l];
+                v[K] = fma(D, D, v[K]);
+#pragma unroll
+                for (int c = 0; c < K; ++c)
+                    if (c < a.k) v[c] = fma(a.U64[(size_t)c * a.n + l], D, v[c]);
+            }
+            double zz, d2;
+            warp_ratio_parts<K>(v, lane, zz, d2);
+            if (d2 == 0.0 || d2 < a.eps2) return;
+            const double q = zz / d2;
+            if (better_q(q, ij.x, ij.y, best.r, best.i, best.j)) best = Partial{q, ij.x, ij.y};
+        }
+    };
+    // the bounds from a round's FP32 ratios (lane e < EX: pair e), then its
+    // survivors to the warp's deferred list
+    auto expl_after = [&](const int2 (&pr)[EX], float rr, int code) {
+        if constexpr (EXPL) {
+            const float wmin = warp_min(rr);
+            // any earlier value of the running bound is a valid (looser) bound
+            float U2 = fminf(fminf(seed, uwarp), load_pos_float(&a.st->run_ub2));
+            auto tighten = [&](float ub) {
+                if (lane == 0 && ub < U2) {
+                    atomic_min_pos_float(&a.st->run_ub2, ub);
+                    atomic_min_pos_float(&a.st->run_ub1, ub);  // bounds the pass's own emission too
+                }
+                U2 = fminf(U2, ub);
+                uwarp = fminf(uwarp, ub);
+            };
+            if (wmin < INFINITY) tighten(cert_upper(wmin, a.cert32));
+            unsigned int m = __ballot_sync(0xffffffffu, code == 2 || (code == 1 && rr <= cert_emit_threshold(U2, a.cert32)));
+            // survivors wait in the warp's list until its tiles are done (the
+            // bound is far tighter by then); a full list evaluates at once
+            while (m) {
+                const int e = __ffs(m) - 1;
+                m &= m - 1u;
+                const float re = __shfl_sync(0xffffffffu, code == 2 ? -1.f : rr, e);
+                if (nd < kDefer) {
+                    if (lane == 0) defer[warp][nd] = DeferredPair{pr[e].x, pr[e].y, re};
+                    ++nd;
+                } else {
+                    fp64_pair(pr[e]);
+                }
+            }
+        }
+    };
+    auto expl_round = [&](const int2 (&pr)[EX], const bool (&valid)[EX]) {
+        if constexpr (EXPL) {
+            float rr;
+            int code;
+            expl32_eval<K, EX>(a.X, a.n, a.U32, a.KP, pr, valid, lane, rr, code);
+            expl_after(pr, rr, code);
         }
     };
     if constexpr (EXPL) {
-        // the near pairs, while the first stages' copies land
+        // the near pairs first, while the first stages' copies land: their
+        // bounds tighten the pass's early (survivors wait, see above)
         const long long G = (long long)gridDim.x * kConsumerWarps * EX;
         for (long long base = ((long long)blockIdx.x * kConsumerWarps + warp) * EX; base < a.n_near; base += G) {
             int2 pr[EX];
@@ -795,6 +856,29 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                             else atomicOr(&a.st->status, ST_OVERFLOW);
                             ++pos;
                         }
+            }
+        }
+    }
+    if constexpr (EXPL) {
+        // the deferred survivors against the bound as it is now
+        __syncwarp();
+        const float U2 = fminf(fminf(seed, uwarp), load_pos_float(&a.st->run_ub2));
+        const float th = cert_emit_threshold(U2, a.cert32);
+        for (int q = 0; q < nd; ++q) {
+            const DeferredPair d = defer[warp][q];
+            if (d.r <= th) fp64_pair(make_int2(d.i, d.j));  // r < 0: too short for FP32
+        }
+        // the block's best pair: the last consumer warp to finish merges
+        if (lane == 0) {
+            pbest[warp] = best;
+            __threadfence_block();
+            if (atomicAdd(&pdone, 1u) == kConsumerWarps - 1) {
+                __threadfence_block();
+                const volatile Partial *vb = pbest;
+                Partial b = {vb[0].r, vb[0].i, vb[0].j};
+                for (int w2 = 1; w2 < kConsumerWarps; ++w2)
+                    if (better_q(vb[w2].r, vb[w2].i, vb[w2].j, b.r, b.i, b.j)) b = Partial{vb[w2].r, vb[w2].i, vb[w2].j};
+                a.partials[blockIdx.x] = b;
             }
         }
     }
@@ -1534,7 +1618,7 @@ size_t pass_smem_bytes(int k, int KY, int stages) { return (size_t)stages * pass
 int pass_pick_stages(int k, int KY)
 {
     int s = kPassStagesMax;
-    while (s > 2 && pass_smem_bytes(k, KY, s) > 222 * 1024) --s;
+    while (s > 2 && pass_smem_bytes(k, KY, s) > (size_t)kPassDynSmem) --s;
     return s;
 }
 
@@ -1555,11 +1639,11 @@ template <int K, int CPT>
 cudaError_t config_pass_k()
 {
     cudaError_t e = cudaFuncSetAttribute(restr_pass_kernel<K, CPT, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kPassDynSmem);
     if constexpr (K <= 16)
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(restr_pass_kernel<K, CPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     224 * 1024);
+                                     kPassDynSmem);
     return e;
 }
 
@@ -1808,15 +1892,17 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
             p.n = n;
             p.U32 = b.U32;
             p.KP = b.KP;
+            p.U64 = b.U64;
+            p.k = b.k;
+            p.eps2 = handle_eps2(h);
             p.near = r.near;
             p.n_near = r.n_near;
-            p.cand2 = b.cand2;
-            p.cap2 = b.cap;
-            p.cert2 = cert_explicit(n, b.k);
+            p.partials = b.partials;
+            p.cert32 = cert_explicit(n, b.k);
         }
         handle_count_launch(h, 1, &ea, &eb);
         if (ea) cudaEventRecord(ea, s);
-        RCK(launch_pass(p, b.k, std::min(r.nwtiles, handle_sms(h)), s));
+        RCK(launch_pass(p, b.k, restructured_pass_grid(h), s));
         if (eb) cudaEventRecord(eb, s);
         handle_push_timing(h, 1, ea, eb);
     }
@@ -1918,6 +2004,8 @@ sap_status restructured_enqueue(sap_handle h, double alpha)
     b.cand1 = handle_cand1(h);
     b.cand2 = handle_cand2(h);
     b.cap = handle_cap(h);
+    b.U64 = handle_u64(h);
+    b.partials = handle_partials(h);
     return restructured_enqueue_basis(h, b, s);
 }
 
@@ -2034,15 +2122,17 @@ int restructured_tier_for(sap_handle h, int k)
 {
     const int t = handle_tune(h).refine;
     const int n = handle_n_dim(h);
-    if (t == 5) return explicit_uses_df(n) || k > 16 ? 0 : 5;
+    if (t == 5) return k > 16 ? 0 : 5;
     if (t == 4) return 4;
     if (t == 3) return k <= 8 ? 3 : 0;
     if (t == 2) return explicit_uses_df(n) ? 0 : 2;
-    if (t < 0) return n > 256 ? 1 : (k <= 16 ? 5 : 0);
+    if (t < 0) return k <= 16 ? 5 : n > 256 ? 1 : 0;
     return t != 0 ? 1 : 0;
 }
 
 int restructured_tier(sap_handle h) { return restructured_tier_for(h, handle_k(h)); }
+
+int restructured_pass_grid(sap_handle h) { return std::min(restr_state(h).nwtiles, handle_sms(h)); }
 
 bool restructured_uses_refine(sap_handle h) { return restructured_tier(h) == 1; }
 
@@ -2053,6 +2143,12 @@ void restructured_fuse_args(sap_handle h, const BasisView &b, SelectUpdateArgs &
     u.n_near = 0;
     u.cert2 = cert_explicit(handle_n_dim(h), b.k);
     const int tier = restructured_tier_for(h, b.k);
+    if (tier == 5) {
+        // the pass left its blocks' best pairs: one block takes the argmin
+        u.pass_parts = restructured_pass_grid(h);
+        u.grid = 1;
+        return;
+    }
     if (tier == 4) {
         // the extended tier's packed list, filtered by the final bound
         u.fused = 4;

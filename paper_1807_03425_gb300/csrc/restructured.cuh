@@ -56,6 +56,9 @@ int handle_sms(sap_handle h);
 ProbState *handle_state(sap_handle h);
 const float *handle_x32(sap_handle h);
 const float *handle_u32(sap_handle h);
+int restructured_pass_grid(sap_handle h);  // blocks of the all-pairs pass
+Partial *handle_partials(sap_handle h);
+double *handle_u64(sap_handle h);
 const float *handle_u32lo(sap_handle h);
 int2 *handle_cand1(sap_handle h);
 int2 *handle_cand2(sap_handle h);
@@ -86,6 +89,8 @@ struct BasisView {
     ProbState *st;
     int2 *cand1, *cand2;      // candidate lists of the pass and of the explicit tier
     long long cap;            // capacity of each list
+    const double *U64;        // n x k FP64 basis, column-major (tiers inside the pass)
+    Partial *partials;        // per-block best pairs (tiers inside the pass)
 };
 
 // Restructured-form entry points (restructured.cu).

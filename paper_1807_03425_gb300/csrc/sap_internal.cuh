@@ -93,8 +93,8 @@ struct TuneParams {
     int pdl = 0;             // programmatic dependent launch between the kernels of an iteration
     int refine = -1;         // second tier: 1 double-float refine, 0 explicit differences, 2 / 3 explicit
                              // (FP32 / extended precision) fused into the FP64 recheck, 4 extended precision
-                             // with ratios for a final filter, 5 explicit FP32 inside the pass, -1 by n
-                             // and k (n > 256: refine, else k <= 16: 5, else 0)
+                             // with ratios for a final filter, 5 extended precision and FP64 inside the
+                             // pass, -1 by k and n (k <= 16: 5, else n > 256: refine, else 0)
     double us_per_iter = 0;  // measured by the tuner (0: not tuned)
 };
 
@@ -220,6 +220,56 @@ __device__ __forceinline__ V warp_reduce_scatter(V (&v)[S], int lane)
 #pragma unroll
     for (int o = 16 / S; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
     return v[0];
+}
+
+// Warp sums of M values at once (levels outer, values inner, so the M
+// dependency chains overlap).
+template <typename V, int M>
+__device__ __forceinline__ void warp_sum_multi(V (&v)[M])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < M; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+}
+
+// d2 = |D|^2 and zz = |U^T D|^2 from per-lane partial sums v[0..K-1] (U^T D)
+// and v[K] (|D|^2), delivered to every lane.
+template <int K>
+__device__ __forceinline__ void warp_ratio_parts(double (&v)[K + 1], int lane, double &zz, double &d2)
+{
+    constexpr int M = K + 1;
+    if constexpr (M <= 32) {
+        constexpr int S = M <= 8 ? 8 : M <= 16 ? 16 : 32;
+        constexpr int dup = 32 / S;  // lanes holding the same entry
+        double r[S];
+#pragma unroll
+        for (int q = 0; q < S; ++q) r[q] = q < M ? v[q < M ? q : 0] : 0.0;
+        const double t = warp_reduce_scatter<S>(r, lane);
+        const int idx = rs_index<S>(lane);
+        double sq = (idx < K && lane % dup == 0) ? t * t : 0.0;
+#pragma unroll
+        for (int o = 16; o >= dup; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        zz = __shfl_sync(0xffffffffu, sq, 0);
+        d2 = __shfl_sync(0xffffffffu, t, K * dup);
+    } else {
+        warp_sum_multi<double, K + 1>(v);
+        d2 = v[K];
+        zz = 0.0;
+#pragma unroll
+        for (int c = 0; c < K; ++c) zz = fma(v[c], v[c], zz);
+    }
+}
+
+// (q, i, j) ordering for q >= 0 (no NaN): the bit patterns of non-negative
+// doubles order like their values, so the compare stays off the FP64 pipe.
+__device__ __forceinline__ bool better_q(double q, int i, int j, double qb, int ib, int jb)
+{
+    const unsigned long long a = (unsigned long long)__double_as_longlong(q);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(qb);
+    if (a != b) return a < b;
+    if (i != ib) return i < ib;
+    return j < jb;
 }
 
 __device__ __forceinline__ float warp_min(float v)
@@ -520,6 +570,10 @@ struct SelectUpdateArgs {
     // data); an update that changes the basis then only resets the seed
     // bound to +inf
     int seeds_in_product = 0;
+    // > 0: the all-pairs pass evaluated every candidate in FP64 and left its
+    // blocks' best pairs in partials[0 .. pass_parts - 1]; one block takes
+    // the argmin and updates (no list is read)
+    int pass_parts = 0;
 };
 cudaError_t launch_select_update(const SelectUpdateArgs &a, cudaStream_t s);
 

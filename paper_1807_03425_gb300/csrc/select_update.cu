@@ -78,17 +78,6 @@ __device__ __forceinline__ TX ld_x(const void *X, size_t idx)
     return static_cast<const TX *>(X)[idx];
 }
 
-// Warp sums of M values at once (levels outer, values inner, so the M
-// dependency chains overlap).
-template <typename V, int M>
-__device__ __forceinline__ void warp_sum_multi(V (&v)[M])
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < M; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-}
-
 // Block sums of M values; result in out[0..M-1] (shared), visible to all.
 template <typename V, int M>
 __device__ __forceinline__ void block_sum_multi(V (&v)[M], V *scratch /* NW*M */, V *out)
@@ -107,45 +96,6 @@ __device__ __forceinline__ void block_sum_multi(V (&v)[M], V *scratch /* NW*M */
         out[threadIdx.x] = s;
     }
     __syncthreads();
-}
-
-// d2 = |D|^2 and zz = |U^T D|^2 from per-lane partial sums v[0..K-1] (U^T D)
-// and v[K] (|D|^2), delivered to every lane.
-template <int K>
-__device__ __forceinline__ void warp_ratio_parts(double (&v)[K + 1], int lane, double &zz, double &d2)
-{
-    constexpr int M = K + 1;
-    if constexpr (M <= 32) {
-        constexpr int S = M <= 8 ? 8 : M <= 16 ? 16 : 32;
-        constexpr int dup = 32 / S;  // lanes holding the same entry
-        double r[S];
-#pragma unroll
-        for (int q = 0; q < S; ++q) r[q] = q < M ? v[q < M ? q : 0] : 0.0;
-        const double t = warp_reduce_scatter<S>(r, lane);
-        const int idx = rs_index<S>(lane);
-        double sq = (idx < K && lane % dup == 0) ? t * t : 0.0;
-#pragma unroll
-        for (int o = 16; o >= dup; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        zz = __shfl_sync(0xffffffffu, sq, 0);
-        d2 = __shfl_sync(0xffffffffu, t, K * dup);
-    } else {
-        warp_sum_multi<double, K + 1>(v);
-        d2 = v[K];
-        zz = 0.0;
-#pragma unroll
-        for (int c = 0; c < K; ++c) zz = fma(v[c], v[c], zz);
-    }
-}
-
-// (q, i, j) ordering for q >= 0 (no NaN): the bit patterns of non-negative
-// doubles order like their values, so the compare stays off the FP64 pipe.
-__device__ __forceinline__ bool better_q(double q, int i, int j, double qb, int ib, int jb)
-{
-    const unsigned long long a = (unsigned long long)__double_as_longlong(q);
-    const unsigned long long b = (unsigned long long)__double_as_longlong(qb);
-    if (a != b) return a < b;
-    if (i != ib) return i < ib;
-    return j < jb;
 }
 
 // Dynamic shared memory of phase 2 when the basis fits: U' (FP64), D (data
@@ -443,7 +393,10 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         grid_dep_wait();
     }
     Partial best = {INFINITY, 0x7fffffff, 0x7fffffff};
-    if (fused3) {
+    if (a.pass_parts > 0) {
+        // the pass evaluated every candidate: its blocks' best pairs wait in
+        // partials[], and this single block goes straight to phase 2
+    } else if (fused3) {
         // ---------------- phase 1 (fused == 3): extended-precision tier ----
         // Each warp evaluates E0 listed pairs from explicit differences in
         // extended precision, tightens the running bound from their minimum
@@ -639,7 +592,9 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
     // each block publishes its best; the last block to finish continues
     if (lane == 0) sh.wb[w] = best;
     __syncthreads();
-    if (tid == 0) {
+    if (a.pass_parts > 0) {
+        if (tid == 0) sh.last = 1;
+    } else if (tid == 0) {
         Partial b = sh.wb[0];
         for (int q = 1; q < NW; ++q)
             if (better_q(sh.wb[q].r, sh.wb[q].i, sh.wb[q].j, b.r, b.i, b.j)) b = sh.wb[q];
@@ -679,7 +634,8 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
     };
     if (w == 0) {
         Partial b = {INFINITY, 0x7fffffff, 0x7fffffff};
-        for (int p = lane; p < (int)gridDim.x; p += 32) {
+        const int nparts = a.pass_parts > 0 ? a.pass_parts : (int)gridDim.x;
+        for (int p = lane; p < nparts; p += 32) {
             const volatile Partial *vp = &a.partials[p];
             const Partial q = {vp->r, vp->i, vp->j};
             if (better_q(q.r, q.i, q.j, b.r, b.i, b.j)) b = q;

@@ -218,6 +218,8 @@ sap_status enqueue_iteration(sap_handle h, SweepState &sw, double alpha, int eva
         v.cand1 = b.cand1;
         v.cand2 = b.cand2;
         v.cap = sw.cap;
+        v.U64 = b.U64;
+        v.partials = b.partials;
         st = restructured_enqueue_basis(h, v, b.stream);
         if (st != SAP_OK) return st;
         const SelectUpdateArgs u = update_args(h, sw, b, alpha, eval_only);

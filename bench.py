@@ -49,8 +49,8 @@ CFG_NAME = "c2"
 # DRAM traffic of one restructured-pass launch from the ncu capture of this
 # kernel on this workload, valid only while the pass kernel's source is
 # unchanged (hash below, kernel_source_sha).
-PASS_TRAFFIC_BYTES = 69096192   # 68.536 MB read + 0.560 MB written
-PASS_SOURCE_SHA = "e29efe2e5bc65299"
+PASS_TRAFFIC_BYTES = 72252672   # 71.113 MB read + 1.139 MB written
+PASS_SOURCE_SHA = "0925291acacc6c75"
 
 
 def kernel_source_sha() -> str:
@@ -72,7 +72,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="moment_curve",
-                    choices=["moment_curve", "fp64_small", "sweep", "batch", "softmin", "subsample", "pca"])
+                    choices=["moment_curve", "fp64_small", "sweep", "batch", "softmin", "subsample", "pca",
+                             "profile"])
     return ap.parse_args()
 
 
@@ -1023,6 +1024,34 @@ def run_pca(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """A few untimed iterations of the bench workload, launched eagerly one
+    by one (no graphs), for a profiler's launch list or a capture of one
+    kernel: set_basis, then --steps iterations of product, pass and update
+    (three launches each).  Default launch parameters but the pass bound the
+    autotuner picks on this workload (2e-3); prints one JSON line."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_1807_03425_gb300 import Sap
+    cfg = W.CONFIGS[CFG_NAME]
+    N, n, k, alpha = cfg["N"], 2 * cfg["m"], cfg["k"], cfg["alpha"]
+    X = W.moment_curve(N, cfg["m"], cfg["data_seed"], np.float32)
+    U0 = W.random_basis(n, k, cfg["basis_seed"])
+    steps = args.steps or 6
+    with Sap(X) as s:
+        s.set_path("restructured")
+        s.set_tuning(pass_bound=2e-3)
+        s.set_basis(U0)
+        for _ in range(steps):
+            s.step(alpha)
+        torch.cuda.synchronize()
+        st = s.stats()
+        print(json.dumps({"workload": cfg["workload"], "profile_steps": steps, "tuning": s.tuning(),
+                          "candidates_last_step": {"pass": st["last_tier1"], "fp64": st["last_tier2"]}}),
+              flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference" or args.workload == "moment_curve":
@@ -1036,7 +1065,8 @@ def main():
         run_native(args)
     else:
         {"fp64_small": run_fp64_small, "sweep": run_sweep, "batch": run_batch,
-         "softmin": run_softmin, "subsample": run_subsample, "pca": run_pca}[args.workload](args)
+         "softmin": run_softmin, "subsample": run_subsample, "pca": run_pca,
+         "profile": run_profile}[args.workload](args)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.impl != "reference":
         import torch.distributed as tdist
         if tdist.is_initialized():

@@ -113,6 +113,7 @@ struct ProbState {
     int hist_cap;           // capacity of the history arrays
     unsigned int ticket;    // blocks of the select/update launch that finished
     int2 watch[kWatch];
+    int seed_miss;          // evaluations since the seed bound was last within 1% of the minimum
     double last_r;          // result of the latest evaluation
     int last_i, last_j;
     // dynamic tiles handed out by the restructured pass; on a cache line of

@@ -681,6 +681,11 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
         }
         const double r = none ? b.r : sqrt(b.r);
         const int it = sh.iter;
+        if (!none) {
+            // whether the seed bound this evaluation started from was tight
+            const float sd = __uint_as_float(st->seed_ub);
+            st->seed_miss = sd <= (float)r * 1.01f ? 0 : min(st->seed_miss + 1, 1 << 20);
+        }
         if (none) atomicOr(&st->status, ST_NO_SECANT);
         if (it < sh.hist_cap) {
             a.hist[it] = none ? __longlong_as_double(0x7ff8000000000000ll) : r;

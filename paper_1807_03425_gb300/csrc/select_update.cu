@@ -635,10 +635,23 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
     if (w == 0) {
         Partial b = {INFINITY, 0x7fffffff, 0x7fffffff};
         const int nparts = a.pass_parts > 0 ? a.pass_parts : (int)gridDim.x;
-        for (int p = lane; p < nparts; p += 32) {
-            const volatile Partial *vp = &a.partials[p];
-            const Partial q = {vp->r, vp->i, vp->j};
-            if (better_q(q.r, q.i, q.j, b.r, b.i, b.j)) b = q;
+        // eight results per lane and round, their loads issued together
+        // (L2 only: the writers were other blocks)
+        for (int p0 = 0; p0 < nparts; p0 += 256) {
+            long long rq[8], ij[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int p = p0 + lane + 32 * u;
+                const long long *src = reinterpret_cast<const long long *>(a.partials + (p < nparts ? p : 0));
+                rq[u] = __ldcg(src);
+                ij[u] = __ldcg(src + 1);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (p0 + lane + 32 * u >= nparts) break;
+                const Partial q = {__longlong_as_double(rq[u]), (int)(ij[u] & 0xffffffff), (int)(ij[u] >> 32)};
+                if (better_q(q.r, q.i, q.j, b.r, b.i, b.j)) b = q;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

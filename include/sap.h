@@ -411,7 +411,8 @@ typedef struct {
  */
 sap_status sap_autotune(sap_handle h, double alpha, int32_t iters, sap_tuning *out);
 
-/* The handle's current launch parameters. */
+/* The handle's current launch parameters (a batch handle: its first
+ * dataset's). */
 sap_status sap_get_tuning(sap_handle h, sap_tuning *out);
 
 /* Set the launch parameters by hand (ranges as in sap_tuning, else

@@ -772,6 +772,15 @@ class SapBatch:
         """Tune every dataset (each against its own shape)."""
         _check(self.h, load_library().sap_autotune(self.h, alpha, iters, None))
 
+    def tuning(self):
+        """The first dataset's launch parameters (sap_get_tuning)."""
+        return sap_get_tuning(self.h)
+
+    def set_tuning(self, **params):
+        """Launch parameters of every dataset (sap_set_tuning); unnamed
+        parameters keep the first dataset's values."""
+        sap_set_tuning(self.h, **params)
+
     def set_pass_bound(self, b_cap):
         sap_set_pass_bound(self.h, b_cap)
 

@@ -822,9 +822,8 @@ static void to_public(const TuneParams &p, sap_tuning *out)
 sap_status sap_get_tuning(sap_handle h, sap_tuning *out)
 {
     CHECK_HANDLE(h);
-    NOT_BATCH(h);
     if (!out) return fail(h, SAP_E_ARG, "null output");
-    to_public(h->tune, out);
+    to_public(h->is_batch ? h->kids[0]->tune : h->tune, out);  // a batch: its first dataset's
     return SAP_OK;
 }
 

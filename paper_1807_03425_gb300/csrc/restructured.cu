@@ -576,19 +576,22 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
         if constexpr (EXPL) {
             if (lane == 0) atomicAdd((unsigned int *)&a.st->cnt2, 1u);
             // FP64: |D|^2 and U^T D with D = x_i - x_j (the FP64 recheck's sums)
-            double v[K + 1];
+            // (the FP64 recheck's compute width for this k, so its sums
+            // are the same in the same order: the same q = r^2 bits)
+            constexpr int KS = K <= 8 ? K : K <= 12 ? 12 : K <= 16 ? 16 : K <= 24 ? 24 : 32;
+            double v[KS + 1];
 #pragma unroll
-            for (int q = 0; q <= K; ++q) v[q] = 0.0;
+            for (int q = 0; q <= KS; ++q) v[q] = 0.0;
 #pragma unroll 4
             for (int l = lane; l < a.n; l += 32) {
                 const double D = (double)a.X[(size_t)ij.x * a.n + l] - (double)a.X[(size_t)ij.y * a.n + l];
-                v[K] = fma(D, D, v[K]);
+                v[KS] = fma(D, D, v[KS]);
 #pragma unroll
-                for (int c = 0; c < K; ++c)
+                for (int c = 0; c < KS; ++c)
                     if (c < a.k) v[c] = fma(a.U64[(size_t)c * a.n + l], D, v[c]);
             }
             double zz, d2;
-            warp_ratio_parts<K>(v, lane, zz, d2);
+            warp_ratio_parts<KS>(v, lane, zz, d2);
             if (d2 == 0.0 || d2 < a.eps2) return;
             const double q = zz / d2;
             if (better_q(q, ij.x, ij.y, best.r, best.i, best.j)) best = Partial{q, ij.x, ij.y};
@@ -1653,7 +1656,7 @@ cudaError_t configure_pass_kernels()
     auto f = [&](cudaError_t x) { if (x != cudaSuccess) e = x; };
     f(config_pass_k<1, 4>()); f(config_pass_k<2, 4>()); f(config_pass_k<3, 4>()); f(config_pass_k<4, 4>());
     f(config_pass_k<5, 4>()); f(config_pass_k<6, 4>()); f(config_pass_k<7, 4>()); f(config_pass_k<8, 4>());
-    f(config_pass_k<12, 2>()); f(config_pass_k<16, 2>()); f(config_pass_k<24, 1>()); f(config_pass_k<32, 1>());
+    f(config_pass_k<10, 2>()); f(config_pass_k<12, 2>()); f(config_pass_k<16, 2>()); f(config_pass_k<24, 1>()); f(config_pass_k<32, 1>());
     return e;
 }
 
@@ -1670,6 +1673,7 @@ cudaError_t launch_pass(const PassArgs &a, int k, int grid, cudaStream_t s)
     case 8: return launch_pass_k<8, 4>(a, grid, s);
     default: break;
     }
+    if (k <= 10) return launch_pass_k<10, 2>(a, grid, s);
     if (k <= 12) return launch_pass_k<12, 2>(a, grid, s);
     if (k <= 16) return launch_pass_k<16, 2>(a, grid, s);
     if (k <= 24) return launch_pass_k<24, 1>(a, grid, s);

@@ -89,6 +89,24 @@ def test_full_size_uneven_batch(P):
     check_eval(X64, Us_small, int(am[small, T, 0]), int(am[small, T, 1]), hist[small, T], cfg["eps"])
 
 
+def test_batch_tuning_applies_to_every_dataset(P):
+    """set_tuning on a batch handle reaches every dataset; the second tier in
+    its own kernel and inside the pass give the same trajectories, bit for
+    bit, for three scenes of different sizes (k = 10: the width-10 pass)."""
+    Xs, _ = W.hyperspectral_batch(3, 11, n_min=300, n_max=1500)
+    Us = [W.random_basis(224, 10, 40 + b) for b in range(3)]
+    runs = []
+    for tier in (0, 5):
+        with P.SapBatch([W.bf16_bits(X) for X in Xs], dtype=P.BF16) as sb:
+            sb.set_min_secant_length(0.05)
+            sb.set_tuning(refine_tier=tier, pass_bound=4e-3)
+            assert sb.tuning()["refine_tier"] == tier and sb.tuning()["pass_bound"] == 4e-3
+            for b in range(3):
+                sb.set_basis(b, Us[b])
+            runs.append(sb.run(0.01, 6))
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
 def test_batch_argument_errors(P):
     Xs, _ = W.hyperspectral_batch(2, 3, n_min=50, n_max=80, n_bands=16)
     with P.SapBatch(Xs) as sb:

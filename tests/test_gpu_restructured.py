@@ -155,7 +155,7 @@ def test_c2_restructured_full_size(P):
 
 
 @pytest.mark.parametrize("tier", [0, 1, 2, 3, 4, 5])
-@pytest.mark.parametrize("N,n,k", [(600, 300, 3), (450, 40, 1), (700, 100, 5), (800, 60, 12)])
+@pytest.mark.parametrize("N,n,k", [(600, 300, 3), (450, 40, 1), (700, 100, 5), (800, 60, 12), (650, 48, 10)])
 def test_second_tiers_lockstep(P, tier, N, n, k):
     """Every second tier (explicit differences, double-float refine,
     explicit differences fused into the FP64 recheck in FP32 or in extended
@@ -179,3 +179,26 @@ def test_second_tiers_lockstep(P, tier, N, n, k):
                      plain_blocks_per_sm=2, programmatic_launch=0, refine_tier=tier)
         for _ in range(5):
             U, _ = lockstep(s, X64, U, 0.01)
+
+
+@pytest.mark.parametrize("k", [3, 9, 10, 12, 16])
+def test_tier_forms_agree_bitwise(P, k):
+    """The second tier in its own kernel (explicit FP32, double-float) and
+    inside the pass (with the FP64 tier, a one-block update over the pass's
+    results) select different candidates but take the same FP64 decisions:
+    15 iterations give bitwise-identical histories, argmins and bases, for
+    the exact and the padded compute widths of the pass (k = 9, 10 use the
+    width-10 pass, k = 12 the width-12 one)."""
+    X = W.moment_curve(1100, 16, 70 + k, np.float32)
+    U0 = W.random_basis(32, k, 71 + k)
+    runs = []
+    for tier in (0, 1, 5):
+        with P.Sap(X) as s:
+            s.set_path("restructured")
+            s.set_tuning(refine_tier=tier)
+            s.set_basis(U0)
+            hist, am = s.run(0.01, 15)
+            runs.append((hist, am, s.get_basis()))
+    for other in runs[1:]:
+        for a, b in zip(runs[0], other):
+            assert np.array_equal(a, b)

@@ -310,12 +310,16 @@ struct PassArgs {
 // pairs, 1 KB each), else the KY components of Y -- and the column side's
 // (k, else KY, components of Y; one copy each, block-major), then the 128
 // point norms nu of each side.
-__host__ __device__ inline uint32_t pass_row_bytes(int k, int KY) { return k <= 8 ? (uint32_t)k * T * 8 : (uint32_t)T * KY * 4; }
-__host__ __device__ inline uint32_t pass_col_bytes(int k, int KY) { return k <= 8 ? (uint32_t)k * T * 4 : (uint32_t)T * KY * 4; }
-__host__ __device__ inline uint32_t pass_stage_bytes(int k, int KY)
+// kd: the compute width of a pass class with four columns per thread
+// (k <= 10), which stages kd components per side (the row side from the
+// doubled copy); 0: the other classes, which stage all KY components.
+__host__ __device__ inline uint32_t pass_row_bytes(int kd, int KY) { return kd ? (uint32_t)kd * T * 8 : (uint32_t)T * KY * 4; }
+__host__ __device__ inline uint32_t pass_col_bytes(int kd, int KY) { return kd ? (uint32_t)kd * T * 4 : (uint32_t)T * KY * 4; }
+__host__ __device__ inline uint32_t pass_stage_bytes(int kd, int KY)
 {
-    return (uint32_t)T * T * 2 + pass_row_bytes(k, KY) + pass_col_bytes(k, KY) + 2u * T * 4;
+    return (uint32_t)T * T * 2 + pass_row_bytes(kd, KY) + pass_col_bytes(kd, KY) + 2u * T * 4;
 }
+inline int pass_kd(int k) { return k <= 8 ? k : k <= 10 ? 10 : 0; }
 
 // Certified error of one stored pair's ratio from the tensor-core Y:
 // |r~ - r| <= beta (nu_i + nu_j) / d_ij + rho r.  1/d_ij is taken as the
@@ -460,9 +464,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int KY = a.KY, S = a.stages;
-    constexpr bool DBL = CPT == 4;  // row side from the doubled copy (k = K <= 8)
-    const uint32_t wbytes = T * T * 2, ibytes = pass_row_bytes(DBL ? K : 9, KY),
-                   jbytes = pass_col_bytes(DBL ? K : 9, KY), sbytes = wbytes + ibytes + jbytes + 2 * T * 4;
+    constexpr bool DBL = CPT == 4;  // row side from the doubled copy (K <= 10)
+    const uint32_t wbytes = T * T * 2, ibytes = pass_row_bytes(DBL ? K : 0, KY),
+                   jbytes = pass_col_bytes(DBL ? K : 0, KY), sbytes = wbytes + ibytes + jbytes + 2 * T * 4;
     // tiles below gridDim.x * S are static (it < S); the rest are dynamic
     const int nall = blockIdx.x < (unsigned)a.ntiles ? (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     const int nstatic = nall < S ? nall : S;
@@ -1616,12 +1620,12 @@ sap_status classify(sap_handle h, int k)
     return SAP_OK;
 }
 
-size_t pass_smem_bytes(int k, int KY, int stages) { return (size_t)stages * pass_stage_bytes(k, KY); }
+size_t pass_smem_bytes(int kd, int KY, int stages) { return (size_t)stages * pass_stage_bytes(kd, KY); }
 
 int pass_pick_stages(int k, int KY)
 {
     int s = kPassStagesMax;
-    while (s > 2 && pass_smem_bytes(k, KY, s) > (size_t)kPassDynSmem) --s;
+    while (s > 2 && pass_smem_bytes(pass_kd(k), KY, s) > (size_t)kPassDynSmem) --s;
     return s;
 }
 
@@ -1629,7 +1633,7 @@ int pass_pick_stages(int k, int KY)
 template <int K, int CPT>
 cudaError_t launch_pass_k(const PassArgs &a, int grid, cudaStream_t s)
 {
-    const size_t shm = pass_smem_bytes(CPT == 4 ? K : 9, a.KY, a.stages);
+    const size_t shm = pass_smem_bytes(CPT == 4 ? K : 0, a.KY, a.stages);
     if constexpr (K <= 16) {
         if (a.X) return launch_pdl(a.pdl != 0, restr_pass_kernel<K, CPT, true>, dim3(grid), dim3(kPassThreads), shm, s, a);
     } else {
@@ -1656,7 +1660,7 @@ cudaError_t configure_pass_kernels()
     auto f = [&](cudaError_t x) { if (x != cudaSuccess) e = x; };
     f(config_pass_k<1, 4>()); f(config_pass_k<2, 4>()); f(config_pass_k<3, 4>()); f(config_pass_k<4, 4>());
     f(config_pass_k<5, 4>()); f(config_pass_k<6, 4>()); f(config_pass_k<7, 4>()); f(config_pass_k<8, 4>());
-    f(config_pass_k<10, 2>()); f(config_pass_k<12, 2>()); f(config_pass_k<16, 2>()); f(config_pass_k<24, 1>()); f(config_pass_k<32, 1>());
+    f(config_pass_k<10, 4>()); f(config_pass_k<12, 2>()); f(config_pass_k<16, 2>()); f(config_pass_k<24, 1>()); f(config_pass_k<32, 1>());
     return e;
 }
 
@@ -1673,7 +1677,7 @@ cudaError_t launch_pass(const PassArgs &a, int k, int grid, cudaStream_t s)
     case 8: return launch_pass_k<8, 4>(a, grid, s);
     default: break;
     }
-    if (k <= 10) return launch_pass_k<10, 2>(a, grid, s);
+    if (k <= 10) return launch_pass_k<10, 4>(a, grid, s);
     if (k <= 12) return launch_pass_k<12, 2>(a, grid, s);
     if (k <= 16) return launch_pass_k<16, 2>(a, grid, s);
     if (k <= 24) return launch_pass_k<24, 1>(a, grid, s);

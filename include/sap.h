@@ -388,8 +388,8 @@ typedef struct {
                                        at once by the warp that found it, and evaluated in FP64
                                        there if it can still be the argmin; one block then takes
                                        the argmin and updates (two launches fewer, no lists;
-                                       k <= 16, else as 0), -1 chosen by k and n (5 for k <= 16,
-                                       else double-float above n = 256, else 0) */
+                                       k <= 16, else as 0), -1 chosen by n and k (double-float
+                                       above n = 256, else 5 for k <= 16, else 0) */
     double us_per_iteration;        /* measured by sap_autotune; 0 when set by hand */
 } sap_tuning;
 

@@ -311,7 +311,7 @@ struct PassArgs {
 // (k, else KY, components of Y; one copy each, block-major), then the 128
 // point norms nu of each side.
 // kd: the compute width of a pass class with four columns per thread
-// (k <= 10), which stages kd components per side (the row side from the
+// (k <= 16), which stages kd components per side (the row side from the
 // doubled copy); 0: the other classes, which stage all KY components.
 __host__ __device__ inline uint32_t pass_row_bytes(int kd, int KY) { return kd ? (uint32_t)kd * T * 8 : (uint32_t)T * KY * 4; }
 __host__ __device__ inline uint32_t pass_col_bytes(int kd, int KY) { return kd ? (uint32_t)kd * T * 4 : (uint32_t)T * KY * 4; }
@@ -319,7 +319,7 @@ __host__ __device__ inline uint32_t pass_stage_bytes(int kd, int KY)
 {
     return (uint32_t)T * T * 2 + pass_row_bytes(kd, KY) + pass_col_bytes(kd, KY) + 2u * T * 4;
 }
-inline int pass_kd(int k) { return k <= 8 ? k : k <= 10 ? 10 : 0; }
+inline int pass_kd(int k) { return k <= 8 ? k : k <= 10 ? 10 : k <= 12 ? 12 : k <= 16 ? 16 : 0; }
 
 // Certified error of one stored pair's ratio from the tensor-core Y:
 // |r~ - r| <= beta (nu_i + nu_j) / d_ij + rho r.  1/d_ij is taken as the
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int KY = a.KY, S = a.stages;
-    constexpr bool DBL = CPT == 4;  // row side from the doubled copy (K <= 10)
+    constexpr bool DBL = CPT == 4;  // row side from the doubled copy (K <= 16)
     const uint32_t wbytes = T * T * 2, ibytes = pass_row_bytes(DBL ? K : 0, KY),
                    jbytes = pass_col_bytes(DBL ? K : 0, KY), sbytes = wbytes + ibytes + jbytes + 2 * T * 4;
     // tiles below gridDim.x * S are static (it < S); the rest are dynamic
@@ -1660,7 +1660,7 @@ cudaError_t configure_pass_kernels()
     auto f = [&](cudaError_t x) { if (x != cudaSuccess) e = x; };
     f(config_pass_k<1, 4>()); f(config_pass_k<2, 4>()); f(config_pass_k<3, 4>()); f(config_pass_k<4, 4>());
     f(config_pass_k<5, 4>()); f(config_pass_k<6, 4>()); f(config_pass_k<7, 4>()); f(config_pass_k<8, 4>());
-    f(config_pass_k<10, 4>()); f(config_pass_k<12, 2>()); f(config_pass_k<16, 2>()); f(config_pass_k<24, 1>()); f(config_pass_k<32, 1>());
+    f(config_pass_k<10, 4>()); f(config_pass_k<12, 4>()); f(config_pass_k<16, 4>()); f(config_pass_k<24, 1>()); f(config_pass_k<32, 1>());
     return e;
 }
 
@@ -1678,8 +1678,8 @@ cudaError_t launch_pass(const PassArgs &a, int k, int grid, cudaStream_t s)
     default: break;
     }
     if (k <= 10) return launch_pass_k<10, 4>(a, grid, s);
-    if (k <= 12) return launch_pass_k<12, 2>(a, grid, s);
-    if (k <= 16) return launch_pass_k<16, 2>(a, grid, s);
+    if (k <= 12) return launch_pass_k<12, 4>(a, grid, s);
+    if (k <= 16) return launch_pass_k<16, 4>(a, grid, s);
     if (k <= 24) return launch_pass_k<24, 1>(a, grid, s);
     return launch_pass_k<32, 1>(a, grid, s);
 }
@@ -2134,7 +2134,7 @@ int restructured_tier_for(sap_handle h, int k)
     if (t == 4) return 4;
     if (t == 3) return k <= 8 ? 3 : 0;
     if (t == 2) return explicit_uses_df(n) ? 0 : 2;
-    if (t < 0) return k <= 16 ? 5 : n > 256 ? 1 : 0;
+    if (t < 0) return n > 256 ? 1 : k <= 16 ? 5 : 0;
     return t != 0 ? 1 : 0;
 }
 

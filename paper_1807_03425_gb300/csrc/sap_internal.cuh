@@ -94,7 +94,7 @@ struct TuneParams {
     int refine = -1;         // second tier: 1 double-float refine, 0 explicit differences, 2 / 3 explicit
                              // (FP32 / extended precision) fused into the FP64 recheck, 4 extended precision
                              // with ratios for a final filter, 5 extended precision and FP64 inside the
-                             // pass, -1 by k and n (k <= 16: 5, else n > 256: refine, else 0)
+                             // pass, -1 by n and k (n > 256: refine, else k <= 16: 5, else 0)
     double us_per_iter = 0;  // measured by the tuner (0: not tuned)
 };
 

@@ -751,7 +751,7 @@ def measure_batch(args, K, Wm, local):
     sb.set_min_secant_length(eps)
     for b in range(B):
         sb.set_basis(b, Us[b])
-    sb.autotune(alpha, 4)
+    tuning = sb.autotune(alpha, 4)  # one set for all datasets, timed on whole batch iterations
     for b in range(B):
         sb.set_basis(b, Us[b])
     sb.run(alpha, Wm, history=False)
@@ -772,7 +772,7 @@ def measure_batch(args, K, Wm, local):
     alg = 2 * (Ptot - st1["n_excluded"] - st1["n_near"])  # BF16 w per stored pair
     line = _common(args, cfg["workload"], it_s, "batch iterations/s", ms / its, its, Wm, "f32",
                    {"datasets": B, "N_min": min(Ns), "N_max": max(Ns), "n": n, "k": k, "alpha": alpha,
-                    "eps": eps, "input": "BF16 data, FP32 arithmetic",
+                    "eps": eps, "input": "BF16 data, FP32 arithmetic", "tuning": tuning,
                     "l2": "inputs larger than L2: %.2f GB of stored lengths streamed every iteration" % (2 * Ptot / 1e9)})
     line.update({
         "sap_iterations_per_s": it_s * B,

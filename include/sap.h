@@ -406,8 +406,10 @@ typedef struct {
  * when their handle reaches a new shape that has a cached choice
  * (parameters set by hand stay until the shape changes); if the environment
  * variable SAP_TUNE_CACHE names a file, choices are appended to it and read back by
- * later processes.  1 <= iters <= 4096.  On a batch handle every dataset is
- * tuned.  out (nullable) receives the chosen set.  Synchronises.
+ * later processes.  1 <= iters <= 4096.  On a batch handle one set is chosen
+ * for all datasets together by timing whole batch iterations (the datasets
+ * run concurrently), and it is not cached.  out (nullable) receives the
+ * chosen set.  Synchronises.
  */
 sap_status sap_autotune(sap_handle h, double alpha, int32_t iters, sap_tuning *out);
 

@@ -769,8 +769,9 @@ class SapBatch:
         sap_set_min_secant_length(self.h, eps)
 
     def autotune(self, alpha, iters=4):
-        """Tune every dataset (each against its own shape)."""
-        _check(self.h, load_library().sap_autotune(self.h, alpha, iters, None))
+        """One launch-parameter set for all datasets, timed on whole batch
+        iterations; returns it."""
+        return sap_autotune(self.h, alpha, iters)
 
     def tuning(self):
         """The first dataset's launch parameters (sap_get_tuning)."""

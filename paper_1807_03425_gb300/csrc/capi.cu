@@ -851,15 +851,106 @@ sap_status sap_set_tuning(sap_handle h, const sap_tuning *in)
     return tune_apply(h, p);
 }
 
+// Batch handles: one parameter set for every dataset, chosen by timing whole
+// batch iterations (the datasets run concurrently, so what matters is the
+// batch's time, not each dataset's alone): coordinate descent over the same
+// parameters as the single-handle tuner, from the first dataset's current
+// set.  The bases are restored afterwards (iteration counters restart).
+static sap_status tune_batch(sap_handle h, double alpha, int iters)
+{
+    const size_t B = h->kids.size();
+    std::vector<std::vector<double>> U(B);
+    for (size_t b = 0; b < B; ++b) {
+        sap_handle kid = h->kids[b];
+        if (kid->k == 0) return fail(h, SAP_E_STATE, "dataset " + std::to_string(b) + " has no basis");
+        U[b].resize((size_t)kid->n * kid->k);
+        sap_status st = sap_get_basis_b(h, (int32_t)b, U[b].data(), 0);
+        if (st != SAP_OK) return st;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(h, SAP_E_CUDA, "autotune: event creation failed");
+    }
+    for (sap_handle kid : h->kids) kid->tuning = true;
+    sap_status st = SAP_OK;
+    auto restore = [&]() -> sap_status {
+        for (size_t b = 0; b < B; ++b) {
+            sap_status r = sap_set_basis_b(h, (int32_t)b, U[b].data(), h->kids[b]->k, 0);
+            if (r != SAP_OK) return r;
+        }
+        return SAP_OK;
+    };
+    auto timed = [&](const TuneParams &c, double *us) -> sap_status {
+        for (sap_handle kid : h->kids) {
+            sap_status r = tune_apply(kid, c);
+            if (r != SAP_OK) return fail(h, r, kid->err);
+        }
+        double best = INFINITY;
+        for (int rep = 0; rep < 3; ++rep) {
+            sap_status r = restore();
+            if (r != SAP_OK) return r;
+            if (rep > 0 && cudaEventRecord(e0, h->stream) != cudaSuccess) return fail(h, SAP_E_CUDA, "event");
+            r = sap_run_batch(h, alpha, iters, nullptr, nullptr);
+            if (r != SAP_OK) return r;
+            if (rep > 0) {
+                if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                    return fail(h, SAP_E_CUDA, "event");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best = std::fmin(best, 1e3 * ms / iters);
+            }
+        }
+        *us = best;
+        return SAP_OK;
+    };
+    TuneParams best = h->kids[0]->tune;
+    double best_us = INFINITY;
+    st = timed(best, &best_us);
+    auto consider = [&](TuneParams c) {
+        if (st != SAP_OK || tune_same_launch(c, best)) return;
+        double us = INFINITY;
+        st = timed(c, &us);
+        if (st == SAP_OK && us < best_us) {
+            best = c;
+            best_us = us;
+        }
+    };
+    if (handle_path_restructured(h->kids[0])) {
+        for (int rf : {0, 1, 5, 2, 3, 4}) { TuneParams c = best; c.refine = rf; consider(c); }
+        for (int pdl : {0, 1}) { TuneParams c = best; c.pdl = pdl; consider(c); }
+        for (double b : {5e-4, 1e-3, 2e-3, 4e-3, 8e-3}) { TuneParams c = best; c.b_cap = b; consider(c); }
+        for (int stg : {0, 2, 3}) { TuneParams c = best; c.pass_stages = stg; consider(c); }
+        for (int e : {1, 2, 4}) { TuneParams c = best; c.expl_per_sm = e; consider(c); }
+    } else {
+        for (int p : {1, 2, 4}) { TuneParams c = best; c.plain_per_sm = p; consider(c); }
+    }
+    for (int sb : {38, 76, 152}) { TuneParams c = best; c.su_blocks = sb; consider(c); }
+    if (st == SAP_OK) {
+        best.us_per_iter = best_us;
+        for (sap_handle kid : h->kids) {
+            sap_status r = tune_apply(kid, best);
+            if (r != SAP_OK && st == SAP_OK) st = fail(h, r, kid->err);
+        }
+    }
+    const sap_status rs = restore();
+    if (st == SAP_OK) st = rs;
+    for (sap_handle kid : h->kids) kid->tuning = false;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
 sap_status sap_autotune(sap_handle h, double alpha, int32_t iters, sap_tuning *out)
 {
     CHECK_HANDLE(h);
     NOT_SHARD(h);
     if (h->is_batch) {
-        for (size_t b = 0; b < h->kids.size(); ++b) {
-            sap_status st = sap_autotune(h->kids[b], alpha, iters, nullptr);
-            if (st != SAP_OK) return fail(h, st, "dataset " + std::to_string(b) + ": " + h->kids[b]->err);
-        }
+        if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(h, SAP_E_ARG, "alpha must be in [0, 1]");
+        if (iters < 1 || iters > 4096) return fail(h, SAP_E_ARG, "iters must be in [1, 4096]");
+        sap_status st = tune_batch(h, alpha, iters);
+        if (st != SAP_OK) return st;
+        if (out) to_public(h->kids[0]->tune, out);
         return SAP_OK;
     }
     if (h->k == 0) return fail(h, SAP_E_STATE, "no basis set");

@@ -100,6 +100,8 @@ bool same_launch(const TuneParams &a, const TuneParams &b)
 
 } // namespace
 
+bool tune_same_launch(const TuneParams &a, const TuneParams &b) { return same_launch(a, b); }
+
 sap_status tune_apply(sap_handle h, const TuneParams &p)
 {
     handle_applied_key(h) = handle_tune_key(h);

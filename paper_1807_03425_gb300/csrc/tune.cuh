@@ -28,6 +28,8 @@ bool &handle_tuning_flag(sap_handle h);
 TuneKey &handle_applied_key(sap_handle h);
 void handle_drop_graphs(sap_handle h);
 
+// Whether two parameter sets launch the same kernels the same way.
+bool tune_same_launch(const TuneParams &a, const TuneParams &b);
 // Apply a parameter set to the handle (re-classifies the near list when the
 // pass bound changes; drops captured graphs when anything changes).
 sap_status tune_apply(sap_handle h, const TuneParams &p);

@@ -119,7 +119,9 @@ def test_batch_autotune_keeps_results(P):
             for b in range(3):
                 sb.set_basis(b, Us[b])
             if tune:
-                sb.autotune(0.01, 4)
+                chosen = sb.autotune(0.01, 4)
+                # one set for every dataset, timed on whole batch iterations
+                assert chosen["us_per_iteration"] > 0 and sb.tuning() == chosen
                 for b in range(3):
                     sb.set_basis(b, Us[b])
             out.append(sb.run(0.01, 12))

@@ -370,7 +370,8 @@ struct DeferredPair {
     int i, j;
     float r;
 };
-constexpr int kDefer = 32;  // deferred survivors per consumer warp
+constexpr int kDefer = 32;     // deferred survivors per consumer warp
+constexpr int kDrainTile = 6;  // tiles before the first check of the deferred survivors
 // dynamic shared memory of the pass: the 227 KB a block may hold, less the
 // static part (barriers, tile coordinates, the deferred survivors)
 constexpr int kPassDynSmem = 216 * 1024;
@@ -633,6 +634,19 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
             }
         }
     };
+    // the deferred survivors against the bound as it is now
+    auto drain = [&]() {
+        if constexpr (EXPL) {
+            __syncwarp();
+            const float U2 = fminf(fminf(seed, uwarp), load_pos_float(&a.st->run_ub2));
+            const float th = cert_emit_threshold(U2, a.cert32);
+            for (int q = 0; q < nd; ++q) {
+                const DeferredPair d = defer[warp][q];
+                if (d.r <= th) fp64_pair(make_int2(d.i, d.j));  // r < 0: too short for FP32
+            }
+            nd = 0;
+        }
+    };
     auto expl_round = [&](const int2 (&pr)[EX], const bool (&valid)[EX]) {
         if constexpr (EXPL) {
             float rr;
@@ -659,7 +673,15 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     // ring position and barrier phase, advanced without integer division
     int s = 0;
     uint32_t phase = 0;
+    int tcount = 0;  // tiles this warp has consumed
     for (;; s = (s + 1 == S) ? 0 : s + 1, phase ^= (s == 0) ? 1u : 0u) {
+        // a checkpoint part-way: the survivors so far against the bound as it
+        // is by then (tight once the minimum's tile has been seen), so their
+        // FP64 evaluations overlap the other warps' tiles instead of the tail
+        if constexpr (EXPL) {
+            if (tcount == kDrainTile && nd) drain();
+            ++tcount;
+        }
         if (!tc::mbar_wait_bounded(&full[s], phase, budget)) {
             if (lane == 0) atomicOr(&a.st->status, ST_TIMEOUT);
             break;
@@ -867,14 +889,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
         }
     }
     if constexpr (EXPL) {
-        // the deferred survivors against the bound as it is now
-        __syncwarp();
-        const float U2 = fminf(fminf(seed, uwarp), load_pos_float(&a.st->run_ub2));
-        const float th = cert_emit_threshold(U2, a.cert32);
-        for (int q = 0; q < nd; ++q) {
-            const DeferredPair d = defer[warp][q];
-            if (d.r <= th) fp64_pair(make_int2(d.i, d.j));  // r < 0: too short for FP32
-        }
+        drain();
         // the block's best pair: the last consumer warp to finish merges
         if (lane == 0) {
             pbest[warp] = best;

@@ -926,6 +926,10 @@ static sap_status tune_batch(sap_handle h, double alpha, int iters)
         for (int p : {1, 2, 4}) { TuneParams c = best; c.plain_per_sm = p; consider(c); }
     }
     for (int sb : {38, 76, 152}) { TuneParams c = best; c.su_blocks = sb; consider(c); }
+    if (handle_path_restructured(h->kids[0])) {  // a second look (see tune_handle)
+        for (int pdl : {0, 1}) { TuneParams c = best; c.pdl = pdl; consider(c); }
+        for (int stg : {0, 2, 3}) { TuneParams c = best; c.pass_stages = stg; consider(c); }
+    }
     if (st == SAP_OK) {
         best.us_per_iter = best_us;
         for (sap_handle kid : h->kids) {

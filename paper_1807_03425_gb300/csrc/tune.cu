@@ -227,6 +227,20 @@ sap_status tune_handle(sap_handle h, double alpha, int iters)
         c.su_blocks = sb;
         consider(c);
     }
+    if (restr) {
+        // a second look at the parameters that interact with those chosen
+        // after them (programmatic launch with the ring depth)
+        for (int pdl : {0, 1}) {
+            TuneParams c = best;
+            c.pdl = pdl;
+            consider(c);
+        }
+        for (int stg : {0, 2, 3}) {
+            TuneParams c = best;
+            c.pass_stages = stg;
+            consider(c);
+        }
+    }
     if (st == SAP_OK) {
         best.us_per_iter = best_us;
         st = tune_apply(h, best);

@@ -418,8 +418,9 @@ __device__ __forceinline__ void expl32_step(float (&acc)[E * (K + 1)], const flo
     float u[KU];
 #pragma unroll
     for (int c = 0; c < KU; c += 4) {
-        // L2 only: the pass leaves little L1 beside its shared memory
-        // (read-only loads through the L1 measured 0.6-0.9 us slower)
+        // L2 only, like the point rows below: the pass leaves little L1
+        // beside its shared memory (read-only loads through the L1 measured
+        // 0.6-0.9 us slower per iteration)
         const float4 t = __ldcg(reinterpret_cast<const float4 *>(U32 + (size_t)l * KP + c));
         u[c] = t.x; u[c + 1] = t.y; u[c + 2] = t.z; u[c + 3] = t.w;
     }
@@ -442,7 +443,7 @@ __device__ __forceinline__ void expl32_eval(const float *X, int n, const float *
     for (int l = lane; l < n; l += 32) {
         float D[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) D[e] = X[(size_t)pr[e].x * n + l] - X[(size_t)pr[e].y * n + l];
+        for (int e = 0; e < E; ++e) D[e] = __ldcg(X + (size_t)pr[e].x * n + l) - __ldcg(X + (size_t)pr[e].y * n + l);
         expl32_step<K, E>(acc, U32, KP, l, D);
     }
     expl32_finish<K, E>(acc, valid, lane, rr, code);

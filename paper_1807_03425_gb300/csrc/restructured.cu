@@ -781,17 +781,19 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 mymin = fminf(mymin, v[r][0]);
             }
         }
-        const float wmin = warp_min(mymin);
         float U = fminf(fminf(seed, gnow), uwarp);
-        const bool refine = wmin < INFINITY && sqrtf(wmin) < U;  // warp-uniform
         float thc = cert_emit_threshold(U, a.cert);
         float thc2 = thc * thc * 1.000001f;
-        if (!refine && !__any_sync(0xffffffffu, mymin <= thc2)) {
+        // thc >= U, so a tile that could tighten the bound (minimum below
+        // U^2) also fails this test: the fast path needs no warp minimum
+        if (!__any_sync(0xffffffffu, mymin <= thc2)) {
             // fast path: nothing in this tile can bound or be the minimum
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&empty[s]);
             continue;
         }
+        const float wmin = warp_min(mymin);
+        const bool refine = wmin < INFINITY && sqrtf(wmin) < U;  // warp-uniform
         const float *nuI = reinterpret_cast<const float *>(sm + (size_t)s * sbytes + wbytes + ibytes + jbytes);
         const float *nuJ = nuI + T;
         if (refine) {

@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libsap.so")
+# SAP_LIBRARY selects another build of the library (e.g. the debug build
+# libsap_dbg.so, see build.py)
+_LIB_PATH = os.environ.get("SAP_LIBRARY") or os.path.join(_HERE, "libsap.so")
 _lib = None
 
 F32, BF16, F64 = 0, 1, 2

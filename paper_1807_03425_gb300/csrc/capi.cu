@@ -211,6 +211,7 @@ sap_status sync_and_status(sap_handle h)
     CK(cudaMemcpy(&status, &h->st->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (status) {
         CK(cudaMemset(&h->st->status, 0, sizeof(int)));
+        if (status & ST_BOUNDS) return fail(h, SAP_E_BOUNDS, "a device index was out of range (debug build)");
         if (status & ST_NO_SECANT) return fail(h, SAP_E_NO_SECANT, "every pair is excluded");
         if (status & ST_TIMEOUT) return fail(h, SAP_E_TIMEOUT, "a device-side wait gave up");
         if (status & ST_OVERFLOW)
@@ -458,6 +459,7 @@ sap_status handle_check_status(sap_handle h, ProbState *st)
     CK(cudaMemcpy(&status, &st->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (status) {
         CK(cudaMemset(&st->status, 0, sizeof(int)));
+        if (status & ST_BOUNDS) return fail(h, SAP_E_BOUNDS, "a device index was out of range (debug build)");
         if (status & ST_NO_SECANT) return fail(h, SAP_E_NO_SECANT, "every pair is excluded");
         if (status & ST_TIMEOUT) return fail(h, SAP_E_TIMEOUT, "a device-side wait gave up");
         if (status & ST_OVERFLOW) return fail(h, SAP_E_UNSUPPORTED, "candidate list overflow (too many near-ties)");
@@ -534,6 +536,7 @@ const char *sap_status_str(sap_status s)
     case SAP_E_TIMEOUT: return "SAP_E_TIMEOUT";
     case SAP_E_NO_DEVICE: return "SAP_E_NO_DEVICE";
     case SAP_E_UNSUPPORTED: return "SAP_E_UNSUPPORTED";
+    case SAP_E_BOUNDS: return "SAP_E_BOUNDS";
     }
     return "SAP_E_UNKNOWN";
 }

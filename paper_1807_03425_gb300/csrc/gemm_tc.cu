@@ -72,6 +72,7 @@ __device__ float product_seeds(const GemmArgs &a, int q0, int step, int lane)
     float best = INFINITY;
     for (int q = q0; q < nw; q += step) {
         const int2 pr = st->watch[q];
+        if (!SAP_PAIR_OK(a.seed_st, pr, a.seed_N)) continue;
         const float *xi = a.seed_X + (size_t)pr.x * n, *xj = a.seed_X + (size_t)pr.y * n;
         float dd = 0.f, zz = 0.f;
         // components c0 .. c0 + 7, and (first chunk) |x_i - x_j|^2 in slot 8

@@ -36,7 +36,7 @@ struct GemmArgs {
     const float *seed_U = nullptr;   // the basis, FP32 n x KP row-major ...
     const float *seed_Ulo = nullptr; // ... and its FP32 residual
     ProbState *seed_st = nullptr;
-    int seed_n = 0, seed_k = 0, seed_KP = 0;
+    int seed_N = 0, seed_n = 0, seed_k = 0, seed_KP = 0;
 };
 
 size_t gemm_smem_bytes(int KPG, int stages);

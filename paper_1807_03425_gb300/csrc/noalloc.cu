@@ -213,6 +213,7 @@ extern "C" sap_status sap_min_secant_noalloc(const float *X, int64_t N, int32_t 
     ProbState st;
     if (cudaMemcpyAsync(&st, &g->st, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SAP_E_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SAP_E_CUDA;
+    if (st.status & ST_BOUNDS) return SAP_E_BOUNDS;
     if (st.status & ST_NO_SECANT) return SAP_E_NO_SECANT;
     if (st.status & ST_TIMEOUT) return SAP_E_TIMEOUT;
     if (st.status & ST_OVERFLOW) return SAP_E_UNSUPPORTED;

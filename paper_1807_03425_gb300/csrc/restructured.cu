@@ -293,7 +293,7 @@ struct PassArgs {
     // update.  No list is written; st->cnt1 counts the emitted pairs,
     // st->cnt2 the FP64 evaluations.
     const float *X = nullptr;  // N x n FP32 points
-    int n = 0;
+    int N = 0, n = 0;
     const float *U32 = nullptr;  // n x KP FP32 basis (pad columns zero)
     int KP = 0;
     const double *U64 = nullptr;  // n x k FP64 basis, column-major
@@ -495,7 +495,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
             const int pre = nstatic;
             for (int it = 0; it < pre; ++it) {
                 const int t = blockIdx.x + it * gridDim.x;
-                const int2 IJ = a.wtiles[t];
+                int2 IJ = a.wtiles[t];
+                if (!SAP_BOUNDS_OK(a.st, IJ.x >= 0 && IJ.x <= IJ.y && IJ.y < a.Npad / T)) IJ = make_int2(0, 0);
                 sIJ[it] = IJ;  // published by the mbarrier completion
                 unsigned char *base = sm + (size_t)it * sbytes;
                 tc::mbar_expect_tx(&full[it], sbytes);
@@ -525,6 +526,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
             };
             int tnext = next_tile(pre);
             int2 IJnext = tnext < a.ntiles ? a.wtiles[tnext] : make_int2(-1, -1);
+            if (tnext < a.ntiles && !SAP_BOUNDS_OK(a.st, IJnext.x >= 0 && IJnext.x <= IJnext.y && IJnext.y < a.Npad / T))
+                IJnext = make_int2(0, 0);
             for (int it = pre;; ++it) {
                 const int s = it % S;
                 const int t = tnext;
@@ -532,6 +535,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
                 if (t < a.ntiles) {
                     tnext = next_tile(it + 1);
                     IJnext = tnext < a.ntiles ? a.wtiles[tnext] : make_int2(-1, -1);
+                    if (tnext < a.ntiles &&
+                        !SAP_BOUNDS_OK(a.st, IJnext.x >= 0 && IJnext.x <= IJnext.y && IJnext.y < a.Npad / T))
+                        IJnext = make_int2(0, 0);
                 }
                 if (it >= S && !tc::mbar_wait_bounded(&empty[s], ((it / S) - 1) & 1, budget)) {
                     atomicOr(&a.st->status, ST_TIMEOUT);
@@ -582,6 +588,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
     int nd = 0;  // deferred survivors of this warp (warp-uniform)
     auto fp64_pair = [&](int2 ij) {
         if constexpr (EXPL) {
+            if (!SAP_PAIR_OK(a.st, ij, a.N)) return;
             if (lane == 0) atomicAdd((unsigned int *)&a.st->cnt2, 1u);
             // FP64: |D|^2 and U^T D with D = x_i - x_j (the FP64 recheck's sums)
             // (the FP64 recheck's compute width for this k, so its sums
@@ -669,6 +676,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) restr_pass_kernel(PassArgs a)
             for (int e = 0; e < EX; ++e) {
                 valid[e] = base + e < a.n_near;
                 pr[e] = valid[e] ? __ldcg(a.near + base + e) : make_int2(0, 0);
+                if (valid[e] && !SAP_PAIR_OK(a.st, pr[e], a.N)) {
+                    valid[e] = false;
+                    pr[e] = make_int2(0, 0);
+                }
             }
             expl_round(pr, valid);
         }
@@ -980,7 +991,7 @@ __global__ void __launch_bounds__(256) explicit_recheck_kernel(ExplArgs a)
         if (base >= total) break;  // uniform over the block
 #pragma unroll
         for (int e = 0; e < EPW; ++e) {
-            valid[e] = base + warp * EPW + e < total;
+            valid[e] = base + warp * EPW + e < total && SAP_PAIR_OK(a.st, pr[e], a.N);
             if (!valid[e]) pr[e] = make_int2(0, 0);
         }
         // any earlier value of the running bound is a valid (looser) bound:
@@ -1103,6 +1114,10 @@ __global__ void __launch_bounds__(256) explicit_df_kernel(ExplArgs a)
             const long long idx = base + e;
             valid[e] = idx < total;
             pr[e] = valid[e] ? (idx < nn ? __ldcg(a.near + idx) : __ldcg(a.cand1 + (idx - nn))) : make_int2(0, 0);
+            if (valid[e] && !SAP_PAIR_OK(a.st, pr[e], a.N)) {
+                valid[e] = false;
+                pr[e] = make_int2(0, 0);
+            }
         }
         // any earlier value of the running bound is a valid (looser) bound
         const float ub2 = load_pos_float(&a.st->run_ub2);
@@ -1348,6 +1363,7 @@ struct RefineArgs {
     const float *w;          // stored 1/d^2, tile-major upper triangle
     int nb;                  // point blocks per side (Npad / 128)
     long long tile0;         // global index of the first stored tile
+    long long nwt;           // stored tiles (index checks of the debug build)
     const float *xn;         // ||x_i||, rounded up
     float beta;              // sqrt(k) (eps_df + 2^-46), rounded up
     const int2 *cand1;
@@ -1393,17 +1409,22 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs a)
             int2 pr = make_int2(0, 0);
             float r = INFINITY, bnd = 0.f;
             if (idx < total) {
-                float wv;
+                float wv = INFINITY;
+                bool ok;
                 if (idx < nn) {
                     pr = __ldcg(a.near + idx);
+                    ok = SAP_BOUNDS_OK(a.st, pr.x >= 0 && pr.x < pr.y && pr.y < a.Npad);
                     wv = __ldcg(a.near_w + idx);
                 } else {
                     pr = __ldcg(a.cand1 + (idx - nn));
                     const int I = pr.x >> 7, J = pr.y >> 7;
                     const long long t = (long long)I * a.nb - (long long)I * (I - 1) / 2 + (J - I) - a.tile0;
-                    wv = __ldg(a.w + t * (T * T) + (pr.x & (T - 1)) * T + (pr.y & (T - 1)));
+                    ok = SAP_BOUNDS_OK(a.st, pr.x >= 0 && pr.x < pr.y && pr.y < a.Npad && t >= 0 && t < a.nwt);
+                    if (ok) wv = __ldg(a.w + t * (T * T) + (pr.x & (T - 1)) * T + (pr.y & (T - 1)));
                 }
-                if (!(wv < INFINITY)) {
+                if (!ok) {
+                    pr = make_int2(0, 0);  // skipped (code 0)
+                } else if (!(wv < INFINITY)) {
                     code = 2;
                 } else {
                     float zz = 0.f;
@@ -1868,6 +1889,7 @@ sap_status restructured_enqueue_product(sap_handle h, const CUtensorMap *mhi, co
         g.seed_U = handle_u32(h);
         g.seed_Ulo = handle_u32lo(h);
         g.seed_st = st;
+        g.seed_N = (int)handle_n_points(h);
         g.seed_n = handle_n_dim(h);
         g.seed_k = handle_k(h);
         g.seed_KP = handle_kp(h);
@@ -1917,6 +1939,7 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         p.pdl = handle_tune(h).pdl;
         if (tier == 5) {
             p.X = handle_x32(h);
+            p.N = (int)handle_n_points(h);
             p.n = n;
             p.U32 = b.U32;
             p.KP = b.KP;
@@ -1982,6 +2005,7 @@ sap_status restructured_enqueue_basis(sap_handle h, const BasisView &b, cudaStre
         x.w = r.w;
         x.nb = r.Npad / T;
         x.tile0 = r.tile0;
+        x.nwt = r.nwtiles;
         x.xn = r.xn;
         x.beta = (float)(std::sqrt((double)b.k) * (df_error_unit(n) + std::ldexp(1.0, -46)) * 1.02);
         x.cand1 = b.cand1;

@@ -79,7 +79,25 @@ enum StatusBits : int {
     ST_NO_SECANT = 1,
     ST_TIMEOUT = 2,
     ST_OVERFLOW = 4,
+    ST_BOUNDS = 8,  // debug build: a data-dependent index was out of range (the access was skipped)
 };
+
+// Debug build (compiled with SAP_DEBUG_BOUNDS): every index a kernel reads
+// from data -- a pair from a list, a tile's block coordinates, the argmin --
+// is checked before it addresses memory; an index out of range sets
+// ST_BOUNDS in the problem's status word (reported as SAP_E_BOUNDS) and the
+// access is skipped, so nothing traps.  Otherwise the check is `true`.
+#ifdef SAP_DEBUG_BOUNDS
+__device__ __forceinline__ bool sap_bounds_ok(int *status, bool cond)
+{
+    if (!cond) atomicOr(status, (int)ST_BOUNDS);
+    return cond;
+}
+#define SAP_BOUNDS_OK(st, cond) sap_bounds_ok(&(st)->status, (cond))
+#else
+#define SAP_BOUNDS_OK(st, cond) true
+#endif
+#define SAP_PAIR_OK(st, ij, N) SAP_BOUNDS_OK(st, (ij).x >= 0 && (ij).x < (N) && (ij).y >= 0 && (ij).y < (N))
 
 // Launch parameters of one handle, chosen by the autotuner (tune.cu) or set
 // explicitly.  Results never depend on them: every choice evaluates the same

@@ -144,6 +144,7 @@ struct Shared {
 template <typename TX, int K>
 __device__ __forceinline__ void fp64_eval(const SelectUpdateArgs &a, int2 ij, int lane, Partial &best)
 {
+    if (!SAP_PAIR_OK(a.st, ij, a.N)) return;
     const int n = a.n, kk = a.k;
     double v[K + 1];
 #pragma unroll
@@ -939,11 +940,12 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
                 for (int h = 0; h < 2; ++h) {
                     const int q = (w - kQW) + h * (NW - kQW);
                     const int2 pr = sh.watch[q < nw ? q : 0];
+                    const bool okq = q < nw && SAP_PAIR_OK(st, pr, a.N);
 #pragma unroll
                     for (int r = 0; r < kQW; ++r) {
                         const int l = lane + 32 * r;
-                        wxi[h][r] = (q < nw && l < n) ? (float)ld_x<TX>(a.X, (size_t)pr.x * n + l) : 0.f;
-                        wxj[h][r] = (q < nw && l < n) ? (float)ld_x<TX>(a.X, (size_t)pr.y * n + l) : 0.f;
+                        wxi[h][r] = (okq && l < n) ? (float)ld_x<TX>(a.X, (size_t)pr.x * n + l) : 0.f;
+                        wxj[h][r] = (okq && l < n) ? (float)ld_x<TX>(a.X, (size_t)pr.y * n + l) : 0.f;
                     }
                 }
             }
@@ -976,7 +978,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int q = h == 0 ? q0 : q1;
-                    if (q >= nwatch) continue;  // uniform over the warp
+                    if (q >= nwatch || !SAP_PAIR_OK(st, sh.watch[q], a.N)) continue;  // uniform over the warp
                     const int2 pr = sh.watch[q];
                     double v[K + 1];
 #pragma unroll
@@ -1020,7 +1022,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
     const int nwatch = sh.watch_n;
     const bool prefetch = n <= 32 * kSeedRegs;
     float wxi[kSeedRegs], wxj[kSeedRegs];
-    if (prefetch && w < nwatch && !a.seeds_in_product) {
+    if (prefetch && w < nwatch && !a.seeds_in_product && SAP_PAIR_OK(st, sh.watch[w], a.N)) {
         const int2 pr = sh.watch[w];
 #pragma unroll
         for (int q = 0; q < kSeedRegs; ++q) {
@@ -1243,7 +1245,7 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
     }
 
     // seeds: the recent argmin pairs under the new basis
-    if (w < nwatch) {
+    if (w < nwatch && SAP_PAIR_OK(st, sh.watch[w], a.N)) {
         const int2 pr = sh.watch[w];
         float seed = INFINITY;
         if (sizeof(TX) == 8) {

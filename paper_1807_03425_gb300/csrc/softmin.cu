@@ -1256,6 +1256,7 @@ sap_status read_dev(sap_handle h, SoftDev *out)
         const int st = out->status;
         SCK(cudaMemsetAsync(&ss.dev->status, 0, sizeof(int), s));
         SCK(cudaStreamSynchronize(s));
+        if (st & ST_BOUNDS) return handle_fail(h, SAP_E_BOUNDS, "a device index was out of range (debug build)");
         if (st & ST_NO_SECANT) return handle_fail(h, SAP_E_NO_SECANT, "every pair is excluded");
         if (st & ST_TIMEOUT) return handle_fail(h, SAP_E_TIMEOUT, "a device-side wait gave up");
         return handle_fail(h, SAP_E_CUDA, "soft-min kernel status");

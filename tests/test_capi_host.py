@@ -41,6 +41,7 @@ def test_status_strings(lib):
     assert capi.sap_status_str(0) == "SAP_OK"
     assert capi.sap_status_str(4) == "SAP_E_NO_SECANT"
     assert capi.sap_status_str(9) == "SAP_E_UNSUPPORTED"
+    assert capi.sap_status_str(10) == "SAP_E_BOUNDS"
     assert "sm_103a" in capi.sap_version()
 
 

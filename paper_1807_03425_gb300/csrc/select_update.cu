@@ -211,10 +211,16 @@ __device__ __forceinline__ void chol_inverse(Shared<TX, K> &sh, int kk, int lane
     constexpr int KS = Shared<TX, K>::KS;
     const double lim = KS == K ? 1e-5 : 1e-6;
     bool small = true;
-    if (KS == K) {  // k = K: compile-time index arithmetic
-        for (int e = lane; e < K * K; e += 32) {
+    // k = K: compile-time bounds, loops unrolled with predicated iterations
+    // (straight-line code: it runs once per launch, so its instruction
+    // fetch is part of the critical path)
+    constexpr int NREP = (K * K + 31) / 32;
+    if (KS == K) {
+#pragma unroll
+        for (int rep = 0; rep < NREP; ++rep) {
+            const int e = lane + 32 * rep;
             const int p = e / K, q = e % K;
-            if (q >= p && fabs(sh.G[p][q] - (p == q ? 1.0 : 0.0)) > lim) small = false;
+            if (e < K * K && q >= p && fabs(sh.G[p % K][q % K] - (p == q ? 1.0 : 0.0)) > lim) small = false;
         }
     } else {
         for (int e = lane; e < kk * kk; e += 32) {
@@ -232,43 +238,63 @@ __device__ __forceinline__ void chol_inverse(Shared<TX, K> &sh, int kk, int lane
         // most k^2 1e-10: its FP32 evaluation from FP32(R1) errs by ~1e-17,
         // below FP64 rounding of the unit diagonal, and the truncation by
         // ~1e-20; each lane forms its entries independently.
-        for (int e = lane; e < K * K; e += 32) {
-            const int p = e / K, q = e % K;
-            const double v = q > p ? sh.G[p][q] : (q == p ? 0.5 * (sh.G[p][p] - 1.0) : 0.0);
-            sh.T1[p][q] = v;
-            sh.S1f[p % KS][q % KS] = (float)v;
+#pragma unroll
+        for (int rep = 0; rep < NREP; ++rep) {
+            const int e = lane + 32 * rep;
+            const int p = (e / K) % K, q = e % K;
+            if (e < K * K) {
+                const double v = q > p ? sh.G[p][q] : (q == p ? 0.5 * (sh.G[p][p] - 1.0) : 0.0);
+                sh.T1[p][q] = v;
+                sh.S1f[p % KS][q % KS] = (float)v;
+            }
         }
         __syncwarp();
-        for (int e = lane; e < K * K; e += 32) {
-            const int p = e / K, q = e % K;
-            float tt = 0.f, sq = 0.f;
-            if (q >= p) {
-                for (int m = 0; m <= p; ++m) tt = fmaf(sh.S1f[m % KS][p % KS], sh.S1f[m % KS][q % KS], tt);  // (R1^T R1)_pq
-                for (int m = p; m <= q; ++m) sq = fmaf(sh.S1f[p % KS][m % KS], sh.S1f[m % KS][q % KS], sq);  // (R1^2)_pq
+#pragma unroll
+        for (int rep = 0; rep < NREP; ++rep) {
+            const int e = lane + 32 * rep;
+            const int p = (e / K) % K, q = e % K;
+            if (e < K * K) {
+                float tt = 0.f, sq = 0.f;
+                if (q >= p) {
+#pragma unroll
+                    for (int m = 0; m < K; ++m)
+                        if (m <= p) tt = fmaf(sh.S1f[m % KS][p % KS], sh.S1f[m % KS][q % KS], tt);  // (R1^T R1)_pq
+#pragma unroll
+                    for (int m = 0; m < K; ++m)
+                        if (m >= p && m <= q) sq = fmaf(sh.S1f[p % KS][m % KS], sh.S1f[m % KS][q % KS], sq);  // (R1^2)_pq
+                }
+                sh.R2f[p % KS][q % KS] = q > p ? -tt : (q == p ? -0.5f * tt : 0.f);
+                sh.Sqf[p % KS][q % KS] = q >= p ? sq : 0.f;
             }
-            sh.R2f[p % KS][q % KS] = q > p ? -tt : (q == p ? -0.5f * tt : 0.f);
-            sh.Sqf[p % KS][q % KS] = q >= p ? sq : 0.f;
         }
         __syncwarp();
-        for (int e = lane; e < K * K; e += 32) {
-            const int p = e / K, q = e % K;
-            if (q < p) {
-                sh.Ri[p][q] = 0.0;
-                continue;
+#pragma unroll
+        for (int rep = 0; rep < NREP; ++rep) {
+            const int e = lane + 32 * rep;
+            const int p = (e / K) % K, q = e % K;
+            if (e < K * K) {
+                if (q < p) {
+                    sh.Ri[p][q] = 0.0;
+                } else {
+                    float m3 = 0.f, r12 = 0.f, r21 = 0.f, r13 = 0.f;
+#pragma unroll
+                    for (int m = 0; m < K; ++m)
+                        if (m <= p) {
+                            m3 = fmaf(sh.S1f[m % KS][p % KS], sh.R2f[m % KS][q % KS], m3);
+                            m3 = fmaf(sh.R2f[m % KS][p % KS], sh.S1f[m % KS][q % KS], m3);
+                        }
+#pragma unroll
+                    for (int m = 0; m < K; ++m)
+                        if (m >= p && m <= q) {
+                            r12 = fmaf(sh.S1f[p % KS][m % KS], sh.R2f[m % KS][q % KS], r12);  // (R1 R2)_pq
+                            r21 = fmaf(sh.R2f[p % KS][m % KS], sh.S1f[m % KS][q % KS], r21);  // (R2 R1)_pq
+                            r13 = fmaf(sh.Sqf[p % KS][m % KS], sh.S1f[m % KS][q % KS], r13);  // (R1^3)_pq
+                        }
+                    const float r3 = q > p ? -m3 : -0.5f * m3;
+                    const float hi = -sh.R2f[p % KS][q % KS] - r3 + sh.Sqf[p % KS][q % KS] + r12 + r21 - r13;
+                    sh.Ri[p][q] = (p == q ? 1.0 : 0.0) - sh.T1[p][q] + (double)hi;
+                }
             }
-            float m3 = 0.f, r12 = 0.f, r21 = 0.f, r13 = 0.f;
-            for (int m = 0; m <= p; ++m) {
-                m3 = fmaf(sh.S1f[m % KS][p % KS], sh.R2f[m % KS][q % KS], m3);
-                m3 = fmaf(sh.R2f[m % KS][p % KS], sh.S1f[m % KS][q % KS], m3);
-            }
-            for (int m = p; m <= q; ++m) {
-                r12 = fmaf(sh.S1f[p % KS][m % KS], sh.R2f[m % KS][q % KS], r12);  // (R1 R2)_pq
-                r21 = fmaf(sh.R2f[p % KS][m % KS], sh.S1f[m % KS][q % KS], r21);  // (R2 R1)_pq
-                r13 = fmaf(sh.Sqf[p % KS][m % KS], sh.S1f[m % KS][q % KS], r13);  // (R1^3)_pq
-            }
-            const float r3 = q > p ? -m3 : -0.5f * m3;
-            const float hi = -sh.R2f[p % KS][q % KS] - r3 + sh.Sqf[p % KS][q % KS] + r12 + r21 - r13;
-            sh.Ri[p][q] = (p == q ? 1.0 : 0.0) - sh.T1[p][q] + (double)hi;
         }
     } else if (small) {
         // R1 = triu(E) with the diagonal halved; R2 from -R1^T R1 the same

@@ -57,19 +57,18 @@ __device__ __forceinline__ void seed_bar() { asm volatile("bar.sync 2, %0;" ::"n
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
 
-// 1/sqrt(x) in FP64 for x > 0 by Newton's iteration y <- y (3 - x y^2) / 2
-// from the FP32 hardware estimate (relative error ~2^-23): two steps square
-// the error twice, to a few FP64 ulps, in seven dependent FP64 operations
-// instead of a full-precision square root and division.
-__device__ __forceinline__ double rsqrt_f64(double x)
+// An approximate 1/sqrt(x) for x > 0 used as a column scale: the FP32
+// hardware estimate (relative error ~2^-23), widened.  A scale s applied to
+// column 0 of the Gram matrix (G' = S G S, S = diag(s, 1, ...)) and to row 0
+// of the Cholesky factor's inverse gives the same orthonormal basis for any
+// s; it only has to bring G'_00 within the series' 1e-5 of one, and this
+// estimate leaves it within ~5e-7.  (Each dependent FP64 operation costs
+// about 0.12 us here, so Newton steps toward full precision are not taken.)
+__device__ __forceinline__ double rsqrt_scale(double x)
 {
     const float xf = (float)x;
     if (!(xf > 1e-30f && xf < 1e30f)) return 1.0 / sqrt(x);
-    const double hx = -0.5 * x;
-    double y = (double)rsqrtf(xf);
-    y = y * fma(hx * y, y, 1.5);
-    y = y * fma(hx * y, y, 1.5);
-    return y;
+    return (double)rsqrtf(xf);
 }
 
 template <typename TX>
@@ -902,10 +901,9 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
                         if (w == 0 && lane < M) {
                             int p = 0, e = lane;
                             while (e >= KW - p) { e -= KW - p; ++p; }
-                            double sum = 0.0;
-#pragma unroll
-                            for (int q = 0; q < kQW; ++q) sum += sh.gred[q][lane];
-                            sh.G[p][p + e] = sum;
+                            // the four warps' sums as a tree: two dependent FP64 additions
+                            static_assert(kQW == 4, "four update warps");
+                            sh.G[p][p + e] = (sh.gred[0][lane] + sh.gred[1][lane]) + (sh.gred[2][lane] + sh.gred[3][lane]);
                         }
                     } else {
                         // k = 8: the 36 products of the row by warp sums
@@ -926,17 +924,14 @@ __global__ void __launch_bounds__(SB) select_update_kernel(SelectUpdateArgs a)
                             for (int e = lane; e < M; e += 32) {
                                 int p = 0, e2 = e;
                                 while (e2 >= KW - p) { e2 -= KW - p; ++p; }
-                                double sum = 0.0;
-#pragma unroll
-                                for (int q = 0; q < kQW; ++q) sum += sh.gq[q][e];
-                                sh.G[p][p + e2] = sum;
+                                sh.G[p][p + e2] = (sh.gq[0][e] + sh.gq[1][e]) + (sh.gq[2][e] + sh.gq[3][e]);
                             }
                     }
                     if (w == 0) {
                         __syncwarp();
                         const double g00 = sh.G[0][0];
                         if (g00 > 0.0) {
-                            const double inv = rsqrt_f64(g00);
+                            const double inv = rsqrt_scale(g00);
                             if (lane < KW) {
                                 if (lane == 0) sh.G[0][0] = g00 * inv * inv;
                                 else sh.G[0][lane] *= inv;

@@ -49,8 +49,8 @@ CFG_NAME = "c2"
 # DRAM traffic of one restructured-pass launch from the ncu capture of this
 # kernel on this workload, valid only while the pass kernel's source is
 # unchanged (hash below, kernel_source_sha).
-PASS_TRAFFIC_BYTES = 71833344   # 71.120 MB read + 0.713 MB written
-PASS_SOURCE_SHA = "c0df71f3f99de875"
+PASS_TRAFFIC_BYTES = 71932416   # 71.120 MB read + 0.812 MB written
+PASS_SOURCE_SHA = "774558e356117a0b"
 
 
 def kernel_source_sha() -> str:

@@ -202,3 +202,21 @@ def test_tier_forms_agree_bitwise(P, k):
     for other in runs[1:]:
         for a, b in zip(runs[0], other):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tier", [0, 5])
+def test_bf16_data_tiers_lockstep(P, tier):
+    """BF16 data (the hyperspectral workload's input type), n = 224, k = 10:
+    the explicit tier in its own kernel and inside the pass (which reads the
+    exact FP32 widening of the BF16 points) follow the oracle in lock-step
+    on the BF16 values, with ε = 0.05 excluding short secants."""
+    Xs, _ = W.hyperspectral_batch(1, 17, n_min=900, n_max=900)
+    Xb = W.to_bf16_exact(Xs[0])
+    X64 = Xb.astype(np.float64)
+    U = W.random_basis(224, 10, 18)
+    with P.Sap(W.bf16_bits(Xb), dtype=P.BF16) as s:
+        s.set_path("restructured")
+        s.set_min_secant_length(0.05)
+        s.set_tuning(refine_tier=tier)
+        for _ in range(3):
+            U, _ = lockstep(s, X64, U, 0.01, eps=0.05)

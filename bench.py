@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="moment_curve",
                     choices=["moment_curve", "fp64_small", "sweep", "batch", "softmin", "subsample", "pca",
-                             "profile"])
+                             "profile", "profile_scene"])
     return ap.parse_args()
 
 
@@ -1052,6 +1052,33 @@ def run_profile(args):
               flush=True)
 
 
+def run_profile_scene(args):
+    """Like run_profile, for the largest scene of the hyperspectral batch
+    alone (N = 19,939, n = 224 BF16 bands, k = 10, eps = 0.05): the width-10
+    pass class on four columns per thread, with the inner tiers."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_1807_03425_gb300 import BF16, Sap
+    cfg = W.CONFIGS["c4"]
+    Xs, Ns = W.hyperspectral_batch(cfg["B"], cfg["data_seed"])
+    b = int(np.argmax(Ns))
+    steps = args.steps or 6
+    with Sap(W.bf16_bits(Xs[b]), dtype=BF16) as s:
+        s.set_path("restructured")
+        s.set_min_secant_length(cfg["eps"])
+        s.set_tuning(pass_bound=2e-3)
+        s.set_basis(W.random_basis(cfg["n"], cfg["k"], cfg["basis_seed"] + b))
+        for _ in range(steps):
+            s.step(cfg["alpha"])
+        torch.cuda.synchronize()
+        st = s.stats()
+        print(json.dumps({"workload": "hyperspectral scene N=%d n=%d k=%d (BF16)" % (Ns[b], cfg["n"], cfg["k"]),
+                          "profile_steps": steps, "near_pairs": st["n_near"],
+                          "candidates_last_step": {"pass": st["last_tier1"], "fp64": st["last_tier2"]}}),
+              flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference" or args.workload == "moment_curve":
@@ -1066,7 +1093,7 @@ def main():
     else:
         {"fp64_small": run_fp64_small, "sweep": run_sweep, "batch": run_batch,
          "softmin": run_softmin, "subsample": run_subsample, "pca": run_pca,
-         "profile": run_profile}[args.workload](args)
+         "profile": run_profile, "profile_scene": run_profile_scene}[args.workload](args)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.impl != "reference":
         import torch.distributed as tdist
         if tdist.is_initialized():

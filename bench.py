@@ -78,12 +78,24 @@ def parse():
 
 
 def peaks():
+    """(HBM GB/s, max SM MHz, label of the HBM figure's source)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
-    return 6800.0, 2070.0, "fallback"
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, 2070.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+def bf16_peak_sustained():
+    """(sustained dense BF16 TFLOP/s, label of its source)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        if "bf16_tflops_sustained" in d:
+            return float(d["bf16_tflops_sustained"]), "measured bf16_tflops_sustained"
+    return 1700.0, "fallback 1.7 PFLOP/s sustained (no MEASURED_PEAKS.json)"
 
 
 class Clocks:
@@ -311,7 +323,7 @@ def run_sharded(args):
         "final_min_ratio": float(hist[-1]),
         "roofline": {"kernel": "restructured_pass (one rank's band)", "bound": "hbm", "achieved": achieved,
                      "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, per GPU)",
+                     "peak_source": peak_src + ", per GPU",
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": pass_ms},
         "e2e": {"value": Ke / te, "unit": "iterations/s", "h2d_bytes_per_step": n * k * 8,
                 "d2h_bytes_per_step": n * k * 8},
@@ -492,7 +504,7 @@ def run_native(args):
         "final_min_ratio": float(hist[-1]),
         "roofline": {"kernel": "restructured_pass", "bound": "hbm", "achieved": achieved,
                      "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                     "peak_source": peak_src,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": pass_ms},
         "plain_roofline": {"kernel": "plain_pass", "bound": "alu", "achieved": plain_flops / (plain_ms * 1e-3) / 1e12,
                            "peak": fp32_peak, "unit": "TFLOP/s",
@@ -673,11 +685,7 @@ def measure_sweep(args, K, Wm, local):
     gemm_flops = 3 * 2 * N * n * 256
     sm_max = peaks()[1]
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    bf16_peak = None
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        with open(pk) as f:
-            bf16_peak = float(json.load(f)["bf16_tflops_sustained"])
+    bf16_peak, bf16_src = bf16_peak_sustained()
     line = _common(args, cfg["workload"], it_s, "sweep iterations/s", ms / its, its, Wm, "f32",
                    {"N": N, "n": n, "k": "1..%d" % kmax, "alpha": alpha, "threshold": thr, "tuning": tuning,
                     "l2": "stored lengths 33.5 MB (L2-resident, shared by the 20 bases); X operands 67 MB"})
@@ -696,7 +704,7 @@ def measure_sweep(args, K, Wm, local):
                           "peak": bf16_peak, "unit": "TFLOP/s",
                           "frac": (gemm_flops / (kt["gemm_y"][0] * 1e-3) / 1e12 / bf16_peak)
                           if (kt["gemm_y"][0] and bf16_peak) else None,
-                          "peak_source": "measured bf16_tflops_sustained (FP16 operands: same nominal rate)"},
+                          "peak_source": bf16_src + " (FP16 operands: same nominal rate)"},
         "kernel_ms_per_launch": {name: v[0] for name, v in kt.items()},
         "pass_ms_per_basis_avg": pass_ms,
         "e2e": {"value": its / wall, "unit": "sweep iterations/s", "h2d_bytes_per_step": n * kmax * 8 / its,
@@ -768,7 +776,7 @@ def measure_batch(args, K, Wm, local):
     launches = st1["kernel_launches"] - st0
     its = K
     it_s = its / (ms * 1e-3)
-    hbm = peaks()[0]
+    hbm, _, peak_src = peaks()
     alg = 2 * (Ptot - st1["n_excluded"] - st1["n_near"])  # BF16 w per stored pair
     line = _common(args, cfg["workload"], it_s, "batch iterations/s", ms / its, its, Wm, "f32",
                    {"datasets": B, "N_min": min(Ns), "N_max": max(Ns), "n": n, "k": k, "alpha": alpha,
@@ -781,7 +789,7 @@ def measure_batch(args, K, Wm, local):
         "roofline": {"kernel": "whole batch iteration (32 passes + tails)", "bound": "hbm",
                      "achieved": alg / (ms * 1e-3 / its) / 1e9, "peak": hbm, "unit": "GB/s",
                      "frac": alg / (ms * 1e-3 / its) / 1e9 / hbm, "traffic": None,
-                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                     "peak_source": peak_src,
                      "alg_bytes_per_iteration": alg},
         "e2e": {"value": its / wall, "unit": "batch iterations/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -843,7 +851,7 @@ def run_softmin(args):
     kt = {name: _kernel_ms(s, name) for name in ("softmin_forward", "softmin_backward", "softmin_near",
                                                  "softmin_other")}
     s.set_profiling(False)
-    hbm = peaks()[0]
+    hbm, _, peak_src = peaks()
     nex = s.stats()["n_excluded"] + s.stats()["n_near"]
     alg = 4 * (P - nex)
     its = K
@@ -861,7 +869,7 @@ def run_softmin(args):
         "min_ratio_final": float(rmin),
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": alg / (dms * 1e-3) / 1e9 if dms else None,
                      "peak": hbm, "unit": "GB/s", "frac": alg / (dms * 1e-3) / 1e9 / hbm if dms else None,
-                     "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                     "traffic": None, "peak_source": peak_src,
                      "alg_bytes_per_launch": alg, "avg_launch_ms": dms},
         "kernel_ms_per_launch": {name: v[0] for name, v in kt.items()},
         "e2e": {"value": its / wall, "unit": "ascent steps/s", "h2d_bytes_per_step": 0,

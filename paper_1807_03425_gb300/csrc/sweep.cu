@@ -88,6 +88,12 @@ sap_status alloc_impl(sap_handle h, SweepState *&swp, int kmax, int hist_need)
     if (!restructured_u_maps(h, sw.Uhi, sw.Ulo, sw.KPG, &sw.mhi, &sw.mlo))
         return handle_fail(h, SAP_E_CUDA, "cuTensorMapEncodeTiled failed for the sweep's bases");
     sw.b.resize(kmax);
+    // Stream priorities, copied into the captured kernel nodes: the wider a
+    // basis, the longer its chain (its one-block FP64 update grows like n k^2
+    // and bounds the iteration), so its kernels are dispatched first when
+    // the chains of all bases compete for SMs.
+    int prio_least = 0, prio_greatest = 0;
+    WCK(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
     int off = 0;
     for (int q = 0; q < kmax; ++q) {
         SweepBasis &b = sw.b[q];
@@ -110,7 +116,8 @@ sap_status alloc_impl(sap_handle h, SweepState *&swp, int kmax, int hist_need)
         WCK(cudaMalloc(&b.partials, (size_t)kRecheckBlocks * sizeof(Partial)));
         WCK(cudaMalloc(&b.hist, (size_t)sw.hist_cap * sizeof(double)));
         WCK(cudaMalloc(&b.am, (size_t)sw.hist_cap * sizeof(int2)));
-        WCK(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
+        const int prio = prio_least + (int)std::lround((double)(prio_greatest - prio_least) * q / std::max(1, kmax - 1));
+        WCK(cudaStreamCreateWithPriority(&b.stream, cudaStreamNonBlocking, prio));
         WCK(cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
     }
     return SAP_OK;
@@ -279,7 +286,7 @@ sap_status run_graph(sap_handle h, SweepState &sw, double alpha, int eval_only, 
                 return st;
             }
             WCK(e);
-            e = cudaGraphInstantiate(&exec, graph, 0);
+            e = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
             cudaGraphDestroy(graph);
             WCK(e);
             sw.graphs.push_back({exec, alpha, eval_only, chunk, n_near, gen, per_chunk});

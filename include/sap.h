@@ -60,7 +60,7 @@ typedef enum {
     SAP_E_CUDA = 6,            /* CUDA runtime error (sticky for the handle) */
     SAP_E_TIMEOUT = 7,         /* a device-side bounded wait gave up */
     SAP_E_NO_DEVICE = 8,       /* no usable CUDA device */
-    SAP_E_UNSUPPORTED = 9,     /* valid request this build does not cover */
+    SAP_E_UNSUPPORTED = 9,     /* valid request the library does not cover */
     SAP_E_BOUNDS = 10          /* debug build (SAP_DEBUG_BOUNDS) only: a kernel met a data-dependent
                                   index out of range and skipped the access */
 } sap_status;

@@ -2,8 +2,8 @@
 reads from data -- a pair from a candidate or near list, a tile's block
 coordinates, a recent argmin pair -- is checked before it addresses memory,
 and an index out of range makes the call return SAP_E_BOUNDS instead of
-touching memory (no trap).  compute-sanitizer is not available on these
-GPUs; this build stands in for its out-of-bounds checks.
+touching memory (no trap): it stands in for a memory checker's
+out-of-bounds checks.
 
 The debug library runs every form of the path -- the restructured form with
 each second tier (the in-pass tiers included), the plain form in FP32 and

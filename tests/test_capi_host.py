@@ -104,7 +104,7 @@ def test_tuning_calls_validate_without_device(lib):
 
 def test_failure_hooks_validate_arguments(lib):
     """The test hooks refuse bad arguments on the host; without a device the
-    wait reports SAP_E_NO_DEVICE (on a GPU machine it is exercised by the GPU
+    wait reports SAP_E_NO_DEVICE (with a GPU it is exercised by the GPU
     tests)."""
     assert capi.sap_status_str(lib.sap_inject_fault(None, 1)) == "SAP_E_ARG"
     assert capi.sap_status_str(lib.sap_selftest_wait(None, -1)) == "SAP_E_ARG"
